@@ -1,0 +1,313 @@
+"""SBCI1 as the paper states it (oracle; test infrastructure only).
+
+Follows Algorithm 1 (SBCI1 for state alpha) with Sections S1.1-S1.5:
+
+* initial trial vectors from the lowest diagonal elements (S1.1, Eqs. S1-S3),
+  or a given vector (then X_0 = H x_0 and E_0 its Rayleigh quotient, Eq. 2);
+* excited-state start from the second eigenvector of V at the converging step
+  (S1.4), orthogonalised against the stored states (Eqs. S4-S7);
+* preconditioned, projected residual z (Eq. S8 / Eq. S31) with
+  M^-1 = (D - E^0 I)^-1 (Eqs. 6-7);
+* one H-product per step, Z = H z (Eq. S9 / Eq. S32);
+* closed-form Gram-Schmidt, subspace matrix and parameters: first step
+  (Eqs. S10-S24), later steps (Eqs. S33-S55);
+* the momentum/position and H-image recurrences (Eqs. S25-S28, S56-S59);
+* residual z' (Eq. S29 / Eq. S60) and convergence (Eq. S30 / Eq. S61);
+* norm-triggered restart (Eqs. S62a-c and max_cycle).
+
+Readings where the paper is silent or ambiguous (each is listed with its
+reason in the design notes of the repository):
+
+R1  z' = (X - E x)/k (Eqs. S29/S60); |z'| is then the residual norm of the
+    unit vector x/|x| because |k| = |x| (Eq. S62b).
+R2  The preconditioner denominator d = D_I - E^0 is replaced by
+    sign(d) * guard when |d| < guard (guard = 1e-8; d = 0 -> +guard).
+R3  E^0 is the current Rayleigh quotient E_t for state 0 and E_c^0 for
+    excited states.
+R4  A restart keeps x/|x| and X/|x|, sets y = Y = 0 and t = 0, and takes the
+    first-step (2x2) path with z'_0 = X_0 - E_0 x_0; no extra H-product.
+R5  max_cycle: a restart is triggered when t + 1 reaches max_cycle.
+R6  A cap of ``max_sigma`` H-products per state ends the state unconverged.
+R7  Gram-Schmidt breakdown: if a squared GS norm falls below gs_tol times the
+    squared norm of the vector being orthogonalised, the direction is dropped
+    (y dropped: first-step path; z dropped: c = 0 and the 2x2 problem in x, y).
+R8  Initial determinants: the n_init lowest diagonal elements ordered by
+    (D_I, flat index I), n_init = max(n_states, 2) unless given.
+R9  X_0 of an excited state uses H x_c = E_c x_c (Eq. S5), no extra H-product.
+R10 sector = 1 keeps c = c^T (Ia <-> Ib swap, n_alpha = n_beta): initial
+    vectors and every z are symmetrised, z <- (z + z^T)/2.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class SBCIParams:
+    eps0: float = 1e-10  # S30/S61, no frozen core
+    r0: float = 1e-5
+    b_th: float = 1e-2  # S62a
+    eps1: float = 1e-7
+    x_th1: float = 0.1  # S62b
+    x_th2: float = 1.2
+    r1: float = 1.0  # S62c
+    max_cycle: int = 20  # S1.5
+    max_sigma: int = 1000  # R6, per state
+    guard: float = 1e-8  # R2
+    gs_tol: float = 1e-14  # S1.1 and R7
+    sector: int = 0  # R10
+    n_init: int | None = None  # R8
+
+
+@dataclass
+class StepRecord:
+    state: int
+    t: int
+    energy: float
+    b: float
+    c: float
+    k: float
+    dE: float
+    dz: float
+    event: str  # "", "converged", "restart:a", "restart:b", "restart:c", "restart:max"
+
+
+@dataclass
+class StateResult:
+    energy: float
+    vector: np.ndarray
+    converged: bool
+    n_sigma: int
+    n_step: int
+    restarts: dict = field(default_factory=dict)
+
+
+def _guarded(d: np.ndarray, guard: float) -> np.ndarray:
+    return np.where(np.abs(d) < guard, np.where(d < 0.0, -guard, guard), d)
+
+
+def _sym(v: np.ndarray, shape) -> np.ndarray:
+    m = v.reshape(shape)
+    return (0.5 * (m + m.T)).reshape(-1)
+
+
+class SBCI1:
+    """SBCI1 driver over a sigma callable ``apply(v) -> H v`` (no e_core)."""
+
+    def __init__(self, apply, diag: np.ndarray, shape, params: SBCIParams | None = None):
+        self.apply = apply
+        self.diag = np.asarray(diag, dtype=np.float64).reshape(-1)
+        self.shape = tuple(shape)  # (Na, Nb)
+        self.p = params or SBCIParams()
+        self.trace: list[StepRecord] = []
+        self.n_sigma = 0
+
+    # -- helpers --------------------------------------------------------------
+    def H(self, v):
+        self.n_sigma += 1
+        return np.asarray(self.apply(v.reshape(self.shape)), dtype=np.float64).reshape(-1)
+
+    def _project(self, v, xc):
+        """(1 - sum_i x_c^i x_c^iT) v (Eq. S8 / S31)."""
+        for u in xc:
+            v = v - u * (u @ v)
+        return v
+
+    # -- S1.1 -----------------------------------------------------------------
+    def initial_guess(self, nstates: int):
+        """Eqs. S1-S3: lowest-diagonal determinants, GS, subspace eigh."""
+        n_init = self.p.n_init or max(nstates, 2)
+        N = self.diag.size
+        order = np.lexsort((np.arange(N), self.diag))  # (D_I, I) ascending
+        basis = []
+        for I in order[:n_init]:
+            e = np.zeros(N)
+            e[I] = 1.0
+            if self.p.sector:
+                e = _sym(e, self.shape)
+            for u in basis:
+                e = e - u * (u @ e)
+            nrm = np.linalg.norm(e)
+            if nrm < self.p.gs_tol:
+                continue
+            basis.append(e / nrm)
+        Xm = [self.H(u) for u in basis]
+        A = np.array([[u @ Xv for Xv in Xm] for u in basis])
+        w, U = np.linalg.eigh(0.5 * (A + A.T))
+        x0 = sum(U[i, 0] * basis[i] for i in range(len(basis)))
+        X0 = sum(U[i, 0] * Xm[i] for i in range(len(basis)))
+        return x0, X0, float(w[0])
+
+    # -- one state (Algorithm 1) ----------------------------------------------
+    def solve_state(self, alpha: int, x0, X0, E0, xc, Ec):
+        p = self.p
+        sigma0 = self.n_sigma
+        # Algorithm 1 start: project out the stored states, Eqs. S4-S7
+        ov = [u @ x0 for u in xc]
+        x0p = x0 - sum((o * u for o, u in zip(ov, xc)), np.zeros_like(x0))
+        X0p = X0 - sum((e * o * u for e, o, u in zip(Ec, ov, xc)), np.zeros_like(X0))
+        nrm = np.linalg.norm(x0p)
+        x, X = x0p / nrm, X0p / nrm
+        E = E0
+        y = np.zeros_like(x)
+        Y = np.zeros_like(x)
+        zp = X - E * x  # residual (H - E_0) x_0 of Algorithm 1, |x| = 1
+        t = 0
+        nstep = 0
+        restarts = {"a": 0, "b": 0, "c": 0, "max": 0}
+        second = None
+        while True:
+            if self.n_sigma - sigma0 >= p.max_sigma:
+                return StateResult(E, x / np.linalg.norm(x), False, self.n_sigma - sigma0,
+                                   nstep, restarts), second
+            E_pre = E if alpha == 0 else Ec[0]  # R3
+            w = zp / _guarded(self.diag - E_pre, p.guard)  # Eq. S31
+            if p.sector:
+                w = _sym(w, self.shape)
+            z = self._project(w, xc)
+            Z = self.H(z)  # Eq. S32
+            if t > 0:
+                Nxx, Nxy, Nyy = x @ x, x @ y, y @ y
+                if Nyy - Nxy * Nxy / Nxx < p.gs_tol * Nyy:  # R7: y inside span{x}
+                    nx = np.sqrt(Nxx)
+                    x, X = x / nx, X / nx
+                    y = np.zeros_like(x)
+                    Y = np.zeros_like(x)
+                    t = 0
+            if t == 0:
+                E_new, b, c, k, sec = self._first_step(x, X, z, Z)
+                y_new = -c * z  # S25
+                Y_new = -c * Z  # S26
+                x_new = x + y_new  # S27 (b_0 = 1)
+                X_new = X + Y_new  # S28
+            else:
+                E_new, b, c, k, sec = self._later_step(x, X, y, Y, z, Z)
+                y_new = y - c * z  # S56
+                Y_new = Y - c * Z  # S57
+                x_new = x + b * y_new  # S58
+                X_new = X + b * Y_new  # S59
+            # second Ritz vector in terms of the pre-update vectors (S1.4)
+            cx, cy, cz, E2 = sec
+            second = (cx * x + cy * y + cz * z, cx * X + cy * Y + cz * Z, E2)
+            zp_new = (X_new - E_new * x_new) / k  # S60 (R1)
+            dE = abs(E_new - E)
+            dz = float(np.linalg.norm(zp_new))
+            nstep += 1
+            x, X, y, Y, zp = x_new, X_new, y_new, Y_new, zp_new
+            if dE < p.eps0 and dz < p.r0:  # S61
+                self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz, "converged"))
+                return StateResult(E_new, x / np.linalg.norm(x), True, self.n_sigma - sigma0,
+                                   nstep, restarts), second
+            cause = ""
+            if alpha > 0 and abs(b) < p.b_th and dE < p.eps1:
+                cause = "a"
+            elif abs(k) < p.x_th1 or abs(k) > p.x_th2:
+                cause = "b"
+            elif dz > p.r1 and t > 0:
+                cause = "c"
+            elif t + 1 >= p.max_cycle:
+                cause = "max"
+            self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz,
+                                         f"restart:{cause}" if cause else ""))
+            E = E_new
+            if cause:  # restart of Algorithm 1 with R4
+                restarts[cause] += 1
+                nx = np.linalg.norm(x)
+                x, X = x / nx, X / nx
+                y = np.zeros_like(x)
+                Y = np.zeros_like(x)
+                zp = X - E * x
+                t = 0
+            else:
+                t += 1
+
+    def _first_step(self, x, X, z, Z):
+        """Eqs. S10-S24 (x normalised, y = 0)."""
+        p = self.p
+        Nxz, Nzz = x @ z, z @ z
+        Hxx, Hxz, Hzz = x @ X, x @ Z, z @ Z
+        g = Nzz - Nxz * Nxz
+        if g < p.gs_tol * Nzz or g <= 0.0:  # R7: z inside span{x}
+            return Hxx, 0.0, 0.0, 1.0, (0.0, 0.0, 0.0, Hxx)
+        Bz = 1.0 / np.sqrt(g)  # S12
+        Bx = -Nxz * Bz  # S13
+        V = np.array([[Hxx, Bx * Hxx + Bz * Hxz],
+                      [Bx * Hxx + Bz * Hxz, Bx * Bx * Hxx + Bz * Bz * Hzz + 2 * Bx * Bz * Hxz]])
+        lam, U = np.linalg.eigh(V)
+        vx, vz = U[0, 0], U[1, 0]
+        k = 1.0 / (vx + vz * Bx)  # S23
+        c = -vz * Bz / (vx + vz * Bx)  # S24
+        wx, wz = U[0, 1], U[1, 1]
+        sec = (wx + wz * Bx, 0.0, wz * Bz, float(lam[1]))
+        return float(lam[0]), 1.0, float(c), float(k), sec
+
+    def _later_step(self, x, X, y, Y, z, Z):
+        """Eqs. S33-S55."""
+        p = self.p
+        Nxx, Nxy, Nxz = x @ x, x @ y, x @ z
+        Nyy, Nyz, Nzz = y @ y, y @ z, z @ z
+        Hxx, Hxy, Hxz = x @ X, x @ Y, x @ Z
+        Hyy, Hyz, Hzz = y @ Y, y @ Z, z @ Z
+        Ax = 1.0 / np.sqrt(Nxx)  # S34
+        gy = Nyy - Nxy * Nxy / Nxx
+        By = 1.0 / np.sqrt(gy)  # S36
+        Bx = -Nxy / Nxx * By  # S37
+        P = Bx * Nxz + By * Nyz  # S42
+        gz = Nzz - Nxz * Nxz / Nxx - P * P
+        if gz < p.gs_tol * Nzz or gz <= 0.0:  # R7: z inside span{x, y}
+            V = np.array([[Ax * Ax * Hxx, Ax * (Bx * Hxx + By * Hxy)],
+                          [Ax * (Bx * Hxx + By * Hxy),
+                           Bx * Bx * Hxx + By * By * Hyy + 2 * Bx * By * Hxy]])
+            lam, U = np.linalg.eigh(V)
+            vx, vy = U[0, 0], U[1, 0]
+            k = 1.0 / (vx * Ax + vy * Bx)
+            b = vy * By * k
+            wx, wy = U[0, 1], U[1, 1]
+            return float(lam[0]), float(b), 0.0, float(k), \
+                (wx * Ax + wy * Bx, wy * By, 0.0, float(lam[1]))
+        Cz = 1.0 / np.sqrt(gz)  # S39
+        Cy = -P * By * Cz  # S40
+        Cx = -(Nxz / Nxx + P * Bx) * Cz  # S41
+        hx = Cx * Hxx + Cy * Hxy + Cz * Hxz  # x^T H zbar / 1
+        hy = Cx * Hxy + Cy * Hyy + Cz * Hyz  # y^T H zbar
+        V = np.empty((3, 3))
+        V[0, 0] = Ax * Ax * Hxx  # S44a
+        V[0, 1] = V[1, 0] = Ax * (Bx * Hxx + By * Hxy)  # S44b
+        V[0, 2] = V[2, 0] = Ax * hx  # S44c
+        V[1, 1] = Bx * Bx * Hxx + By * By * Hyy + 2 * Bx * By * Hxy  # S44d
+        V[1, 2] = V[2, 1] = Bx * hx + By * hy  # S44e (ybar^T H zbar)
+        V[2, 2] = (Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz
+                   + 2 * Cx * Cy * Hxy + 2 * Cx * Cz * Hxz + 2 * Cy * Cz * Hyz)  # S44f
+        lam, U = np.linalg.eigh(V)
+        vx, vy, vz = U[:, 0]
+        den = vx * Ax + vy * Bx + vz * Cx
+        k = 1.0 / den  # S53
+        b = (vy * By + vz * Cy) / den  # S54
+        c = -vz * Cz / (vy * By + vz * Cy)  # S55
+        wx, wy, wz = U[:, 1]
+        sec = (wx * Ax + wy * Bx + wz * Cx, wy * By + wz * Cy, wz * Cz, float(lam[1]))
+        return float(lam[0]), float(b), float(c), float(k), sec
+
+    # -- driver ---------------------------------------------------------------
+    def solve(self, nstates: int, c0: np.ndarray | None = None):
+        """States 0..nstates-1 in sequence (Fig. 1A)."""
+        xc, Ec, results = [], [], []
+        if c0 is None:
+            x0, X0, E0 = self.initial_guess(nstates)
+        else:
+            x0 = np.asarray(c0, dtype=np.float64).reshape(-1).copy()
+            if self.p.sector:
+                x0 = _sym(x0, self.shape)
+            x0 /= np.linalg.norm(x0)
+            X0 = self.H(x0)
+            E0 = float(x0 @ X0)
+        for alpha in range(nstates):
+            res, second = self.solve_state(alpha, x0, X0, E0, xc, Ec)
+            results.append(res)
+            xc.append(res.vector)
+            Ec.append(res.energy)
+            if alpha + 1 < nstates:
+                x0, X0, E0 = second  # S1.4
+        return results
