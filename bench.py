@@ -1,0 +1,349 @@
+"""Benchmark of the GB300 SBCI library on the H10 singlet workload.
+
+Workload: linear H10 chain, STO-3G, Loewdin basis, 1.2 A spacing, 10 orbitals,
+5 alpha / 5 beta electrons, 252 x 252 = 63,504 determinants; the ground state
+and 3 excited states in the c = c^T (singlet) sector; SBCI1 with the paper's
+thresholds.  One step = one complete solve of the 4 states.
+
+Default arm: the CUDA library (device-resident integrals, CUDA-event timing on
+the library stream, L2 flushed between steps), plus an end-to-end number
+through the C ABI with host buffers, a roofline entry for the dominant kernel
+and the CPU oracle timed on the host cores.  ``--impl reference`` times the
+oracle alone (bounded samples).  Under torchrun every rank runs independent
+solves (replicas); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FCI solves/sec (H10 STO-3G 1.2 A, 4 singlet-sector states, SBCI1)"
+WORKLOAD = "h10_sto3g_1.2A_4states_singlet"
+NSTATES = 4
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (profiling recipe table)
+BF16_NOMINAL_TFLOPS = 2250.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2603_06101_gb300 import inputs
+
+    return inputs.h_chain(10, 1.2)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for row in csv.reader(f):
+                    if len(row) < 9:
+                        continue
+                    try:
+                        sm.append(float(row[1]))
+                        smax.append(float(row[2]))
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, row[5:9]):
+                        if "Active" in v and "Not" not in v:
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source
+    is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    if e.get("source_sha") != source_sha(*e["sources"]):
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+# ----------------------------------------------------------------------------
+def oracle_solve_time(I, nstates, max_steps=None):
+    """Times the oracle's SBCI1 on the workload; returns (seconds, steps, done)."""
+    from oracle import sbci as osb
+    from oracle import sigma as osg
+    from oracle import slater_condon as osc
+
+    sig = osg.StringSigma(I.h1, I.eri, I.nalpha, I.nbeta)
+    D = osc.diagonal_by_occupation(I.h1, I.eri, I.nalpha, I.nbeta)
+
+    class Capped(osb.SBCI1):
+        steps = 0
+
+        def H(self, v):
+            if max_steps is not None and self.n_sigma >= max_steps:
+                raise StopIteration
+            return super().H(v)
+
+    run = Capped(sig.apply, D, (sig.Na, sig.Nb), osb.SBCIParams(sector=1))
+    t0 = time.perf_counter()
+    done = True
+    try:
+        run.solve(nstates)
+    except StopIteration:
+        done = False
+    return time.perf_counter() - t0, run.n_sigma, done
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    I = workload()
+    # one untimed full solve fixes the number of H-products per solve
+    t_full, nsig_full, _ = oracle_solve_time(I, NSTATES)
+    sample = 12  # H-products per bounded sample (initial guess + first SB steps)
+    for _ in range(args.warmup):
+        oracle_solve_time(I, NSTATES, max_steps=sample)
+    times = []
+    for _ in range(args.steps):
+        t, n, _ = oracle_solve_time(I, NSTATES, max_steps=sample)
+        times.append(t / n)
+    per_sigma = float(np.mean(times))
+    value = 1.0 / (per_sigma * nsig_full)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "norb": 10, "ndet": 63504, "states": NSTATES, "sector": "c=c^T"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: the first {sample} H-products of the oracle SBCI1 solve "
+                                   f"(time per H-product incl. its SB work), scaled by the "
+                                   f"{nsig_full} H-products of one full oracle solve ({t_full:.1f} s)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+
+    from paper_2603_06101_gb300 import sbci
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    I = workload()
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    stream = torch.cuda.Stream()
+    ctx = sbci.Context.from_integrals(I, stream=stream.cuda_stream)
+    p = sbci.params(sector=1, prec=prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_solve():
+        E, _, R, st = ctx.solve(NSTATES, p)
+        return E, R, st
+
+    for _ in range(max(args.warmup, 3)):
+        E, R, st = one_solve()
+    nsig = sum(r.n_sigma for r in R)
+    # ---------------- timed region: device-resident, CUDA events on the library stream
+    sampler = ClockSampler(local_rank)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_ms = 0.0
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)  # L2 flush: 256 MB > 129 MB L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E, R, st = one_solve()
+        e1.record(stream)
+        e1.synchronize()
+        t_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    stats = ctx.profile_read()
+    ctx.profile(False)
+    t_max = t_ms
+    if dist:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1000.0)
+    launches = sum(v[0] for v in stats.values())
+    # ---------------- roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms) = dom
+    npair, ndet = ctx.npair, ctx.ndet
+    avg_s = ms / 1000.0 / max(nl, 1)
+    if name == "sigma_gather_contract":
+        flops = 2.0 * npair * npair * ndet
+        if args.prec == "fp64":
+            peak = pk.get("bf16_tflops", 1900.0) * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_kind": f"{pk_kind} bf16 x nominal FP64/BF16 ratio (1.25/2250)"}
+        else:
+            peak = 2.0 * 152 * 128 * (clocks["sm_mhz"] or 1900.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock"}
+        roof["algorithmic_per_launch"] = flops
+    else:
+        bytes_alg = 16.0 * ndet if name == "sigma_scatter" else 13 * 8.0 * ndet
+        roof = {"bound": "hbm", "achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_kind": pk_kind, "algorithmic_per_launch": bytes_alg}
+    roof["kernel"] = name
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(name)
+    roof["avg_launch_us"] = avg_s * 1e6
+    roof["share_of_step"] = ms / max(t_ms, 1e-9)
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h1 = np.ascontiguousarray(I.h1)
+        eri = np.ascontiguousarray(I.eri)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            c2 = sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=stream.cuda_stream)
+            E2, V2, _, _ = c2.solve(NSTATES, p, want_vectors=True)
+            c2.close()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": args.steps / te, "unit": "solves/s",
+               "h2d_bytes_per_step": int(h1.nbytes + eri.nbytes),
+               "d2h_bytes_per_step": int(E2.nbytes + V2.nbytes)}
+    # ---------------- CPU oracle on the host cores (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_full, nsig_o, _ = oracle_solve_time(I, NSTATES)
+        cpu = {"value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one full oracle SBCI1 solve of the same workload ({nsig_o} H-products, "
+                         f"{t_full:.1f} s, numpy/OpenBLAS on all host cores)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "norb": 10, "ndet": ndet, "states": NSTATES,
+                       "sector": "c=c^T", "sigma_precision": args.prec, "l2": "flushed (256 MB write) between steps",
+                       "parallelism": f"replicas x{world}", "sigma_per_solve": nsig,
+                       "energies": [float(e) for e in E]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items() if v[0]},
+            "clocks": clocks, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_gb300(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

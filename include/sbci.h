@@ -1,0 +1,184 @@
+/*
+ * sbci.h -- C ABI of the GB300 SBCI library (libsbci.so).
+ *
+ * SBCI (simulated-bifurcation-based configuration interaction, arXiv
+ * 2603.06101) finds the lowest k eigenpairs of the FCI Hamiltonian H by
+ * integrating a classical system whose positions are the CI coefficients
+ * (Eq. 1-11, Algorithm 1).  Every step needs one H-product Z = H z (Eq. S9,
+ * Eq. S32), the "sigma build", which this library runs as CUDA kernels for
+ * sm_103a over alpha/beta determinant strings.
+ *
+ * Conventions shared by every entry point:
+ *  - Orbitals are real; h1 is the n x n core Hamiltonian, eri the n^4
+ *    chemists'-notation integrals (ij|kl), both row-major FP64.
+ *  - A string is an m-subset of the n orbitals; strings are ordered by
+ *    increasing bitmask value.  A determinant |Ia Ib> has all alpha creators
+ *    (ascending) left of all beta creators (ascending).  CI vectors are FP64
+ *    [Na][Nb] row-major with flat index Ia*Nb + Ib.
+ *  - sigma is the electronic H c, without e_core; energies are totals
+ *    (electronic + e_core).
+ *  - The caller owns every pointer it passes.  Host arrays are read or
+ *    written during the call only; the library keeps no caller pointer.
+ *    "Device" pointers are CUDA global-memory addresses on the context's GPU.
+ *  - Every call returns sbci_status; no exception crosses the ABI.  On an
+ *    error, sbci_last_error() gives a thread-local message.
+ *  - NaN/Inf in caller inputs -> SBCI_ERR_NUMERIC before any GPU work.
+ *  - The library never traps or spins without bound on the GPU.
+ *  - Size limits: 1 <= n <= 16, 0 <= nalpha, nbeta <= n, nalpha+nbeta >= 1.
+ */
+#ifndef SBCI_H
+#define SBCI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbci_ctx sbci_ctx;
+
+typedef enum {
+  SBCI_OK = 0,
+  SBCI_ERR_INVALID = 1,       /* bad argument or call order */
+  SBCI_ERR_NOMEM = 2,         /* device or host allocation failed */
+  SBCI_ERR_CUDA = 3,          /* CUDA runtime error (message has the code) */
+  SBCI_ERR_NUMERIC = 4,       /* NaN/Inf in inputs or in a device reduction */
+  SBCI_ERR_NOT_CONVERGED = 5, /* step cap reached; best energies written */
+  SBCI_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+  SBCI_ERR_CANCELLED = 7      /* request cancelled (serving) */
+} sbci_status;
+
+/* Arithmetic of the two-electron contraction inside sigma. */
+typedef enum {
+  SBCI_FP64 = 0,   /* FP64 gather, FP64 contraction (DFMA), FP64 scatter */
+  SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
+  SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores, FP32 accumulation */
+  SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */
+} sbci_precision;
+
+/* Solver parameters.  Defaults (sbci_params_init) are the paper's values for
+ * calculations without frozen core (Section S1.3, S1.5). */
+typedef struct {
+  double eps0;      /* |E_{t+1}-E_t| < eps0 ... (Eq. S61), default 1e-10 */
+  double r0;        /* ... and |z'| < r0, default 1e-5 */
+  double b_th;      /* restart S62a: alpha>0, |b|<b_th, dE<eps1; 1e-2 */
+  double eps1;      /* 1e-7 */
+  double x_th1;     /* restart S62b: |k| < x_th1 or |k| > x_th2; 0.1 */
+  double x_th2;     /* 1.2 */
+  double r1;        /* restart S62c: |z'| > r1 and t > 0; 1.0 */
+  int max_cycle;    /* restart when t+1 reaches max_cycle (S1.5); 20 */
+  int max_sigma;    /* cap on H-products per state; 1000 */
+  double guard;     /* |D_I - E0| floor of the preconditioner; 1e-8 */
+  double gs_tol;    /* Gram-Schmidt drop tolerance (S1.1); 1e-14 */
+  int sector;       /* 0: every determinant; 1: c = c^T (needs nalpha == nbeta) */
+  int n_init;       /* determinants of the initial guess; 0 -> max(k, 2) */
+  int init;         /* 0: lowest diagonal (S1.1); 1: caller vector c0 */
+  int prec;         /* sbci_precision of the main stage; SBCI_FP64 */
+  double mixed_eps; /* low-precision stage ends at dE < mixed_eps ... ; 1e-8 */
+  double mixed_r;   /* ... and |z'| < mixed_r; 1e-4 */
+  int refine_max_sigma; /* FP64 refinement cap per state; 30 */
+} sbci_params;
+
+typedef struct {
+  double energy;      /* total energy (electronic + e_core) */
+  double residual;    /* |H x - E x| / |x| from the carried H-image */
+  int converged;      /* 1 if Eq. S61 held (in FP64 after refinement) */
+  int n_sigma;        /* H-products spent on this state (all precisions) */
+  int n_sigma_fp64;   /* of which FP64 */
+  int n_step;         /* SB steps */
+  int n_restart[4];   /* restarts by cause: S62a, S62b, S62c, max_cycle */
+} sbci_report;
+
+typedef struct {
+  int state;          /* alpha */
+  int t;              /* step index within the current restart cycle */
+  double energy;      /* E_{t+1}, electronic (no e_core) */
+  double b, c, k;     /* parameters of the step (Eqs. S23-S24, S53-S55) */
+  double dE, dz;      /* |E_{t+1}-E_t| and |z'_{t+1}| */
+  int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle */
+  int prec;           /* sbci_precision of the sigma used in the step */
+} sbci_trace_record;
+
+/* Fills *p with the defaults listed above.  Returns SBCI_ERR_INVALID on NULL. */
+sbci_status sbci_params_init(sbci_params *p);
+
+/* Creates a context on the current CUDA device for one active space.
+ * Builds the string tables (host), the packed two-electron operator W
+ * (one-electron part absorbed), the diagonal of H, and uploads them.
+ * h1: host [norb*norb]; eri: host [norb^4] (ij|kl); both FP64, read only.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a library-owned stream.
+ * On success *out owns all device memory until sbci_destroy. */
+sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
+                                const double *h1, const double *eri, double e_core,
+                                void *cuda_stream);
+
+/* Sizes of the determinant space: Ndet = Na*Nb; nlink = m(n-m+1) per string;
+ * npair = n(n+1)/2.  Any output pointer may be NULL. */
+sbci_status sbci_dims(const sbci_ctx *ctx, long long *ndet, int *na, int *nb,
+                      int *nlink_a, int *nlink_b, int *npair);
+
+/* Copies the device excitation table of one spin (0 alpha, 1 beta) to host
+ * out[nstr*nlink*3] as (pair index, target string J, sign) triples in the
+ * stored order: for each string I, for each occupied l ascending, for each
+ * k in unocc(I) U {l} ascending, a+_k a_l |I> = sign |J>, pair = max(k,l)*
+ * (max(k,l)+1)/2 + min(k,l). */
+sbci_status sbci_string_table(const sbci_ctx *ctx, int spin, int *out);
+
+/* D_I = <I|H|I> (electronic).  out: [Ndet] host (on_device = 0) or device. */
+sbci_status sbci_diagonal(sbci_ctx *ctx, double *out, int on_device);
+
+/* sigma = H c for nvec vectors, each [Ndet] (electronic H, no e_core).
+ * c and sigma: host (on_device = 0) or device (on_device = 1) pointers to
+ * nvec*Ndet doubles; they must not overlap.  prec: sbci_precision. */
+sbci_status sbci_sigma(sbci_ctx *ctx, const double *c, double *sigma, int nvec,
+                       int prec, int on_device);
+
+/* Starts an SBCI1 solve for the k lowest states (Fig. 1A, Algorithm 1).
+ * params may be NULL (defaults).  c0: host [Ndet] when params->init == 1,
+ * else ignored (may be NULL).  Allocates the per-solve vectors. */
+sbci_status sbci_begin(sbci_ctx *ctx, int k, const sbci_params *params, const double *c0);
+
+/* One SB step of the current state (preconditioned projected residual,
+ * sigma, 2x2/3x3 subspace solve, update, convergence/restart test).
+ * rec (may be NULL) receives the step record.  *done = 1 when all k states
+ * have ended.  Returns SBCI_ERR_NOT_CONVERGED when a state hit max_sigma
+ * (the solve then moves on to the next state). */
+sbci_status sbci_step(sbci_ctx *ctx, sbci_trace_record *rec, int *done);
+
+/* Results of the solve: energies [k] (total), vecs [k*Ndet] host (or NULL),
+ * rep [k] (or NULL). */
+sbci_status sbci_finish(sbci_ctx *ctx, double *energies, double *vecs, sbci_report *rep);
+
+/* begin + steps until done + finish.  Returns SBCI_ERR_NOT_CONVERGED if any
+ * state stopped at its cap (results still written). */
+sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const double *c0,
+                       double *energies, double *vecs, sbci_report *rep);
+
+/* Copies up to cap trace records of the last solve; *n = records available. */
+sbci_status sbci_trace(const sbci_ctx *ctx, sbci_trace_record *buf, int cap, int *n);
+
+/* Per-kernel statistics of the library's own launches on the context stream. */
+typedef struct {
+  char name[32];       /* kernel family, e.g. "sigma_gather_contract" */
+  long long launches;  /* launches since the last sbci_profile call */
+  double total_ms;     /* summed CUDA-event time of those launches (0 if timing off) */
+} sbci_kernel_stat;
+
+/* Resets the statistics; enable = 1 also brackets every launch with CUDA
+ * events on the context stream (adds ~2 event records per launch). */
+sbci_status sbci_profile(sbci_ctx *ctx, int enable);
+
+/* Waits for the recorded events and copies up to cap entries; *n = families. */
+sbci_status sbci_profile_read(sbci_ctx *ctx, sbci_kernel_stat *out, int cap, int *n);
+
+/* Thread-local message of the last error in this thread ("" if none). */
+const char *sbci_last_error(void);
+
+/* Frees everything the context owns.  NULL is a no-op. */
+void sbci_destroy(sbci_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBCI_H */

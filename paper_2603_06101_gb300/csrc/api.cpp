@@ -1,0 +1,1103 @@
+// C ABI of libsbci: context and integral preparation, the sigma entry point,
+// and the host controller of SBCI1 (Algorithm 1 with Sections S1.1-S1.5).
+//
+// Per SB step the controller launches, on one stream and without a host
+// round trip in between:
+//   update sweep (Eqs. 10-11, S56-S60, preconditioner Eqs. 6-7)
+//   -> [reduce x_c.w -> projection (Eq. S31)] -> sigma(z) (Eq. S32) with dots
+//   -> reduction of every dot -> one 8-byte-per-slot copy to pinned memory,
+// then synchronises once and solves the 2x2 (Eqs. S10-S24) or 3x3
+// (Eqs. S33-S55) subspace problem on the host in FP64.  A restart (S62) is
+// applied lazily: the next update scales x, X by 1/|x| and zeroes y, Y.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "../../include/sbci.h"
+#include "sbci_internal.h"
+
+namespace sbci {
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+}  // namespace sbci
+
+using namespace sbci;
+
+#define CK(expr)                                                                      \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      set_error(std::string("CUDA error ") + cudaGetErrorName(_e) + " (" +            \
+                cudaGetErrorString(_e) + ") at " + #expr);                            \
+      return (_e == cudaErrorMemoryAllocation) ? SBCI_ERR_NOMEM : SBCI_ERR_CUDA;      \
+    }                                                                                 \
+  } while (0)
+
+#define RET(st)                         \
+  do {                                  \
+    sbci_status _s = (st);              \
+    if (_s != SBCI_OK) return _s;       \
+  } while (0)
+
+namespace {
+
+// Per-kernel launch counts (always) and CUDA-event times on the context stream
+// (when profiling is enabled).
+enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_COUNT };
+const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
+                                       "sb_project", "reduce", "lincomb", "dots", "diagonal"};
+
+struct Prof {
+  bool on = false;
+  long long launches[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> kid;
+};
+
+struct Solver {
+  bool active = false, done = false;
+  int k = 0;
+  sbci_params p{};
+  int alpha = 0;
+  int prec = SBCI_FP64;  // precision of the sigma in use
+  // device vectors [ndet] each
+  double *x = nullptr, *X = nullptr, *y = nullptr, *Y = nullptr, *w = nullptr;
+  double *z[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr};
+  double *xc = nullptr;  // [k][ndet]
+  int cur = 0;
+  // host scalars of the current state
+  double E = 0.0;        // E_t
+  int t = 0;
+  bool first = true;     // next step takes the first-step (2x2) path
+  double sx_pending = 1.0;
+  bool proj = false;     // projection kernel in use (alpha > 0 or sector)
+  double dots[S_COUNT];
+  std::vector<double> Ec;
+  std::vector<sbci_report> rep;
+  std::vector<sbci_trace_record> trace;
+  int any_unconverged = 0;
+};
+
+}  // namespace
+
+struct sbci_ctx {
+  int n = 0, ne_a = 0, ne_b = 0;
+  StringSet sa, sb;
+  int Na = 0, Nb = 0, npair = 0, npair_pad = 0;
+  long long ndet = 0;
+  double e_core = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int grid = 0;
+  uint32_t *d_link_a = nullptr, *d_link_b = nullptr, *d_mask_b = nullptr;
+  double *d_W = nullptr;
+  float *d_Wf = nullptr;
+  double *d_diag = nullptr;
+  double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
+  void *d_G = nullptr;
+  size_t G_bytes = 0;
+  double *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
+  double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
+  size_t tmp_elems = 0;
+  std::vector<double> W_host;
+  Solver s;
+  Prof prof;
+};
+
+namespace {
+
+sbci_status check_finite(const double *v, size_t n, const char *what) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) {
+      set_error(std::string("non-finite value in ") + what);
+      return SBCI_ERR_NUMERIC;
+    }
+  return SBCI_OK;
+}
+
+template <typename T>
+sbci_status dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  CK(cudaMalloc((void **)p, count * sizeof(T)));
+  return SBCI_OK;
+}
+
+sbci_status ensure_G(sbci_ctx *c, int prec) {
+  const size_t need = sigma_scratch_bytes(c->npair, c->ndet, prec == SBCI_FP64 ? 0 : 1);
+  if (c->G_bytes >= need) return SBCI_OK;
+  if (c->d_G) CK(cudaFree(c->d_G));
+  c->d_G = nullptr;
+  c->G_bytes = 0;
+  CK(cudaMalloc(&c->d_G, need));
+  c->G_bytes = need;
+  return SBCI_OK;
+}
+
+sbci_status prof_flush(sbci_ctx *c) {
+  Prof &p = c->prof;
+  for (size_t i = 0; i < p.kid.size(); ++i) {
+    float ms = 0.0f;
+    CK(cudaEventSynchronize(p.pool[2 * i + 1]));
+    CK(cudaEventElapsedTime(&ms, p.pool[2 * i], p.pool[2 * i + 1]));
+    p.ms[p.kid[i]] += ms;
+  }
+  p.kid.clear();
+  p.used = 0;
+  return SBCI_OK;
+}
+
+// Launch wrapper: counts the launch and, when profiling, brackets it with events.
+template <typename F>
+sbci_status timed(sbci_ctx *c, int kid, F &&launch) {
+  Prof &p = c->prof;
+  p.launches[kid] += 1;
+  if (!p.on) {
+    CK(launch());
+    return SBCI_OK;
+  }
+  if (p.used + 2 > 8192) RET(prof_flush(c));
+  while (p.pool.size() < p.used + 2) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    p.pool.push_back(e);
+  }
+  CK(cudaEventRecord(p.pool[p.used], c->stream));
+  CK(launch());
+  CK(cudaEventRecord(p.pool[p.used + 1], c->stream));
+  p.used += 2;
+  p.kid.push_back(kid);
+  return SBCI_OK;
+}
+
+// sigma of one device vector, optional epilogue dots against u[0..2].
+sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, const double *u0,
+                      const double *u1, const double *u2) {
+  if (prec != SBCI_FP64 && prec != SBCI_FP32) {
+    set_error("precision mode not available in this build");
+    return SBCI_ERR_INVALID;
+  }
+  RET(ensure_G(c, prec));
+  SigmaArgs a{};
+  a.c = in;
+  a.sigma = out;
+  a.G = c->d_G;
+  a.link_a = c->d_link_a;
+  a.link_b = c->d_link_b;
+  a.W = c->d_W;
+  a.Wf = c->d_Wf;
+  a.na = c->Na;
+  a.nb = c->Nb;
+  a.nlink_a = c->sa.nlink;
+  a.nlink_b = c->sb.nlink;
+  a.npair = c->npair;
+  a.npair_pad = c->npair_pad;
+  a.ndet = c->ndet;
+  a.dot_u[0] = u0;
+  a.dot_u[1] = u1;
+  a.dot_u[2] = u2;
+  a.dot_slot[0] = S_HXZ;
+  a.dot_slot[1] = S_HYZ;
+  a.dot_slot[2] = S_HZZ;
+  a.partials = c->d_partials;
+  a.grid = c->grid;
+  const int p32 = (prec == SBCI_FP64) ? 0 : 1;
+  RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
+  RET(timed(c, K_SC, [&] { return launch_scatter(a, p32, c->stream); }));
+  return SBCI_OK;
+}
+
+sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
+  RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, c->grid, s0, s1, c->d_result, c->stream); }));
+  CK(cudaMemcpyAsync(c->h_result + s0, c->d_result + s0, sizeof(double) * (s1 - s0),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = s0; i < s1; ++i)
+    if (!std::isfinite(c->h_result[i])) {
+      set_error("non-finite dot product in a device reduction");
+      return SBCI_ERR_NUMERIC;
+    }
+  return SBCI_OK;
+}
+
+// dots over up to 16 pairs, results in h_result[S_GEN0 + i]
+sbci_status gen_dots(sbci_ctx *c, std::vector<const double *> u, std::vector<const double *> v) {
+  RET(timed(c, K_DOTS, [&] {
+    return launch_dots(u.data(), v.data(), (int)u.size(), c->ndet, c->d_partials, c->grid, c->stream);
+  }));
+  return reduce_and_fetch(c, S_GEN0, S_GEN0 + (int)u.size());
+}
+
+sbci_status lincomb(sbci_ctx *c, double *out, std::vector<const double *> in, std::vector<double> co) {
+  RET(timed(c, K_LIN, [&] { return launch_lincomb(out, in.data(), co.data(), (int)in.size(), c->ndet, c->stream); }));
+  return SBCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SBCI1 controller
+
+double Epre_of(const sbci_ctx *c) {
+  const Solver &s = c->s;
+  return s.alpha == 0 ? s.E : s.Ec[0];  // newest ground-state Rayleigh quotient (Eqs. 6-7)
+}
+
+// update sweep with the given parameters, then projection and sigma of the
+// next z, reductions and one synchronisation.  E is E_{t+1}, Epre the shift
+// of the preconditioner.
+sbci_status advance(sbci_ctx *c, double sx, double sy, double b, double cc, double E, double kinv,
+                    double Epre) {
+  Solver &s = c->s;
+  const int nxt = s.cur ^ 1;
+  UpdateArgs u{};
+  u.x = s.x;
+  u.X = s.X;
+  u.y = s.y;
+  u.Y = s.Y;
+  u.z = s.z[s.cur];
+  u.Z = s.Z[s.cur];
+  u.w = s.proj ? s.w : s.z[nxt];
+  u.diag = c->d_diag;
+  u.n = c->ndet;
+  u.sx = sx;
+  u.sy = sy;
+  u.b = b;
+  u.c = cc;
+  u.E = E;
+  u.kinv = kinv;
+  u.Epre = Epre;
+  u.guard = s.p.guard;
+  u.w_is_z = s.proj ? 0 : 1;
+  u.nxc = s.proj ? s.alpha : 0;
+  for (int i = 0; i < u.nxc; ++i) u.xc[i] = s.xc + (size_t)i * c->ndet;
+  u.partials = c->d_partials;
+  u.grid = c->grid;
+  RET(timed(c, K_UPD, [&] { return launch_update(u, c->stream); }));
+  if (s.proj) {
+    if (u.nxc > 0)
+      RET(timed(c, K_RED, [&] {
+        return launch_reduce(c->d_partials, c->grid, S_XCW0, S_XCW0 + u.nxc, c->d_result, c->stream);
+      }));
+    ProjectArgs pa{};
+    pa.w = s.w;
+    pa.z = s.z[nxt];
+    pa.x = s.x;
+    pa.y = s.y;
+    pa.nxc = u.nxc;
+    for (int i = 0; i < pa.nxc; ++i) pa.xc[i] = u.xc[i];
+    pa.coef = c->d_result + S_XCW0;
+    pa.sector = s.p.sector;
+    pa.na = c->Na;
+    pa.nb = c->Nb;
+    pa.n = c->ndet;
+    pa.partials = c->d_partials;
+    pa.grid = c->grid;
+    RET(timed(c, K_PROJ, [&] { return launch_project(pa, c->stream); }));
+  }
+  s.cur = nxt;
+  RET(run_sigma(c, s.z[nxt], s.Z[nxt], s.prec, s.x, s.y, s.z[nxt]));
+  return reduce_and_fetch(c, 0, S_XCW0);
+}
+
+// Begin state alpha from x, X (normalised, orthogonal to the stored states) and E.
+sbci_status start_state(sbci_ctx *c) {
+  Solver &s = c->s;
+  s.proj = (s.alpha > 0) || (s.p.sector != 0);
+  s.t = 0;
+  s.first = true;
+  s.sx_pending = 1.0;
+  // residual z'_0 = X_0 - E_0 x_0 and w = M^-1 z'_0: an update with b = c = 0, y = 0
+  return advance(c, 1.0, 0.0, 0.0, 0.0, s.E, 1.0, Epre_of(c));
+}
+
+struct StepOut {
+  double E, b, c, k;
+  double r[3];  // second Ritz vector on (x_new, y_new, z_t)
+  double E2;
+  double sx, sy;
+};
+
+// First-step path (Eqs. S10-S24) on x_0 = sx * x (|x_0| = 1).
+void first_step(const Solver &s, StepOut &o) {
+  const double *d = s.dots;
+  const double sx = s.sx_pending;
+  const double Hxx = sx * sx * d[S_HXX];
+  const double Nxz = sx * d[S_NXZ], Hxz = sx * d[S_HXZ];
+  const double Nzz = d[S_NZZ], Hzz = d[S_HZZ];
+  o.sx = sx;
+  o.sy = 0.0;
+  o.b = 1.0;
+  const double g = Nzz - Nxz * Nxz;
+  if (!(g > 0.0) || g < s.p.gs_tol * Nzz) {  // z inside span{x}: no move
+    o.E = Hxx;
+    o.c = 0.0;
+    o.k = 1.0;
+    o.E2 = Hxx;
+    o.r[0] = 0.0;
+    o.r[1] = 0.0;
+    o.r[2] = 0.0;
+    return;
+  }
+  const double Bz = 1.0 / std::sqrt(g);  // S12
+  const double Bx = -Nxz * Bz;           // S13
+  double V[4], w[2], U[4];
+  V[0] = Hxx;
+  V[1] = V[2] = Bx * Hxx + Bz * Hxz;
+  V[3] = Bx * Bx * Hxx + Bz * Bz * Hzz + 2.0 * Bx * Bz * Hxz;
+  jacobi_eigh(2, V, w, U);
+  const double vx = U[0], vz = U[2];
+  o.E = w[0];
+  o.k = 1.0 / (vx + vz * Bx);            // S23
+  o.c = -vz * Bz / (vx + vz * Bx);       // S24
+  const double wx = U[1], wz = U[3];
+  const double A = wx + wz * Bx;         // coefficient on x_0 = x_new - y_new
+  o.r[0] = A;
+  o.r[1] = -A;
+  o.r[2] = wz * Bz;
+  o.E2 = w[1];
+}
+
+// Later-step path (Eqs. S33-S55).
+void later_step(const Solver &s, StepOut &o) {
+  const double *d = s.dots;
+  const double Nxx = d[S_NXX], Nxy = d[S_NXY], Nxz = d[S_NXZ];
+  const double Nyy = d[S_NYY], Nyz = d[S_NYZ], Nzz = d[S_NZZ];
+  const double Hxx = d[S_HXX], Hxy = d[S_HXY], Hxz = d[S_HXZ];
+  const double Hyy = d[S_HYY], Hyz = d[S_HYZ], Hzz = d[S_HZZ];
+  o.sx = 1.0;
+  o.sy = 1.0;
+  const double Ax = 1.0 / std::sqrt(Nxx);             // S34
+  const double By = 1.0 / std::sqrt(Nyy - Nxy * Nxy / Nxx);  // S36
+  const double Bx = -Nxy / Nxx * By;                   // S37
+  const double P = Bx * Nxz + By * Nyz;                // S42
+  const double gz = Nzz - Nxz * Nxz / Nxx - P * P;
+  if (!(gz > 0.0) || gz < s.p.gs_tol * Nzz) {          // z inside span{x, y}: c = 0
+    double V[4], w[2], U[4];
+    V[0] = Ax * Ax * Hxx;
+    V[1] = V[2] = Ax * (Bx * Hxx + By * Hxy);
+    V[3] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;
+    jacobi_eigh(2, V, w, U);
+    const double vx = U[0], vy = U[2];
+    o.k = 1.0 / (vx * Ax + vy * Bx);
+    o.b = vy * By * o.k;
+    o.c = 0.0;
+    o.E = w[0];
+    const double wx = U[1], wy = U[3];
+    const double cx = wx * Ax + wy * Bx, cy = wy * By;
+    o.r[0] = cx;
+    o.r[1] = cy - cx * o.b;
+    o.r[2] = 0.0;
+    o.E2 = w[1];
+    return;
+  }
+  const double Cz = 1.0 / std::sqrt(gz);               // S39
+  const double Cy = -P * By * Cz;                      // S40
+  const double Cx = -(Nxz / Nxx + P * Bx) * Cz;        // S41
+  const double hx = Cx * Hxx + Cy * Hxy + Cz * Hxz;
+  const double hy = Cx * Hxy + Cy * Hyy + Cz * Hyz;
+  double V[9], w[3], U[9];
+  V[0] = Ax * Ax * Hxx;                                        // S44a
+  V[1] = V[3] = Ax * (Bx * Hxx + By * Hxy);                    // S44b
+  V[2] = V[6] = Ax * hx;                                       // S44c
+  V[4] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;  // S44d
+  V[5] = V[7] = Bx * hx + By * hy;                             // S44e
+  V[8] = Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz + 2.0 * Cx * Cy * Hxy +
+         2.0 * Cx * Cz * Hxz + 2.0 * Cy * Cz * Hyz;            // S44f
+  jacobi_eigh(3, V, w, U);
+  const double vx = U[0], vy = U[3], vz = U[6];
+  const double den = vx * Ax + vy * Bx + vz * Cx;
+  o.E = w[0];
+  o.k = 1.0 / den;                                     // S53
+  o.b = (vy * By + vz * Cy) / den;                     // S54
+  o.c = -vz * Cz / (vy * By + vz * Cy);                // S55
+  const double wx = U[1], wy = U[4], wz = U[7];
+  const double cx = wx * Ax + wy * Bx + wz * Cx, cy = wy * By + wz * Cy, cz = wz * Cz;
+  // pre-update vectors: y_t = y_new + c z_t, x_t = x_new - b y_new
+  o.r[0] = cx;
+  o.r[1] = cy - cx * o.b;
+  o.r[2] = cy * o.c + cz;
+  o.E2 = w[1];
+}
+
+sbci_status finalize_state(sbci_ctx *c, bool converged, const StepOut *o) {
+  Solver &s = c->s;
+  const double nx = std::sqrt(s.dots[S_NXX]);
+  double *xca = s.xc + (size_t)s.alpha * c->ndet;
+  RET(lincomb(c, xca, {s.x}, {1.0 / nx}));
+  s.Ec.push_back(s.E);
+  sbci_report &r = s.rep[s.alpha];
+  r.energy = s.E + c->e_core;
+  r.residual = std::sqrt(s.dots[S_ZPZP]);
+  r.converged = converged ? 1 : 0;
+  if (!converged) s.any_unconverged = 1;
+  if (s.alpha + 1 >= s.k) {
+    s.done = true;
+    return SBCI_OK;
+  }
+  // next state's start: second Ritz vector of the last subspace (S1.4)
+  const int prev = s.cur ^ 1;  // z_t, Z_t of the step that ended the state
+  RET(lincomb(c, s.x, {s.x, s.y, s.z[prev]}, {o->r[0], o->r[1], o->r[2]}));
+  RET(lincomb(c, s.X, {s.X, s.Y, s.Z[prev]}, {o->r[0], o->r[1], o->r[2]}));
+  // Eqs. S4-S7: project against every stored state, X via H x_c = E_c x_c
+  std::vector<const double *> u, v;
+  for (int i = 0; i <= s.alpha; ++i) {
+    u.push_back(s.xc + (size_t)i * c->ndet);
+    v.push_back(s.x);
+  }
+  RET(gen_dots(c, u, v));
+  std::vector<double> ov(s.alpha + 1);
+  for (int i = 0; i <= s.alpha; ++i) ov[i] = c->h_result[S_GEN0 + i];
+  for (int i = 0; i <= s.alpha; ++i) {
+    const double *xci = s.xc + (size_t)i * c->ndet;
+    RET(lincomb(c, s.x, {s.x, xci}, {1.0, -ov[i]}));
+    RET(lincomb(c, s.X, {s.X, xci}, {1.0, -s.Ec[i] * ov[i]}));
+  }
+  RET(gen_dots(c, {s.x}, {s.x}));
+  const double nrm = std::sqrt(c->h_result[S_GEN0]);
+  if (!(nrm > 0.0)) {
+    set_error("excited-state start vector vanished after projection");
+    return SBCI_ERR_NUMERIC;
+  }
+  RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
+  RET(lincomb(c, s.X, {s.X}, {1.0 / nrm}));
+  s.E = o->E2;
+  s.alpha += 1;
+  return start_state(c);
+}
+
+void free_solver(sbci_ctx *c) {
+  Solver &s = c->s;
+  double **ptrs[] = {&s.x, &s.X, &s.y, &s.Y, &s.w, &s.z[0], &s.z[1], &s.Z[0], &s.Z[1], &s.xc};
+  for (double **p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  s.active = false;
+}
+
+sbci_status alloc_solver(sbci_ctx *c, int k) {
+  Solver &s = c->s;
+  free_solver(c);
+  double **ptrs[] = {&s.x, &s.X, &s.y, &s.Y, &s.w, &s.z[0], &s.z[1], &s.Z[0], &s.Z[1]};
+  for (double **p : ptrs) {
+    RET(dmalloc(p, (size_t)c->ndet));
+    CK(cudaMemsetAsync(*p, 0, sizeof(double) * c->ndet, c->stream));
+  }
+  RET(dmalloc(&s.xc, (size_t)k * c->ndet));
+  CK(cudaMemsetAsync(s.xc, 0, sizeof(double) * (size_t)k * c->ndet, c->stream));
+  return SBCI_OK;
+}
+
+// S1.1: lowest-diagonal determinants -> GS -> H in the subspace -> x_0, X_0, E_0.
+sbci_status initial_guess(sbci_ctx *c, int k) {
+  Solver &s = c->s;
+  const int n_init = s.p.n_init > 0 ? s.p.n_init : std::max(k, 2);
+  std::vector<double> D(c->ndet);
+  CK(cudaMemcpyAsync(D.data(), c->d_diag, sizeof(double) * c->ndet, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // n_init smallest (D_I, I) with a bounded max-heap
+  typedef std::pair<double, long long> Key;
+  std::priority_queue<Key> heap;
+  for (long long i = 0; i < c->ndet; ++i) {
+    Key kk(D[i], i);
+    if ((int)heap.size() < n_init) heap.push(kk);
+    else if (kk < heap.top()) {
+      heap.pop();
+      heap.push(kk);
+    }
+  }
+  std::vector<Key> sel;
+  while (!heap.empty()) {
+    sel.push_back(heap.top());
+    heap.pop();
+  }
+  std::sort(sel.begin(), sel.end());
+  // sparse basis vectors with Gram-Schmidt (S1.1)
+  typedef std::map<long long, double> Sparse;
+  std::vector<Sparse> basis;
+  for (const Key &kk : sel) {
+    Sparse e;
+    const long long I = kk.second;
+    if (s.p.sector) {
+      const long long ia = I / c->Nb, ib = I % c->Nb, T = ib * c->Nb + ia;
+      e[I] += 0.5;
+      e[T] += 0.5;
+    } else {
+      e[I] = 1.0;
+    }
+    for (const Sparse &b : basis) {
+      double ov = 0.0;
+      for (auto &kv : e) {
+        auto it = b.find(kv.first);
+        if (it != b.end()) ov += it->second * kv.second;
+      }
+      for (auto &kv : b) e[kv.first] -= ov * kv.second;
+    }
+    double nrm = 0.0;
+    for (auto &kv : e) nrm += kv.second * kv.second;
+    nrm = std::sqrt(nrm);
+    if (nrm < s.p.gs_tol) continue;
+    for (auto &kv : e) kv.second /= nrm;
+    basis.push_back(e);
+  }
+  const int m = (int)basis.size();
+  if (m == 0 || m > 8) {
+    set_error("initial guess: unsupported subspace size");
+    return SBCI_ERR_INVALID;
+  }
+  // X_{-1}^i = H x_{-1}^i (Eq. S1); X buffers: use xc storage rows as scratch when k >= m,
+  // otherwise a temporary allocation.
+  double *tmp = nullptr;
+  RET(dmalloc(&tmp, (size_t)m * c->ndet));
+  std::vector<double> A(m * m);
+  for (int i = 0; i < m; ++i) {
+    CK(cudaMemsetAsync(s.w, 0, sizeof(double) * c->ndet, c->stream));
+    for (auto &kv : basis[i])
+      CK(cudaMemcpyAsync(s.w + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, SBCI_FP64, nullptr, nullptr, nullptr));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double a = 0.0;
+      for (auto &kv : basis[i]) {
+        double v;
+        CK(cudaMemcpy(&v, tmp + (size_t)j * c->ndet + kv.first, sizeof(double), cudaMemcpyDeviceToHost));
+        a += kv.second * v;
+      }
+      A[i * m + j] = a;
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < i; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);
+  std::vector<double> w(m), U(m * m);
+  jacobi_eigh(m, A.data(), w.data(), U.data());
+  // x_0 = sum_i U[i,0] x_{-1}^i (Eq. S2), X_0 = sum_i U[i,0] X_{-1}^i (Eq. S3)
+  Sparse x0;
+  for (int i = 0; i < m; ++i)
+    for (auto &kv : basis[i]) x0[kv.first] += U[i * m] * kv.second;
+  CK(cudaMemsetAsync(s.x, 0, sizeof(double) * c->ndet, c->stream));
+  for (auto &kv : x0)
+    CK(cudaMemcpyAsync(s.x + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  std::vector<const double *> in;
+  std::vector<double> co;
+  for (int i = 0; i < m; ++i) {
+    in.push_back(tmp + (size_t)i * c->ndet);
+    co.push_back(U[i * m]);
+  }
+  RET(lincomb(c, s.X, in, co));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaFree(tmp));
+  s.E = w[0];
+  return SBCI_OK;
+}
+
+sbci_status init_from_vector(sbci_ctx *c, const double *c0) {
+  Solver &s = c->s;
+  std::vector<double> v(c0, c0 + c->ndet);
+  RET(check_finite(v.data(), v.size(), "c0"));
+  if (s.p.sector) {
+    for (int a = 0; a < c->Na; ++a)
+      for (int b = a + 1; b < c->Nb; ++b) {
+        const double m = 0.5 * (v[(size_t)a * c->Nb + b] + v[(size_t)b * c->Nb + a]);
+        v[(size_t)a * c->Nb + b] = m;
+        v[(size_t)b * c->Nb + a] = m;
+      }
+  }
+  CK(cudaMemcpyAsync(s.x, v.data(), sizeof(double) * c->ndet, cudaMemcpyHostToDevice, c->stream));
+  RET(gen_dots(c, {s.x}, {s.x}));
+  const double nrm = std::sqrt(c->h_result[S_GEN0]);
+  if (!(nrm > 0.0)) {
+    set_error("c0 is zero");
+    return SBCI_ERR_INVALID;
+  }
+  RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(gen_dots(c, {s.x}, {s.X}));
+  s.E = c->h_result[S_GEN0];
+  return SBCI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *sbci_last_error(void) { return g_err.c_str(); }
+
+sbci_status sbci_params_init(sbci_params *p) {
+  if (!p) {
+    set_error("sbci_params_init: NULL");
+    return SBCI_ERR_INVALID;
+  }
+  p->eps0 = 1e-10;
+  p->r0 = 1e-5;
+  p->b_th = 1e-2;
+  p->eps1 = 1e-7;
+  p->x_th1 = 0.1;
+  p->x_th2 = 1.2;
+  p->r1 = 1.0;
+  p->max_cycle = 20;
+  p->max_sigma = 1000;
+  p->guard = 1e-8;
+  p->gs_tol = 1e-14;
+  p->sector = 0;
+  p->n_init = 0;
+  p->init = 0;
+  p->prec = SBCI_FP64;
+  p->mixed_eps = 1e-8;
+  p->mixed_r = 1e-4;
+  p->refine_max_sigma = 30;
+  return SBCI_OK;
+}
+
+void sbci_destroy(sbci_ctx *c) {
+  if (!c) return;
+  free_solver(c);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  void *ptrs[] = {c->d_link_a, c->d_mask_b, c->d_W, c->d_Wf, c->d_diag, c->d_ea, c->d_eb,
+                  c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in, c->d_tmp_out};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
+  if (c->h_result) cudaFreeHost(c->h_result);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta, const double *h1,
+                                const double *eri, double e_core, void *cuda_stream) {
+  if (!out || !h1 || !eri) {
+    set_error("sbci_init_integrals: NULL argument");
+    return SBCI_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (norb < 1 || norb > kMaxOrb || nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb ||
+      nalpha + nbeta < 1) {
+    set_error("sbci_init_integrals: need 1 <= norb <= 16, 0 <= nalpha, nbeta <= norb, nalpha+nbeta >= 1");
+    return SBCI_ERR_INVALID;
+  }
+  const int n = norb;
+  const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+  RET(check_finite(h1, n2, "h1"));
+  RET(check_finite(eri, n4, "eri"));
+  if (!std::isfinite(e_core)) {
+    set_error("non-finite e_core");
+    return SBCI_ERR_NUMERIC;
+  }
+  // the packed contraction relies on h = h^T and the 8-fold symmetry of (ij|kl)
+  double scale = 0.0;
+  for (size_t i = 0; i < n4; ++i) scale = std::max(scale, std::fabs(eri[i]));
+  for (size_t i = 0; i < n2; ++i) scale = std::max(scale, std::fabs(h1[i]));
+  const double tol = 1e-10 * (scale > 0 ? scale : 1.0);
+  auto E4 = [&](int i, int j, int k, int l) { return eri[(((size_t)i * n + j) * n + k) * n + l]; };
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (std::fabs(h1[i * n + j] - h1[j * n + i]) > tol) {
+        set_error("h1 is not symmetric");
+        return SBCI_ERR_INVALID;
+      }
+      for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) {
+          const double v = E4(i, j, k, l);
+          if (std::fabs(v - E4(j, i, k, l)) > tol || std::fabs(v - E4(i, j, l, k)) > tol ||
+              std::fabs(v - E4(k, l, i, j)) > tol) {
+            set_error("eri lacks the 8-fold symmetry of real-orbital (ij|kl)");
+            return SBCI_ERR_INVALID;
+          }
+        }
+    }
+  sbci_ctx *c = new sbci_ctx();
+  c->n = n;
+  c->ne_a = nalpha;
+  c->ne_b = nbeta;
+  c->e_core = e_core;
+  build_strings(n, nalpha, c->sa);
+  build_strings(n, nbeta, c->sb);
+  c->Na = c->sa.nstr;
+  c->Nb = c->sb.nstr;
+  c->ndet = (long long)c->Na * c->Nb;
+  c->npair = n * (n + 1) / 2;
+  c->npair_pad = (c->npair + 7) / 8 * 8;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+      delete c;
+      return SBCI_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  int dev = 0, nsm = 0;
+  sbci_status st = SBCI_OK;
+#define TRY(x)                  \
+  do {                          \
+    st = (x);                   \
+    if (st != SBCI_OK) {        \
+      sbci_destroy(c);          \
+      return st;                \
+    }                           \
+  } while (0)
+  auto cuda_ok = [&](cudaError_t e, const char *what) -> sbci_status {
+    if (e == cudaSuccess) return SBCI_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SBCI_ERR_NOMEM : SBCI_ERR_CUDA;
+  };
+  TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
+  TRY(cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"));
+  c->grid = 4 * std::max(nsm, 1);
+  // packed operator W[P][Q], P = (i>=j), Q = (k>=l):
+  //   W = 1/2 (ij|kl) + (k_ij d_kl + d_ij k_kl) / (2N),  k_ij = h_ij - 1/2 sum_m (im|mj)
+  const int N = nalpha + nbeta;
+  std::vector<double> kmat(n2);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = h1[i * n + j];
+      for (int m = 0; m < n; ++m) s -= 0.5 * E4(i, m, m, j);
+      kmat[i * n + j] = s;
+    }
+  c->W_host.assign((size_t)c->npair_pad * c->npair, 0.0);
+  for (int i = 0, P = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j, ++P)
+      for (int k = 0, Q = 0; k < n; ++k)
+        for (int l = 0; l <= k; ++l, ++Q) {
+          double v = 0.5 * E4(i, j, k, l);
+          if (k == l) v += kmat[i * n + j] / (2.0 * N);
+          if (i == j) v += kmat[k * n + l] / (2.0 * N);
+          c->W_host[(size_t)P * c->npair + Q] = v;
+        }
+  std::vector<float> Wf(c->W_host.begin(), c->W_host.end());
+  // per-string diagonal pieces
+  std::vector<double> ea(c->Na), eb(c->Nb), ja((size_t)c->Na * n);
+  auto string_energy = [&](uint32_t m) {
+    double e = 0.0;
+    for (int p = 0; p < n; ++p) {
+      if (!(m >> p & 1u)) continue;
+      e += h1[p * n + p];
+      for (int q = 0; q < n; ++q)
+        if (m >> q & 1u) e += 0.5 * (E4(p, p, q, q) - E4(p, q, q, p));
+    }
+    return e;
+  };
+  for (int a = 0; a < c->Na; ++a) {
+    ea[a] = string_energy(c->sa.masks[a]);
+    for (int q = 0; q < n; ++q) {
+      double s = 0.0;
+      for (int p = 0; p < n; ++p)
+        if (c->sa.masks[a] >> p & 1u) s += E4(p, p, q, q);
+      ja[(size_t)a * n + q] = s;
+    }
+  }
+  for (int b = 0; b < c->Nb; ++b) eb[b] = string_energy(c->sb.masks[b]);
+  // device uploads
+  auto up = [&](void **dst, const void *src, size_t bytes) -> sbci_status {
+    sbci_status r = cuda_ok(cudaMalloc(dst, bytes ? bytes : 1), "cudaMalloc");
+    if (r != SBCI_OK) return r;
+    return cuda_ok(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream), "H2D");
+  };
+  TRY(up((void **)&c->d_link_a, c->sa.links.data(), c->sa.links.size() * 4));
+  if (nbeta == nalpha) c->d_link_b = c->d_link_a;
+  else TRY(up((void **)&c->d_link_b, c->sb.links.data(), c->sb.links.size() * 4));
+  TRY(up((void **)&c->d_mask_b, c->sb.masks.data(), c->sb.masks.size() * 4));
+  TRY(up((void **)&c->d_W, c->W_host.data(), c->W_host.size() * 8));
+  TRY(up((void **)&c->d_Wf, Wf.data(), Wf.size() * 4));
+  TRY(up((void **)&c->d_ea, ea.data(), ea.size() * 8));
+  TRY(up((void **)&c->d_eb, eb.data(), eb.size() * 8));
+  TRY(up((void **)&c->d_ja, ja.data(), ja.size() * 8));
+  TRY(cuda_ok(cudaMalloc((void **)&c->d_diag, sizeof(double) * c->ndet), "cudaMalloc diag"));
+  TRY(cuda_ok(cudaMalloc((void **)&c->d_partials, sizeof(double) * S_COUNT * c->grid), "cudaMalloc"));
+  TRY(cuda_ok(cudaMemsetAsync(c->d_partials, 0, sizeof(double) * S_COUNT * c->grid, c->stream), "memset"));
+  TRY(cuda_ok(cudaMalloc((void **)&c->d_result, sizeof(double) * S_COUNT), "cudaMalloc"));
+  TRY(cuda_ok(cudaMallocHost((void **)&c->h_result, sizeof(double) * S_COUNT), "cudaMallocHost"));
+  TRY(cuda_ok(launch_diagonal(c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_mask_b, c->Na, c->Nb, n,
+                              c->stream), "diagonal kernel"));
+  TRY(cuda_ok(cudaStreamSynchronize(c->stream), "sync"));
+#undef TRY
+  *out = c;
+  return SBCI_OK;
+}
+
+sbci_status sbci_dims(const sbci_ctx *c, long long *ndet, int *na, int *nb, int *nlink_a,
+                      int *nlink_b, int *npair) {
+  if (!c) {
+    set_error("sbci_dims: NULL context");
+    return SBCI_ERR_INVALID;
+  }
+  if (ndet) *ndet = c->ndet;
+  if (na) *na = c->Na;
+  if (nb) *nb = c->Nb;
+  if (nlink_a) *nlink_a = c->sa.nlink;
+  if (nlink_b) *nlink_b = c->sb.nlink;
+  if (npair) *npair = c->npair;
+  return SBCI_OK;
+}
+
+sbci_status sbci_string_table(const sbci_ctx *c, int spin, int *out) {
+  if (!c || !out || (spin != 0 && spin != 1)) {
+    set_error("sbci_string_table: bad argument");
+    return SBCI_ERR_INVALID;
+  }
+  const StringSet &S = spin == 0 ? c->sa : c->sb;
+  std::vector<uint32_t> buf((size_t)S.nstr * S.nlink);
+  CK(cudaMemcpy(buf.data(), spin == 0 ? c->d_link_a : c->d_link_b, buf.size() * 4,
+                cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < buf.size(); ++i) {
+    out[3 * i + 0] = link_pair(buf[i]);
+    out[3 * i + 1] = link_J(buf[i]);
+    out[3 * i + 2] = link_neg(buf[i]) ? -1 : 1;
+  }
+  return SBCI_OK;
+}
+
+sbci_status sbci_diagonal(sbci_ctx *c, double *out, int on_device) {
+  if (!c || !out) {
+    set_error("sbci_diagonal: NULL argument");
+    return SBCI_ERR_INVALID;
+  }
+  CK(cudaMemcpyAsync(out, c->d_diag, sizeof(double) * c->ndet,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SBCI_OK;
+}
+
+sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int prec, int on_device) {
+  if (!c || !in || !out || nvec < 0) {
+    set_error("sbci_sigma: bad argument");
+    return SBCI_ERR_INVALID;
+  }
+  if (prec != SBCI_FP64 && prec != SBCI_FP32 && prec != SBCI_TF32X3 && prec != SBCI_BF16X3) {
+    set_error("sbci_sigma: unknown precision");
+    return SBCI_ERR_INVALID;
+  }
+  const size_t n = (size_t)c->ndet;
+  if (!on_device) {
+    RET(check_finite(in, n * nvec, "c"));
+    if (c->tmp_elems < n) {
+      if (c->d_tmp_in) cudaFree(c->d_tmp_in);
+      if (c->d_tmp_out) cudaFree(c->d_tmp_out);
+      c->d_tmp_in = c->d_tmp_out = nullptr;
+      c->tmp_elems = 0;
+      RET(dmalloc(&c->d_tmp_in, n));
+      RET(dmalloc(&c->d_tmp_out, n));
+      c->tmp_elems = n;
+    }
+  }
+  for (int v = 0; v < nvec; ++v) {
+    const double *src = in + v * n;
+    double *dst = out + v * n;
+    if (!on_device) {
+      CK(cudaMemcpyAsync(c->d_tmp_in, src, n * 8, cudaMemcpyHostToDevice, c->stream));
+      RET(run_sigma(c, c->d_tmp_in, c->d_tmp_out, prec, nullptr, nullptr, nullptr));
+      CK(cudaMemcpyAsync(dst, c->d_tmp_out, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      RET(run_sigma(c, src, dst, prec, nullptr, nullptr, nullptr));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return SBCI_OK;
+}
+
+sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const double *c0) {
+  if (!c || k < 1 || k > kMaxStates) {
+    set_error("sbci_begin: need a context and 1 <= k <= 8");
+    return SBCI_ERR_INVALID;
+  }
+  Solver &s = c->s;
+  if (params) s.p = *params;
+  else sbci_params_init(&s.p);
+  if (s.p.sector && c->ne_a != c->ne_b) {
+    set_error("sector = 1 needs nalpha == nbeta");
+    return SBCI_ERR_INVALID;
+  }
+  if (s.p.init == 1 && !c0) {
+    set_error("init = 1 needs c0");
+    return SBCI_ERR_INVALID;
+  }
+  if (s.p.prec != SBCI_FP64 && s.p.prec != SBCI_FP32) {
+    set_error("sbci_begin: precision mode not available in this build");
+    return SBCI_ERR_INVALID;
+  }
+  if ((long long)k > c->ndet) {
+    set_error("sbci_begin: more states than determinants");
+    return SBCI_ERR_INVALID;
+  }
+  RET(alloc_solver(c, k));
+  s.k = k;
+  s.alpha = 0;
+  s.done = false;
+  s.cur = 0;
+  s.prec = s.p.prec;
+  s.Ec.clear();
+  s.trace.clear();
+  s.rep.assign(k, sbci_report{});
+  s.any_unconverged = 0;
+  s.active = true;
+  if (s.p.init == 1) RET(init_from_vector(c, c0));
+  else RET(initial_guess(c, k));
+  return start_state(c);
+}
+
+sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
+  if (!c || !c->s.active) {
+    set_error("sbci_step: no active solve (call sbci_begin)");
+    return SBCI_ERR_INVALID;
+  }
+  Solver &s = c->s;
+  if (done) *done = s.done ? 1 : 0;
+  if (s.done) return SBCI_OK;
+  std::memcpy(s.dots, c->h_result, sizeof(s.dots));
+  sbci_report &r = s.rep[s.alpha];
+  StepOut o{};
+  if (s.first) first_step(s, o);
+  else later_step(s, o);
+  if (!std::isfinite(o.E) || !std::isfinite(o.k) || !std::isfinite(o.b) || !std::isfinite(o.c)) {
+    set_error("non-finite SB parameters");
+    return SBCI_ERR_NUMERIC;
+  }
+  const double Eold = s.E;
+  const int t_now = s.t;
+  r.n_sigma += 1;
+  if (s.prec == SBCI_FP64) r.n_sigma_fp64 += 1;
+  r.n_step += 1;
+  s.E = o.E;
+  RET(advance(c, o.sx, o.sy, o.b, o.c, o.E, 1.0 / o.k, Epre_of(c)));
+  s.first = false;
+  std::memcpy(s.dots, c->h_result, sizeof(s.dots));
+  const double dz = std::sqrt(s.dots[S_ZPZP]);
+  const double dE = std::fabs(o.E - Eold);
+  sbci_trace_record tr{};
+  tr.state = s.alpha;
+  tr.t = t_now;
+  tr.energy = o.E;
+  tr.b = o.b;
+  tr.c = o.c;
+  tr.k = o.k;
+  tr.dE = dE;
+  tr.dz = dz;
+  tr.prec = s.prec;
+  sbci_status ret = SBCI_OK;
+  if (dE < s.p.eps0 && dz < s.p.r0) {  // Eq. S61
+    tr.event = 1;
+    s.trace.push_back(tr);
+    if (rec) *rec = tr;
+    RET(finalize_state(c, true, &o));
+  } else {
+    int cause = 0;  // S62a, S62b, S62c, max_cycle
+    if (s.alpha > 0 && std::fabs(o.b) < s.p.b_th && dE < s.p.eps1) cause = 1;
+    else if (std::fabs(o.k) < s.p.x_th1 || std::fabs(o.k) > s.p.x_th2) cause = 2;
+    else if (dz > s.p.r1 && t_now > 0) cause = 3;
+    else if (t_now + 1 >= s.p.max_cycle) cause = 4;
+    tr.event = cause ? cause + 1 : 0;
+    s.trace.push_back(tr);
+    if (rec) *rec = tr;
+    if (cause) {
+      r.n_restart[cause - 1] += 1;
+      s.first = true;
+      s.sx_pending = 1.0 / std::sqrt(s.dots[S_NXX]);
+      s.t = 0;
+    } else {
+      s.t += 1;
+      // Gram-Schmidt breakdown of y (y inside span{x}): take the first-step path
+      const double gy = s.dots[S_NYY] - s.dots[S_NXY] * s.dots[S_NXY] / s.dots[S_NXX];
+      if (gy < s.p.gs_tol * s.dots[S_NYY]) {
+        s.first = true;
+        s.sx_pending = 1.0 / std::sqrt(s.dots[S_NXX]);
+        s.t = 0;
+      }
+    }
+    if (r.n_sigma >= s.p.max_sigma) {
+      ret = SBCI_ERR_NOT_CONVERGED;
+      set_error("state reached max_sigma without converging");
+      RET(finalize_state(c, false, &o));
+    }
+  }
+  if (done) *done = s.done ? 1 : 0;
+  return ret;
+}
+
+sbci_status sbci_finish(sbci_ctx *c, double *energies, double *vecs, sbci_report *rep) {
+  if (!c || !c->s.active) {
+    set_error("sbci_finish: no active solve");
+    return SBCI_ERR_INVALID;
+  }
+  Solver &s = c->s;
+  const int nst = (int)s.Ec.size();
+  for (int i = 0; i < nst; ++i) {
+    if (energies) energies[i] = s.Ec[i] + c->e_core;
+    if (rep) rep[i] = s.rep[i];
+  }
+  if (vecs && nst > 0)
+    CK(cudaMemcpyAsync(vecs, s.xc, sizeof(double) * (size_t)nst * c->ndet, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (nst < s.k) {
+    set_error("sbci_finish: solve not finished");
+    return SBCI_ERR_INVALID;
+  }
+  return s.any_unconverged ? SBCI_ERR_NOT_CONVERGED : SBCI_OK;
+}
+
+sbci_status sbci_solve(sbci_ctx *c, int k, const sbci_params *params, const double *c0,
+                       double *energies, double *vecs, sbci_report *rep) {
+  RET(sbci_begin(c, k, params, c0));
+  int done = 0;
+  while (!done) {
+    sbci_status st = sbci_step(c, nullptr, &done);
+    if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
+  }
+  return sbci_finish(c, energies, vecs, rep);
+}
+
+sbci_status sbci_trace(const sbci_ctx *c, sbci_trace_record *buf, int cap, int *n) {
+  if (!c) {
+    set_error("sbci_trace: NULL context");
+    return SBCI_ERR_INVALID;
+  }
+  const int m = (int)c->s.trace.size();
+  if (n) *n = m;
+  if (buf)
+    for (int i = 0; i < m && i < cap; ++i) buf[i] = c->s.trace[i];
+  return SBCI_OK;
+}
+
+sbci_status sbci_profile(sbci_ctx *c, int enable) {
+  if (!c) {
+    set_error("sbci_profile: NULL context");
+    return SBCI_ERR_INVALID;
+  }
+  RET(prof_flush(c));
+  Prof &p = c->prof;
+  for (int i = 0; i < K_COUNT; ++i) {
+    p.launches[i] = 0;
+    p.ms[i] = 0.0;
+  }
+  p.on = enable != 0;
+  return SBCI_OK;
+}
+
+sbci_status sbci_profile_read(sbci_ctx *c, sbci_kernel_stat *out, int cap, int *n) {
+  if (!c) {
+    set_error("sbci_profile_read: NULL context");
+    return SBCI_ERR_INVALID;
+  }
+  RET(prof_flush(c));
+  if (n) *n = K_COUNT;
+  for (int i = 0; i < K_COUNT && out && i < cap; ++i) {
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, kKidName[i], sizeof(out[i].name) - 1);
+    out[i].launches = c->prof.launches[i];
+    out[i].total_ms = c->prof.ms[i];
+  }
+  return SBCI_OK;
+}
+
+}  // extern "C"

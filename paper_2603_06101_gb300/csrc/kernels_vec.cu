@@ -1,0 +1,255 @@
+// FP64 vector kernels of the SBCI1 step: the fused symplectic-Euler update
+// sweep (Eqs. 10-11 with the H-image recurrences S56-S59, the residual S60
+// and the preconditioner of Eqs. 6-7), the projection against the stored
+// states (Eq. S31), the diagonal of H, and deterministic reductions.
+//
+// Every dot product is reduced in two fixed-order stages (block partials,
+// then one pass per slot), so results do not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "sbci_internal.h"
+
+namespace sbci {
+
+constexpr int kVecThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of NV values per thread; thread 0 writes partials.
+template <int NV>
+__device__ __forceinline__ void block_store(double (&v)[NV], const int *slots, double *partials,
+                                            int grid) {
+  __shared__ double red[NV][kVecThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const double s = warp_sum(v[j]);
+    if (lane == 0) red[j][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int j = threadIdx.x;
+    double s = 0.0;
+    for (int i = 0; i < kVecThreads / 32; ++i) s += red[j][i];
+    if (slots[j] >= 0) partials[(size_t)slots[j] * grid + blockIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ double guarded(double d, double g) {
+  if (fabs(d) < g) return d < 0.0 ? -g : g;
+  return d;
+}
+
+// y <- sy*y - c*z ; Y <- sy*Y - c*Z ; x <- sx*x + b*y ; X <- sx*X + b*Y
+// z' = (X - E x) * kinv ; w = z' / guarded(D - Epre)
+// dots: Nxx Nxy Nyy Hxx Hxy Hyy |z'|^2 [Nxw Nyw Nww] [x_c^i . w]
+__global__ void __launch_bounds__(kVecThreads) k_update(UpdateArgs a) {
+  constexpr int NV = 10 + kMaxStates;
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const double zi = a.z[i], Zi = a.Z[i];
+    const double y = a.sy * a.y[i] - a.c * zi;
+    const double Y = a.sy * a.Y[i] - a.c * Zi;
+    const double x = a.sx * a.x[i] + a.b * y;
+    const double X = a.sx * a.X[i] + a.b * Y;
+    a.y[i] = y;
+    a.Y[i] = Y;
+    a.x[i] = x;
+    a.X[i] = X;
+    const double zp = (X - a.E * x) * a.kinv;
+    const double w = zp / guarded(a.diag[i] - a.Epre, a.guard);
+    a.w[i] = w;
+    acc[0] += x * x;
+    acc[1] += x * y;
+    acc[2] += y * y;
+    acc[3] += x * X;
+    acc[4] += x * Y;
+    acc[5] += y * Y;
+    acc[6] += zp * zp;
+    if (a.w_is_z) {
+      acc[7] += x * w;
+      acc[8] += y * w;
+      acc[9] += w * w;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxStates; ++j)
+      if (j < a.nxc) acc[10 + j] += a.xc[j][i] * w;
+  }
+  int slots[NV];
+  for (int j = 0; j < 7; ++j) slots[j] = S_NXX + j;
+  for (int j = 7; j < 10; ++j) slots[j] = a.w_is_z ? (S_NXZ + j - 7) : -1;
+  for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < a.nxc) ? S_XCW0 + j : -1;
+  block_store<NV>(acc, slots, a.partials, a.grid);
+}
+
+// z = sym(w) - sum_i coef_i x_c^i ; dots Nxz Nyz Nzz.
+__global__ void __launch_bounds__(kVecThreads) k_project(ProjectArgs a) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    double v = a.w[i];
+    if (a.sector) {
+      const int ia = (int)(i / a.nb), ib = (int)(i - (long long)ia * a.nb);
+      v = 0.5 * (v + a.w[(size_t)ib * a.nb + ia]);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxStates; ++j)
+      if (j < a.nxc) v -= __ldg(a.coef + j) * a.xc[j][i];
+    a.z[i] = v;
+    acc[0] += a.x[i] * v;
+    acc[1] += a.y[i] * v;
+    acc[2] += v * v;
+  }
+  const int slots[3] = {S_NXZ, S_NYZ, S_NZZ};
+  block_store<3>(acc, slots, a.partials, a.grid);
+}
+
+struct LinComb {
+  const double *in[8];
+  double coef[8];
+  int nin;
+};
+
+__global__ void k_lincomb(double *out, LinComb L, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double s = 0.0;
+    for (int j = 0; j < L.nin; ++j) s += L.coef[j] * L.in[j][i];
+    out[i] = s;
+  }
+}
+
+struct DotList {
+  const double *u[16];
+  const double *v[16];
+  int n;
+};
+
+__global__ void __launch_bounds__(kVecThreads) k_dots(DotList L, long long n, double *partials, int grid) {
+  double acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < L.n) acc[j] += L.u[j][i] * L.v[j][i];
+  }
+  int slots[16];
+  for (int j = 0; j < 16; ++j) slots[j] = (j < L.n) ? S_GEN0 + j : -1;
+  block_store<16>(acc, slots, partials, grid);
+}
+
+__global__ void k_reduce(const double *partials, int grid, int s0, double *result) {
+  __shared__ double red[kVecThreads / 32];
+  const int slot = s0 + blockIdx.x;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < grid; i += blockDim.x) v += partials[(size_t)slot * grid + i];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    result[slot] = s;
+  }
+}
+
+// D_I = ea[Ia] + eb[Ib] + sum_{q in occ(Ib)} ja[Ia][q]
+__global__ void k_diagonal(double *diag, const double *ea, const double *eb, const double *ja,
+                           const uint32_t *mask_b, int na, int nb, int norb) {
+  const long long n = (long long)na * nb;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int ia = (int)(i / nb), ib = (int)(i - (long long)ia * nb);
+    double s = ea[ia] + eb[ib];
+    uint32_t m = mask_b[ib];
+    while (m) {
+      const int q = __ffs(m) - 1;
+      s += ja[(size_t)ia * norb + q];
+      m &= m - 1u;
+    }
+    diag[i] = s;
+  }
+}
+
+__global__ void k_symmetrize(double *v, int n) {
+  const long long total = (long long)n * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int a = (int)(i / n), b = (int)(i - (long long)a * n);
+    if (a < b) {
+      const double s = 0.5 * (v[i] + v[(size_t)b * n + a]);
+      v[i] = s;
+      v[(size_t)b * n + a] = s;
+    }
+  }
+}
+
+static int grid_for(long long n, int cap) {
+  long long g = (n + kVecThreads - 1) / kVecThreads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s) {
+  k_update<<<a.grid, kVecThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s) {
+  k_project<<<a.grid, kVecThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(double *out, const double *const *in, const double *coef, int nin,
+                           long long n, cudaStream_t s) {
+  LinComb L{};
+  L.nin = nin;
+  for (int j = 0; j < nin && j < 8; ++j) {
+    L.in[j] = in[j];
+    L.coef[j] = coef[j];
+  }
+  k_lincomb<<<grid_for(n, 4096), kVecThreads, 0, s>>>(out, L, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots(const double *const *u, const double *const *v, int npairs, long long n,
+                        double *partials, int grid, cudaStream_t s) {
+  DotList L{};
+  L.n = npairs;
+  for (int j = 0; j < npairs && j < 16; ++j) {
+    L.u[j] = u[j];
+    L.v[j] = v[j];
+  }
+  k_dots<<<grid, kVecThreads, 0, s>>>(L, n, partials, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double *partials, int grid, int s0, int s1, double *result,
+                          cudaStream_t s) {
+  if (s1 <= s0) return cudaSuccess;
+  k_reduce<<<s1 - s0, kVecThreads, 0, s>>>(partials, grid, s0, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, const double *ja,
+                            const uint32_t *mask_b, int na, int nb, int norb, cudaStream_t s) {
+  k_diagonal<<<grid_for((long long)na * nb, 8192), kVecThreads, 0, s>>>(diag, ea, eb, ja, mask_b,
+                                                                        na, nb, norb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s) {
+  k_symmetrize<<<grid_for((long long)n * n, 8192), kVecThreads, 0, s>>>(v, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sbci

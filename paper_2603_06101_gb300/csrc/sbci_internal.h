@@ -1,0 +1,124 @@
+// Internal declarations shared by the host C++ and the CUDA translation units
+// of libsbci.  Nothing here is part of the C ABI (see include/sbci.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace sbci {
+
+// ---------------------------------------------------------------------------
+// Packed excitation-table entry.  For string I, entry e encodes
+//   a+_k a_l |I> = sign |J>  as  J | pair(k,l) << 20 | (sign < 0) << 31.
+// J < 2^20 strings, pair < 2^11.
+constexpr uint32_t kJMask = (1u << 20) - 1u;
+constexpr int kPairShift = 20;
+constexpr uint32_t kPairMask = (1u << 11) - 1u;
+constexpr uint32_t kSignBit = 1u << 31;
+
+__host__ __device__ inline int link_J(uint32_t v) { return (int)(v & kJMask); }
+__host__ __device__ inline int link_pair(uint32_t v) { return (int)((v >> kPairShift) & kPairMask); }
+__host__ __device__ inline bool link_neg(uint32_t v) { return (v & kSignBit) != 0u; }
+
+constexpr int kMaxOrb = 16;
+constexpr int kMaxPair = kMaxOrb * (kMaxOrb + 1) / 2;  // 136
+constexpr int kMaxStates = 8;
+
+// Host-side string data of one spin.
+struct StringSet {
+  int norb = 0, nelec = 0, nstr = 0, nlink = 0;
+  std::vector<uint32_t> masks;  // increasing
+  std::vector<uint32_t> links;  // [nstr][nlink]
+};
+void build_strings(int norb, int nelec, StringSet &out);
+
+// ---------------------------------------------------------------------------
+// Dot-product slots of the per-step reduction buffer.
+enum Slot : int {
+  S_NXX = 0, S_NXY, S_NYY, S_HXX, S_HXY, S_HYY, S_ZPZP,   // written by the update sweep
+  S_NXZ, S_NYZ, S_NZZ,                                   // update (no projection) or project
+  S_HXZ, S_HYZ, S_HZZ,                                   // sigma epilogue
+  S_XCW0,                                                // x_c^i . w, i < kMaxStates
+  S_GEN0 = S_XCW0 + kMaxStates,                          // general-purpose dots
+  S_COUNT = S_GEN0 + 16
+};
+
+// Arguments of the sigma kernels for one vector.
+struct SigmaArgs {
+  const double *c;       // [Na*Nb]
+  double *sigma;         // [Na*Nb]
+  void *G;               // [npair][ndet] FP64 or FP32 scratch
+  const uint32_t *link_a, *link_b;
+  const double *W;       // [npair_pad][npair] FP64 (rows padded with zeros)
+  const float *Wf;       // FP32 copy (same layout), SBCI_FP32 mode
+  int na, nb, nlink_a, nlink_b, npair, npair_pad;
+  long long ndet;
+  // epilogue dots of sigma against up to three vectors (nullptr = unused)
+  const double *dot_u[3];
+  int dot_slot[3];
+  double *partials;      // [S_COUNT][grid]
+  int grid;
+};
+
+// Launchers (kernels_sigma.cu)
+// prec: 0 = FP64 scratch and contraction, 1 = FP32 (SIMT) contraction
+cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s);
+cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
+size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
+
+// Vector kernels (kernels_vec.cu)
+struct UpdateArgs {
+  double *x, *X, *y, *Y;
+  const double *z, *Z;
+  double *w;              // out: next preconditioned residual (z' / guarded(D - Epre))
+  const double *diag;
+  long long n;
+  double sx, sy, b, c, E, kinv, Epre, guard;
+  int w_is_z;             // 1: w is used directly as the next z (slots NXZ.. from w)
+  const double *xc[kMaxStates];
+  int nxc;                // number of x_c dots (x_c^i . w) to produce
+  double *partials;
+  int grid;
+};
+cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s);
+
+struct ProjectArgs {
+  const double *w;
+  double *z;
+  const double *x, *y;
+  const double *xc[kMaxStates];
+  const double *coef;     // device [nxc]: z = sym(w) - sum coef_i x_c^i
+  int nxc;
+  int sector;             // 1: symmetrise w over the Ia <-> Ib swap
+  int na, nb;
+  long long n;
+  double *partials;
+  int grid;
+};
+cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
+
+// out = sum_i coef_i in_i (out may alias in[0]); up to 8 inputs.
+cudaError_t launch_lincomb(double *out, const double *const *in, const double *coef, int nin,
+                           long long n, cudaStream_t s);
+// partial dots of up to 16 (u, v) pairs into slots S_GEN0 + i.
+cudaError_t launch_dots(const double *const *u, const double *const *v, int npairs, long long n,
+                        double *partials, int grid, cudaStream_t s);
+// result[slot] = sum of partials[slot][0..grid) in fixed order, slots [s0, s1).
+cudaError_t launch_reduce(const double *partials, int grid, int s0, int s1, double *result,
+                          cudaStream_t s);
+// D_I from per-string energies and ja[Ia][q] = sum_{p in a} (pp|qq).
+cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, const double *ja,
+                            const uint32_t *mask_b, int na, int nb, int norb, cudaStream_t s);
+cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Small dense symmetric eigen-solver (cyclic Jacobi), ascending eigenvalues,
+// eigenvectors in columns of V (row-major n x n).
+void jacobi_eigh(int n, const double *A, double *w, double *V);
+
+void set_error(const std::string &msg);
+
+}  // namespace sbci

@@ -1,0 +1,261 @@
+"""Thin Python binding of the C ABI in include/sbci.h (ctypes, marshalling only).
+
+Every computation runs in libsbci.so; this module converts numpy arrays and
+torch CUDA tensors to pointers and raises on error statuses.  Importing it
+fails loudly when the shared library has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsbci.so")
+
+SBCI_OK = 0
+SBCI_ERR_INVALID = 1
+SBCI_ERR_NOMEM = 2
+SBCI_ERR_CUDA = 3
+SBCI_ERR_NUMERIC = 4
+SBCI_ERR_NOT_CONVERGED = 5
+SBCI_ERR_TIMEOUT = 6
+SBCI_ERR_CANCELLED = 7
+
+SBCI_FP64 = 0
+SBCI_TF32X3 = 1
+SBCI_BF16X3 = 2
+SBCI_FP32 = 3
+
+_STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NUMERIC", 5: "NOT_CONVERGED",
+           6: "TIMEOUT", 7: "CANCELLED"}
+
+
+class SbciError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sbci {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sbci_params(C.Structure):
+    _fields_ = [("eps0", C.c_double), ("r0", C.c_double), ("b_th", C.c_double), ("eps1", C.c_double),
+                ("x_th1", C.c_double), ("x_th2", C.c_double), ("r1", C.c_double),
+                ("max_cycle", C.c_int), ("max_sigma", C.c_int), ("guard", C.c_double),
+                ("gs_tol", C.c_double), ("sector", C.c_int), ("n_init", C.c_int), ("init", C.c_int),
+                ("prec", C.c_int), ("mixed_eps", C.c_double), ("mixed_r", C.c_double),
+                ("refine_max_sigma", C.c_int)]
+
+
+class sbci_report(C.Structure):
+    _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("converged", C.c_int),
+                ("n_sigma", C.c_int), ("n_sigma_fp64", C.c_int), ("n_step", C.c_int),
+                ("n_restart", C.c_int * 4)]
+
+
+class sbci_trace_record(C.Structure):
+    _fields_ = [("state", C.c_int), ("t", C.c_int), ("energy", C.c_double), ("b", C.c_double),
+                ("c", C.c_double), ("k", C.c_double), ("dE", C.c_double), ("dz", C.c_double),
+                ("event", C.c_int), ("prec", C.c_int)]
+
+
+class sbci_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double)]
+
+
+_lib = None
+
+EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_table",
+           "sbci_diagonal", "sbci_sigma", "sbci_begin", "sbci_step", "sbci_finish", "sbci_solve",
+           "sbci_trace", "sbci_profile", "sbci_profile_read", "sbci_last_error", "sbci_destroy"]
+
+
+def load(path: str = LIB_PATH):
+    """Loads libsbci.so and declares the prototypes.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libsbci.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    lib.sbci_params_init.argtypes = [C.POINTER(sbci_params)]
+    lib.sbci_init_integrals.argtypes = [C.POINTER(P), I, I, I, P, P, D, P]
+    lib.sbci_dims.argtypes = [P, C.POINTER(LL), C.POINTER(I), C.POINTER(I), C.POINTER(I),
+                              C.POINTER(I), C.POINTER(I)]
+    lib.sbci_string_table.argtypes = [P, I, P]
+    lib.sbci_diagonal.argtypes = [P, P, I]
+    lib.sbci_sigma.argtypes = [P, P, P, I, I, I]
+    lib.sbci_begin.argtypes = [P, I, C.POINTER(sbci_params), P]
+    lib.sbci_step.argtypes = [P, C.POINTER(sbci_trace_record), C.POINTER(I)]
+    lib.sbci_finish.argtypes = [P, P, P, P]
+    lib.sbci_solve.argtypes = [P, I, C.POINTER(sbci_params), P, P, P, P]
+    lib.sbci_trace.argtypes = [P, C.POINTER(sbci_trace_record), I, C.POINTER(I)]
+    lib.sbci_profile.argtypes = [P, I]
+    lib.sbci_profile_read.argtypes = [P, C.POINTER(sbci_kernel_stat), I, C.POINTER(I)]
+    lib.sbci_last_error.restype = C.c_char_p
+    lib.sbci_last_error.argtypes = []
+    lib.sbci_destroy.argtypes = [P]
+    lib.sbci_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("sbci_last_error", "sbci_destroy"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, allow=()):
+    if st != SBCI_OK and st not in allow:
+        raise SbciError(st, _lib.sbci_last_error().decode())
+    return st
+
+
+def _ptr(a):
+    """Pointer of a C-contiguous float64 numpy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return a.ctypes.data_as(C.c_void_p), False
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        if a.is_cuda:
+            # the library runs on its own stream: make torch's pending work visible
+            import torch
+
+            torch.cuda.current_stream(a.device).synchronize()
+        return C.c_void_p(a.data_ptr()), bool(a.is_cuda)
+    raise TypeError(type(a))
+
+
+def params(**kw) -> sbci_params:
+    lib = load()
+    p = sbci_params()
+    _check(lib.sbci_params_init(C.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One active space on the current CUDA device (owns the device memory)."""
+
+    def __init__(self, norb, nalpha, nbeta, h1, eri, e_core=0.0, stream=None):
+        lib = load()
+        self._lib = lib
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        self._h = C.c_void_p()
+        st = lib.sbci_init_integrals(C.byref(self._h), int(norb), int(nalpha), int(nbeta),
+                                     h1.ctypes.data_as(C.c_void_p), eri.ctypes.data_as(C.c_void_p),
+                                     float(e_core), C.c_void_p(stream) if stream else None)
+        _check(st)
+        nd, na, nb, la, lb, npair = C.c_longlong(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib.sbci_dims(self._h, C.byref(nd), C.byref(na), C.byref(nb), C.byref(la),
+                             C.byref(lb), C.byref(npair)))
+        self.ndet, self.na, self.nb = nd.value, na.value, nb.value
+        self.nlink_a, self.nlink_b, self.npair = la.value, lb.value, npair.value
+        self.norb, self.nalpha, self.nbeta = norb, nalpha, nbeta
+
+    @classmethod
+    def from_integrals(cls, I, stream=None):
+        return cls(I.norb, I.nalpha, I.nbeta, I.h1, I.eri, I.e_core, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.sbci_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -------------------------------------------------------
+    def string_table(self, spin: int) -> np.ndarray:
+        nstr, nl = (self.na, self.nlink_a) if spin == 0 else (self.nb, self.nlink_b)
+        out = np.zeros((nstr, nl, 3), dtype=np.int32)
+        _check(self._lib.sbci_string_table(self._h, spin, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def diagonal(self, out=None):
+        if out is None:
+            out = np.zeros(self.ndet)
+        p, dev = _ptr(out)
+        _check(self._lib.sbci_diagonal(self._h, p, int(dev)))
+        return out
+
+    def sigma(self, c, out=None, prec: int = SBCI_FP64):
+        """sigma = H c for c of shape [..., Na, Nb] (numpy host or torch CUDA)."""
+        if isinstance(c, np.ndarray):
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            if out is None:
+                out = np.zeros_like(c)
+        elif out is None:
+            out = c.new_zeros(c.shape)
+        nvec = int(np.prod(c.shape)) // self.ndet
+        pc, dev = _ptr(c)
+        po, dev2 = _ptr(out)
+        assert dev == dev2, "input and output must both be host or both be device"
+        _check(self._lib.sbci_sigma(self._h, pc, po, nvec, int(prec), int(dev)))
+        return out
+
+    def begin(self, k, p: sbci_params | None = None, c0=None):
+        pc = None
+        if c0 is not None:
+            c0 = np.ascontiguousarray(c0, dtype=np.float64).reshape(-1)
+            self._c0 = c0
+            pc = c0.ctypes.data_as(C.c_void_p)
+        _check(self._lib.sbci_begin(self._h, int(k), C.byref(p) if p is not None else None, pc))
+        self._k = k
+
+    def step(self):
+        rec = sbci_trace_record()
+        done = C.c_int()
+        st = self._lib.sbci_step(self._h, C.byref(rec), C.byref(done))
+        _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
+        return rec, bool(done.value)
+
+    def finish(self, want_vectors=False):
+        k = self._k
+        E = np.zeros(k)
+        V = np.zeros((k, self.ndet)) if want_vectors else None
+        R = (sbci_report * k)()
+        st = self._lib.sbci_finish(self._h, E.ctypes.data_as(C.c_void_p),
+                                   V.ctypes.data_as(C.c_void_p) if V is not None else None, R)
+        _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
+        return E, V, list(R), st
+
+    def solve(self, k, p: sbci_params | None = None, c0=None, want_vectors=False):
+        pc = None
+        if c0 is not None:
+            c0 = np.ascontiguousarray(c0, dtype=np.float64).reshape(-1)
+            pc = c0.ctypes.data_as(C.c_void_p)
+        E = np.zeros(k)
+        V = np.zeros((k, self.ndet)) if want_vectors else None
+        R = (sbci_report * k)()
+        st = self._lib.sbci_solve(self._h, int(k), C.byref(p) if p is not None else None, pc,
+                                  E.ctypes.data_as(C.c_void_p),
+                                  V.ctypes.data_as(C.c_void_p) if V is not None else None, R)
+        _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
+        self._k = k
+        return E, V, list(R), st
+
+    def profile(self, enable: bool = True):
+        """Resets the per-kernel statistics; enable also times every launch."""
+        _check(self._lib.sbci_profile(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        buf = (sbci_kernel_stat * 32)()
+        n = C.c_int()
+        _check(self._lib.sbci_profile_read(self._h, buf, 32, C.byref(n)))
+        return {b.name.decode(): (int(b.launches), float(b.total_ms)) for b in list(buf)[: n.value]}
+
+    def trace(self):
+        n = C.c_int()
+        _check(self._lib.sbci_trace(self._h, None, 0, C.byref(n)))
+        buf = (sbci_trace_record * max(n.value, 1))()
+        _check(self._lib.sbci_trace(self._h, buf, n.value, C.byref(n)))
+        return list(buf)[: n.value]
