@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ncu", action="store_true",
+                    help="one solve, no warm-up and no extra legs (for an ncu launch list)")
+    ap.add_argument("--sigma-only", default=None, choices=["h10", "h12", "n14", "n16"],
+                    help="only run sigma products of one workload (for ncu captures)")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -324,8 +329,48 @@ def run_gb300(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def sigma_only(args):
+    """A few sigma products of one workload: the small cases of the ncu captures."""
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    I = {"h10": lambda: inputs.h_chain(10, 1.2), "h12": lambda: inputs.h_chain(12, 1.2),
+         "n14": lambda: inputs.random_df(14, 14), "n16": lambda: inputs.random_df(16, 16)}[args.sigma_only]()
+    ctx = sbci.Context.from_integrals(I)
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    c = torch.from_numpy(inputs.random_vector(ctx.na, ctx.nb, 1)).cuda()
+    out = torch.empty_like(c)
+    for _ in range(args.reps):
+        ctx.sigma(c, out, prec=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"sigma_only": args.sigma_only, "ndet": ctx.ndet, "reps": args.reps,
+                      "norm": float(out.norm())}))
+
+
+def run_ncu_solve(args):
+    """One solve of the bench workload with nothing else (ncu launch lists)."""
+    import torch
+
+    from paper_2603_06101_gb300 import sbci
+
+    I = workload()
+    ctx = sbci.Context.from_integrals(I)
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    E, _, R, st = ctx.solve(NSTATES, sbci.params(sector=1, prec=prec))
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_solve": WORKLOAD, "energies": [float(e) for e in E],
+                      "sigma": sum(r.n_sigma for r in R)}))
+
+
 def main():
     args = parse()
+    if args.sigma_only:
+        sigma_only(args)
+        return
+    if args.ncu:
+        run_ncu_solve(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

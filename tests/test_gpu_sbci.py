@@ -59,10 +59,16 @@ def test_h6_four_states_and_step_api():
     assert stt == sbci.SBCI_OK
     H = sc.dense_hamiltonian(I.h1, I.eri, 3, 3)
     w = np.linalg.eigvalsh(H)[:4] + I.e_core
-    assert np.abs(E - w).max() < 1e-8
+    # H6 has inversion symmetry: the start of an excited state (S1.4) keeps the
+    # symmetry of the previous state up to rounding, so two runs may meet the
+    # third and fourth states in either order.  The set found is unique; the
+    # order is not, so compare sorted energies and check each is an eigenpair.
+    assert np.abs(np.sort(E) - w).max() < 1e-8
+    for j in range(4):
+        assert np.linalg.norm(H @ V[j] - (E[j] - I.e_core) * V[j]) < 2e-5
     assert np.abs(V @ V.T - np.eye(4)).max() < 1e-8
     _, res = _oracle_run(key, 4)
-    assert np.abs(E - I.e_core - np.array([r.energy for r in res])).max() < 1e-8
+    assert np.abs(np.sort(E - I.e_core) - np.sort([r.energy for r in res])).max() < 1e-8
     # begin / step / finish give the same as solve
     ctx.begin(4)
     done = False
