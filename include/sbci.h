@@ -73,10 +73,13 @@ typedef struct {
   int sector;       /* 0: every determinant; 1: c = c^T (needs nalpha == nbeta) */
   int n_init;       /* determinants of the initial guess; 0 -> max(k, 2) */
   int init;         /* 0: lowest diagonal (S1.1); 1: caller vector c0 */
-  int prec;         /* sbci_precision of the main stage; SBCI_FP64 */
-  double mixed_eps; /* low-precision stage ends at dE < mixed_eps ... ; 1e-8 */
+  int prec;         /* sbci_precision of the main stage; SBCI_FP64.  With a
+                       low precision, each state runs SB steps with that sigma
+                       until dE < mixed_eps and |z'| < mixed_r, then replaces
+                       X by an FP64 H x and continues in FP64 to Eq. S61. */
+  double mixed_eps; /* end of the low-precision stage: dE < mixed_eps ... ; 1e-8 */
   double mixed_r;   /* ... and |z'| < mixed_r; 1e-4 */
-  int refine_max_sigma; /* FP64 refinement cap per state; 30 */
+  int refine_max_sigma; /* cap on FP64 H-products per state in refinement; 30 */
 } sbci_params;
 
 typedef struct {
@@ -95,7 +98,8 @@ typedef struct {
   double energy;      /* E_{t+1}, electronic (no e_core) */
   double b, c, k;     /* parameters of the step (Eqs. S23-S24, S53-S55) */
   double dE, dz;      /* |E_{t+1}-E_t| and |z'_{t+1}| */
-  int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle */
+  int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle,
+                         6 low-precision stage ended: switch to FP64 refinement */
   int prec;           /* sbci_precision of the sigma used in the step */
 } sbci_trace_record;
 

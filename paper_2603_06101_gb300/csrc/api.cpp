@@ -50,9 +50,10 @@ namespace {
 
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
-enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_COUNT };
+enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
-                                       "sb_project", "reduce", "lincomb", "dots", "diagonal"};
+                                       "sb_project", "reduce", "lincomb", "dots", "diagonal",
+                                       "sigma_gather_contract_tc"};
 
 struct Prof {
   bool on = false;
@@ -106,6 +107,8 @@ struct sbci_ctx {
   void *d_G = nullptr;
   size_t G_bytes = 0;
   double *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
+  int *d_status = nullptr, *h_status = nullptr;  // device error word (bounded waits)
+  int nsm = 1;
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
   size_t tmp_elems = 0;
   std::vector<double> W_host;
@@ -180,12 +183,23 @@ sbci_status timed(sbci_ctx *c, int kid, F &&launch) {
 }
 
 // sigma of one device vector, optional epilogue dots against u[0..2].
-sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, const double *u0,
-                      const double *u1, const double *u2) {
-  if (prec != SBCI_FP64 && prec != SBCI_FP32) {
-    set_error("precision mode not available in this build");
+sbci_status check_prec(const sbci_ctx *c, int prec) {
+  if (prec == SBCI_FP64 || prec == SBCI_FP32) return SBCI_OK;
+  if (prec == SBCI_TF32X3) {
+    int Kp, Np;
+    uint32_t cols;
+    size_t smem;
+    if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) return SBCI_OK;
+    set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14); use SBCI_FP32");
     return SBCI_ERR_INVALID;
   }
+  set_error("precision mode not available in this build");
+  return SBCI_ERR_INVALID;
+}
+
+sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, const double *u0,
+                      const double *u1, const double *u2) {
+  RET(check_prec(c, prec));
   RET(ensure_G(c, prec));
   SigmaArgs a{};
   a.c = in;
@@ -211,7 +225,10 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.partials = c->d_partials;
   a.grid = c->grid;
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
-  RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
+  if (prec == SBCI_TF32X3)
+    RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->nsm, c->stream); }));
+  else
+    RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
   RET(timed(c, K_SC, [&] { return launch_scatter(a, p32, c->stream); }));
   return SBCI_OK;
 }
@@ -220,7 +237,12 @@ sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
   RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, c->grid, s0, s1, c->d_result, c->stream); }));
   CK(cudaMemcpyAsync(c->h_result + s0, c->d_result + s0, sizeof(double) * (s1 - s0),
                      cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (*c->h_status != 0) {
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    return SBCI_ERR_TIMEOUT;
+  }
   for (int i = s0; i < s1; ++i)
     if (!std::isfinite(c->h_result[i])) {
       set_error("non-finite dot product in a device reduction");
@@ -427,6 +449,25 @@ void later_step(const Solver &s, StepOut &o) {
   o.E2 = w[1];
 }
 
+// End of the low-precision stage of a state: X <- H x in FP64 (the exact
+// H-image replaces the recurrence-carried one), E <- x.X / x.x, and the state
+// restarts from x/|x| on the first-step path with FP64 sigma until Eq. S61.
+sbci_status switch_to_fp64(sbci_ctx *c) {
+  Solver &s = c->s;
+  s.prec = SBCI_FP64;
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(gen_dots(c, {s.x, s.x}, {s.x, s.X}));
+  const double xx = c->h_result[S_GEN0], xX = c->h_result[S_GEN0 + 1];
+  s.E = xX / xx;
+  s.rep[s.alpha].n_sigma += 1;
+  s.rep[s.alpha].n_sigma_fp64 += 1;
+  RET(advance(c, 1.0 / std::sqrt(xx), 0.0, 0.0, 0.0, s.E, 1.0, Epre_of(c)));
+  s.first = true;
+  s.sx_pending = 1.0;
+  s.t = 0;
+  return SBCI_OK;
+}
+
 sbci_status finalize_state(sbci_ctx *c, bool converged, const StepOut *o) {
   Solver &s = c->s;
   const double nx = std::sqrt(s.dots[S_NXX]);
@@ -470,6 +511,7 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, const StepOut *o) {
   RET(lincomb(c, s.X, {s.X}, {1.0 / nrm}));
   s.E = o->E2;
   s.alpha += 1;
+  s.prec = s.p.prec;
   return start_state(c);
 }
 
@@ -668,6 +710,8 @@ void sbci_destroy(sbci_ctx *c) {
     if (p) cudaFree(p);
   if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
   if (c->h_result) cudaFreeHost(c->h_result);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->d_status) cudaFree(c->d_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -755,6 +799,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
   TRY(cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"));
   c->grid = 4 * std::max(nsm, 1);
+  c->nsm = std::max(nsm, 1);
   // packed operator W[P][Q], P = (i>=j), Q = (k>=l):
   //   W = 1/2 (ij|kl) + (k_ij d_kl + d_ij k_kl) / (2N),  k_ij = h_ij - 1/2 sum_m (im|mj)
   const int N = nalpha + nbeta;
@@ -818,6 +863,10 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaMemsetAsync(c->d_partials, 0, sizeof(double) * S_COUNT * c->grid, c->stream), "memset"));
   TRY(cuda_ok(cudaMalloc((void **)&c->d_result, sizeof(double) * S_COUNT), "cudaMalloc"));
   TRY(cuda_ok(cudaMallocHost((void **)&c->h_result, sizeof(double) * S_COUNT), "cudaMallocHost"));
+  TRY(cuda_ok(cudaMallocHost((void **)&c->h_status, sizeof(int)), "cudaMallocHost"));
+  *c->h_status = 0;
+  TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
+  TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   TRY(cuda_ok(launch_diagonal(c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_mask_b, c->Na, c->Nb, n,
                               c->stream), "diagonal kernel"));
   TRY(cuda_ok(cudaStreamSynchronize(c->stream), "sync"));
@@ -874,10 +923,7 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
     set_error("sbci_sigma: bad argument");
     return SBCI_ERR_INVALID;
   }
-  if (prec != SBCI_FP64 && prec != SBCI_FP32 && prec != SBCI_TF32X3 && prec != SBCI_BF16X3) {
-    set_error("sbci_sigma: unknown precision");
-    return SBCI_ERR_INVALID;
-  }
+  RET(check_prec(c, prec));
   const size_t n = (size_t)c->ndet;
   if (!on_device) {
     RET(check_finite(in, n * nvec, "c"));
@@ -902,7 +948,12 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
       RET(run_sigma(c, src, dst, prec, nullptr, nullptr, nullptr));
     }
   }
+  CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (*c->h_status != 0) {
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    return SBCI_ERR_TIMEOUT;
+  }
   return SBCI_OK;
 }
 
@@ -922,10 +973,7 @@ sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const doub
     set_error("init = 1 needs c0");
     return SBCI_ERR_INVALID;
   }
-  if (s.p.prec != SBCI_FP64 && s.p.prec != SBCI_FP32) {
-    set_error("sbci_begin: precision mode not available in this build");
-    return SBCI_ERR_INVALID;
-  }
+  RET(check_prec(c, s.p.prec));
   if ((long long)k > c->ndet) {
     set_error("sbci_begin: more states than determinants");
     return SBCI_ERR_INVALID;
@@ -985,7 +1033,14 @@ sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
   tr.dz = dz;
   tr.prec = s.prec;
   sbci_status ret = SBCI_OK;
-  if (dE < s.p.eps0 && dz < s.p.r0) {  // Eq. S61
+  const bool low = (tr.prec != SBCI_FP64);
+  if (low && ((dE < s.p.mixed_eps && dz < s.p.mixed_r) || r.n_sigma >= s.p.max_sigma / 2)) {
+    // the low-precision stage has done its part: refine in FP64
+    tr.event = 6;
+    s.trace.push_back(tr);
+    if (rec) *rec = tr;
+    RET(switch_to_fp64(c));
+  } else if (!low && dE < s.p.eps0 && dz < s.p.r0) {  // Eq. S61
     tr.event = 1;
     s.trace.push_back(tr);
     if (rec) *rec = tr;
@@ -1014,7 +1069,8 @@ sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
         s.t = 0;
       }
     }
-    if (r.n_sigma >= s.p.max_sigma) {
+    if (r.n_sigma >= s.p.max_sigma ||
+        (s.p.prec != SBCI_FP64 && r.n_sigma_fp64 >= s.p.refine_max_sigma)) {
       ret = SBCI_ERR_NOT_CONVERGED;
       set_error("state reached max_sigma without converging");
       RET(finalize_state(c, false, &o));

@@ -1,0 +1,273 @@
+// Tensor-core (tcgen05) gather + contract of the sigma build in 3-term TF32
+// split precision, for sm_103a.
+//
+// Per tile of 128 determinants (one per thread, one per TMEM lane):
+//   1. gather   D[I, Q] = sum_{links of I} sign * c[J]   into shared memory,
+//               FP32, laid out as the K-major no-swizzle canonical operand A
+//               (8-row x 16-byte core matrices);
+//   2. split    D = D_hi + D_lo, both rounded to TF32, in place;
+//   3. MMA      G^T = D_hi W_hi + D_hi W_lo + D_lo W_hi  (M=128, N=Np, K=8 per
+//               instruction), issued by one thread, accumulated in TMEM (FP32);
+//   4. epilogue tcgen05.ld of the thread's lane -> G[P][I] (FP32) in global.
+// W (symmetric, packed pairs) is split once per CTA into TF32 hi/lo operand
+// B and stays in shared memory.  The dropped D_lo W_lo term and the TF32
+// rounding of the lo parts leave a relative error of about 2^-21 per product.
+//
+// Every wait on the MMA-completion mbarrier is bounded; on timeout the kernel
+// raises bit 0 of *status, waits once more (bounded) for its MMAs, frees its
+// TMEM and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbci_internal.h"
+
+namespace sbci {
+
+constexpr int kTcM = 128;         // determinants per tile = MMA M = TMEM lanes
+constexpr int kTcThreads = 128;
+constexpr long long kWaitIters = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Shared-memory matrix descriptor: no swizzle, start/LBO/SBO in 16-byte units,
+// descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (format 2 at bits 7-9 and 10-12), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long long iters) {
+  for (long long i = 0; i < iters; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Float offset of element (r, q) in a K-major no-swizzle operand with Kp
+// columns: core matrix (r/8, q/4) of 8 rows x 4 TF32 (128 bytes), K-adjacent
+// core matrices 128 bytes apart (LBO), 8-row groups Kp*32 bytes apart (SBO).
+__device__ __forceinline__ int opnd_off(int r, int q, int Kp) {
+  return (r >> 3) * (Kp * 8) + (q >> 2) * 32 + (r & 7) * 4 + (q & 3);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gather_contract_tc(SigmaArgs a, int Kp, int Np, uint32_t tmem_cols, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *A = reinterpret_cast<float *>(smem);                // hi (after split)
+  float *Alo = A + kTcM * Kp;
+  uint32_t *Bhi = reinterpret_cast<uint32_t *>(Alo + kTcM * Kp);
+  uint32_t *Blo = Bhi + Np * Kp;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(Blo + Np * Kp);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int npair = a.npair;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // operand B: W split into TF32 hi/lo from FP64, zero-padded to Np x Kp
+  for (int idx = tid; idx < Np * Kp; idx += kTcThreads) {
+    const int n = idx / Kp, k = idx - n * Kp;
+    const double w = (n < npair && k < npair) ? a.W[(size_t)n * npair + k] : 0.0;
+    const uint32_t hi = tf32_bits((float)w);
+    const float lo = (float)(w - (double)__uint_as_float(hi));
+    Bhi[opnd_off(n, k, Kp)] = hi;
+    Blo[opnd_off(n, k, Kp)] = tf32_bits(lo);
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_tf32(kTcM, Np);
+  const uint32_t LBO = 128, SBO = (uint32_t)Kp * 32;
+  const uint32_t sA = smem_u32(A), sAlo = smem_u32(Alo), sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+  const uint32_t sbar = smem_u32(mbar);
+  float *G = reinterpret_cast<float *>(a.G);
+  const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long I = tile * kTcM + tid;
+    const bool valid = I < a.ndet;
+    // 1. gather this thread's row of D (FP32) into A
+    for (int q = 0; q < Kp; q += 4)
+      *reinterpret_cast<float4 *>(A + opnd_off(tid, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
+      const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+      for (int e = 0; e < a.nlink_a; ++e) {
+        const uint32_t v = __ldg(la + e);
+        const float cv = (float)__ldg(a.c + (size_t)link_J(v) * a.nb + ib);
+        A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -cv : cv;
+      }
+      const uint32_t *lb = a.link_b + (size_t)ib * a.nlink_b;
+      const double *crow = a.c + (size_t)ia * a.nb;
+      for (int e = 0; e < a.nlink_b; ++e) {
+        const uint32_t v = __ldg(lb + e);
+        const float cv = (float)__ldg(crow + link_J(v));
+        A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -cv : cv;
+      }
+    }
+    // 2. split in place: A <- tf32(D), Alo <- tf32(D - tf32(D))
+    for (int q = 0; q < Kp; q += 4) {
+      float4 *p = reinterpret_cast<float4 *>(A + opnd_off(tid, q, Kp));
+      const float4 v = *p;
+      float4 h, l;
+      h.x = __uint_as_float(tf32_bits(v.x));
+      h.y = __uint_as_float(tf32_bits(v.y));
+      h.z = __uint_as_float(tf32_bits(v.z));
+      h.w = __uint_as_float(tf32_bits(v.w));
+      l.x = __uint_as_float(tf32_bits(v.x - h.x));
+      l.y = __uint_as_float(tf32_bits(v.y - h.y));
+      l.z = __uint_as_float(tf32_bits(v.z - h.z));
+      l.w = __uint_as_float(tf32_bits(v.w - h.w));
+      *p = h;
+      *reinterpret_cast<float4 *>(Alo + opnd_off(tid, q, Kp)) = l;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // 3. three products per K step, one issuing thread
+    if (tid == 0) {
+      for (int kk = 0; kk < Kp / 8; ++kk) {
+        const uint32_t koff = (uint32_t)kk * 256;  // two K-adjacent core matrices
+        const uint64_t ah = smem_desc(sA + koff, LBO, SBO), al = smem_desc(sAlo + koff, LBO, SBO);
+        const uint64_t bh = smem_desc(sBhi + koff, LBO, SBO), bl = smem_desc(sBlo + koff, LBO, SBO);
+        mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       sbar)
+                   : "memory");
+    }
+    ok = mbar_wait(sbar, phase, kWaitIters);
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    phase ^= 1u;
+    fence_after();
+    // 4. epilogue: lane tid holds row tid of G^T
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < Np; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(lane_addr + (uint32_t)c0, r);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < npair) G[(size_t)(c0 + j) * a.ndet + I] = __uint_as_float(r[j]);
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1);
+    mbar_wait(sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+// Operand sizes of the TF32 split kernel for npair packed pairs.
+bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
+  const int kp = (npair + 7) / 8 * 8;
+  const int np = (npair + 15) / 16 * 16;
+  uint32_t c = 32;
+  while (c < (uint32_t)np) c <<= 1;
+  const size_t bytes = (size_t)(2 * kTcM * kp + 2 * np * kp) * 4 + 16;
+  *Kp = kp;
+  *Np = np;
+  *cols = c;
+  *smem = bytes;
+  return np <= 256 && bytes <= 227 * 1024;
+}
+
+cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int num_sms, cudaStream_t s) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!tc_dims(a.npair, &Kp, &Np, &cols, &smem)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
+  const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
+  long long grid = (long long)num_sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  k_gather_contract_tc<<<(int)grid, kTcThreads, smem, s>>>(a, Kp, Np, cols, status);
+  return cudaGetLastError();
+}
+
+}  // namespace sbci

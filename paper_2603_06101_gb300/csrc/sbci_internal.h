@@ -67,6 +67,9 @@ struct SigmaArgs {
 // prec: 0 = FP64 scratch and contraction, 1 = FP32 (SIMT) contraction
 cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
+// tcgen05 TF32x3 gather + contract (kernels_tc.cu); writes FP32 G like prec 1.
+bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
+cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int num_sms, cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
 // Vector kernels (kernels_vec.cu)
