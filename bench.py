@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu", action="store_true",
@@ -216,7 +216,7 @@ def run_gb300(args, rank, world, local_rank):
         import torch.distributed as dist
 
     I = workload()
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
     stream = torch.cuda.Stream()
     ctx = sbci.Context.from_integrals(I, stream=stream.cuda_stream)
     p = sbci.params(sector=1, prec=prec)
@@ -269,7 +269,14 @@ def run_gb300(args, rank, world, local_rank):
     name, (nl, ms) = dom
     npair, ndet = ctx.npair, ctx.ndet
     avg_s = ms / 1000.0 / max(nl, 1)
-    if name == "sigma_gather_contract":
+    if name == "sigma_gather_contract_tc":
+        flops = 2.0 * npair * npair * ndet
+        peak = pk.get("bf16_tflops", 1900.0) * 0.5  # TF32 dense = half the BF16 rate (nominal 1.1 vs 2.25 PF)
+        roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_kind": f"{pk_kind} bf16 x nominal TF32/BF16 ratio (0.5); achieved counts algorithmic "
+                             "flops once (the 3-term split executes 3x)",
+                "algorithmic_per_launch": flops}
+    elif name == "sigma_gather_contract":
         flops = 2.0 * npair * npair * ndet
         if args.prec == "fp64":
             peak = pk.get("bf16_tflops", 1900.0) * FP64_NOMINAL_TFLOPS / BF16_NOMINAL_TFLOPS
@@ -316,7 +323,7 @@ def run_gb300(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "norb": 10, "ndet": ndet, "states": NSTATES,
                        "sector": "c=c^T", "sigma_precision": args.prec, "l2": "flushed (256 MB write) between steps",
@@ -338,7 +345,7 @@ def sigma_only(args):
     I = {"h10": lambda: inputs.h_chain(10, 1.2), "h12": lambda: inputs.h_chain(12, 1.2),
          "n14": lambda: inputs.random_df(14, 14), "n16": lambda: inputs.random_df(16, 16)}[args.sigma_only]()
     ctx = sbci.Context.from_integrals(I)
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
     c = torch.from_numpy(inputs.random_vector(ctx.na, ctx.nb, 1)).cuda()
     out = torch.empty_like(c)
     for _ in range(args.reps):
@@ -356,7 +363,7 @@ def run_ncu_solve(args):
 
     I = workload()
     ctx = sbci.Context.from_integrals(I)
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
     E, _, R, st = ctx.solve(NSTATES, sbci.params(sector=1, prec=prec))
     torch.cuda.synchronize()
     print(json.dumps({"ncu_solve": WORKLOAD, "energies": [float(e) for e in E],
