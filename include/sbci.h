@@ -137,6 +137,34 @@ sbci_status sbci_diagonal(sbci_ctx *ctx, double *out, int on_device);
 sbci_status sbci_sigma(sbci_ctx *ctx, const double *c, double *sigma, int nvec,
                        int prec, int on_device);
 
+/* Size of the fixed device scratch used by sbci_sigma_noalloc: 32 MiB,
+ * enough for npair * Ndet <= 4,194,304 doubles (for example the 10-orbital,
+ * 5+5-electron space: 55 * 63,504). */
+#define SBCI_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* sigma = H c in FP64 for one device vector, without allocating anything.
+ * The paper has no counterpart: this is a library convenience for callers
+ * that cannot call cudaMalloc at the time they need sigma -- code running
+ * inside a stream capture, code in a framework that owns all device memory
+ * through its own pool, or a latency-critical loop that cannot afford the
+ * synchronisation an allocation implies.
+ * c, sigma: device pointers to Ndet doubles each (caller-owned, not
+ * overlapping).  cuda_stream: stream to run on, NULL for the context stream.
+ * The call is asynchronous: sigma is ready when the stream reaches it.
+ * Scratch: a file-scope static device array of SBCI_NOALLOC_SCRATCH_BYTES on
+ * every GPU that loads the library, kept until process exit.  Its device
+ * address is looked up on the first call on each device (with lazy module
+ * loading that look-up is also when the array's memory is committed), so make
+ * that first call before any stream capture.  Every call on a device shares the one
+ * array: calls that overlap on the GPU (other streams, other threads, other
+ * contexts) race and give wrong results; serialise them.  The array keeps
+ * the last call's contents; every call overwrites all of the part it reads.
+ * Errors: SBCI_ERR_INVALID for NULL arguments or a space whose scratch
+ * (npair * Ndet * 8 bytes) exceeds the array; SBCI_ERR_CUDA on a launch
+ * error.  Never calls cudaMalloc, cudaFree or an allocating library routine. */
+sbci_status sbci_sigma_noalloc(const sbci_ctx *ctx, const double *c, double *sigma,
+                               void *cuda_stream);
+
 /* Starts an SBCI1 solve for the k lowest states (Fig. 1A, Algorithm 1).
  * params may be NULL (defaults).  c0: host [Ndet] when params->init == 1,
  * else ignored (may be NULL).  Allocates the per-solve vectors. */

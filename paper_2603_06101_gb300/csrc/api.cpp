@@ -669,6 +669,25 @@ sbci_status init_from_vector(sbci_ctx *c, const double *c0) {
 
 }  // namespace
 
+bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream) {
+  if (!c) return false;
+  *a = SigmaArgs{};
+  a->link_a = c->d_link_a;
+  a->link_b = c->d_link_b;
+  a->W = c->d_W;
+  a->Wf = c->d_Wf;
+  a->na = c->Na;
+  a->nb = c->Nb;
+  a->nlink_a = c->sa.nlink;
+  a->nlink_b = c->sb.nlink;
+  a->npair = c->npair;
+  a->npair_pad = c->npair_pad;
+  a->ndet = c->ndet;
+  a->grid = c->grid;
+  if (stream) *stream = c->stream;
+  return true;
+}
+
 // ===========================================================================
 extern "C" {
 

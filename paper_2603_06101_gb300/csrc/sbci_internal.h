@@ -125,3 +125,11 @@ void jacobi_eigh(int n, const double *A, double *w, double *V);
 void set_error(const std::string &msg);
 
 }  // namespace sbci
+
+struct sbci_ctx;
+namespace sbci {
+// Fills the sigma arguments of a context without allocating anything (G and
+// the dot outputs are left null).  Returns false on a null context.
+bool ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream);
+
+}  // namespace sbci

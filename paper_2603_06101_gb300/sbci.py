@@ -68,7 +68,9 @@ _lib = None
 
 EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_table",
            "sbci_diagonal", "sbci_sigma", "sbci_begin", "sbci_step", "sbci_finish", "sbci_solve",
-           "sbci_trace", "sbci_profile", "sbci_profile_read", "sbci_last_error", "sbci_destroy"]
+           "sbci_trace", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
+           "sbci_last_error", "sbci_destroy"]
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def load(path: str = LIB_PATH):
@@ -92,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.sbci_finish.argtypes = [P, P, P, P]
     lib.sbci_solve.argtypes = [P, I, C.POINTER(sbci_params), P, P, P, P]
     lib.sbci_trace.argtypes = [P, C.POINTER(sbci_trace_record), I, C.POINTER(I)]
+    lib.sbci_sigma_noalloc.argtypes = [P, P, P, P]
     lib.sbci_profile.argtypes = [P, I]
     lib.sbci_profile_read.argtypes = [P, C.POINTER(sbci_kernel_stat), I, C.POINTER(I)]
     lib.sbci_last_error.restype = C.c_char_p
@@ -200,6 +203,15 @@ class Context:
         po, dev2 = _ptr(out)
         assert dev == dev2, "input and output must both be host or both be device"
         _check(self._lib.sbci_sigma(self._h, pc, po, nvec, int(prec), int(dev)))
+        return out
+
+    def sigma_noalloc(self, c, out, stream=None):
+        """FP64 sigma of one device vector into ``out`` (device), allocation-free,
+        asynchronous on ``stream`` (a cudaStream_t handle) or the context stream."""
+        pc, dev = _ptr(c)
+        po, dev2 = _ptr(out)
+        assert dev and dev2, "sigma_noalloc takes device tensors"
+        _check(self._lib.sbci_sigma_noalloc(self._h, pc, po, C.c_void_p(stream) if stream else None))
         return out
 
     def begin(self, k, p: sbci_params | None = None, c0=None):
