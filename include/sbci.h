@@ -196,12 +196,50 @@ typedef struct {
   double total_ms;     /* summed CUDA-event time of those launches (0 if timing off) */
 } sbci_kernel_stat;
 
-/* Resets the statistics; enable = 1 also brackets every launch with CUDA
- * events on the context stream (adds ~2 event records per launch). */
+/* Resets the statistics.  Launches are always counted (including the kernels
+ * a solve's CUDA graph runs).  enable = 1 also brackets every launch with
+ * CUDA events on the context stream; solves then launch their step kernels
+ * one by one instead of through the graph, so that each can be timed. */
 sbci_status sbci_profile(sbci_ctx *ctx, int enable);
 
 /* Waits for the recorded events and copies up to cap entries; *n = families. */
 sbci_status sbci_profile_read(sbci_ctx *ctx, sbci_kernel_stat *out, int cap, int *n);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solves on one GPU (no counterpart in the
+ * paper, which runs one solve at a time; this is the request loop around the
+ * same SBCI1 solve).  Requests are admitted from a FIFO queue into slots while
+ * a slot is free and the request's device-memory footprint fits the budget;
+ * each admitted solve keeps its state resident and runs its SB steps as a
+ * CUDA-graph loop on its own stream, so solves overlap on the device.  One
+ * host thread drives the server; calls are not thread-safe. */
+typedef struct sbci_server sbci_server;
+
+/* mem_budget_bytes: device memory the server may hold for admitted solves;
+ * max_slots: solves in flight at once (1..1024). */
+sbci_status sbci_server_create(sbci_server **out, size_t mem_budget_bytes, int max_slots);
+
+/* Queues one solve of the k lowest states (1 <= k <= 8).  h1, eri, e_core as
+ * in sbci_init_integrals (copied at the call); params may be NULL.
+ * *ticket identifies the request.  SBCI_ERR_NOMEM if its footprint alone
+ * exceeds the budget. */
+sbci_status sbci_server_submit(sbci_server *sv, int norb, int nalpha, int nbeta, const double *h1,
+                               const double *eri, double e_core, int k, const sbci_params *params,
+                               long long *ticket);
+
+/* Non-blocking progress: admits what fits, handles every slot whose graph
+ * round has finished (controller event, next round or retirement).  Outputs
+ * (nullable): solves in slots, requests still queued. */
+sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued);
+
+/* *done = 1 once the request has finished; then energies [k] (total),
+ * rep [k] and times [2] = {queueing seconds, latency seconds from submit to
+ * completion} are written (each nullable) and the solve's status returned. */
+sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, double *energies,
+                             sbci_report *rep, double *times);
+
+/* Waits for in-flight rounds and frees every slot.  NULL is a no-op. */
+void sbci_server_destroy(sbci_server *sv);
 
 /* Thread-local message of the last error in this thread ("" if none). */
 const char *sbci_last_error(void);

@@ -1,14 +1,16 @@
 // C ABI of libsbci: context and integral preparation, the sigma entry point,
-// and the host controller of SBCI1 (Algorithm 1 with Sections S1.1-S1.5).
+// and the driver of SBCI1 (Algorithm 1 with Sections S1.1-S1.5).
 //
-// Per SB step the controller launches, on one stream and without a host
-// round trip in between:
-//   update sweep (Eqs. 10-11, S56-S60, preconditioner Eqs. 6-7)
-//   -> [reduce x_c.w -> projection (Eq. S31)] -> sigma(z) (Eq. S32) with dots
-//   -> reduction of every dot -> one 8-byte-per-slot copy to pinned memory,
-// then synchronises once and solves the 2x2 (Eqs. S10-S24) or 3x3
-// (Eqs. S33-S55) subspace problem on the host in FP64.  A restart (S62) is
-// applied lazily: the next update scales x, X by 1/|x| and zeroes y, Y.
+// The SB steps run under a device-resident controller (ctl.h): one step is
+//   update sweep (Eqs. 10-11, S56-S60; preconditioner Eqs. 6-7) whose last
+//   block runs the convergence / restart test (Eqs. S61, S62)
+//   -> projection against stored states (Eq. S31)
+//   -> sigma of the next z (Eq. S32), whose last block solves the 2x2
+//      (Eqs. S10-S24) or 3x3 (Eqs. S33-S55) subspace problem,
+// and a CUDA graph repeats that body in a device-side while loop until the
+// controller halts.  The host only handles the rare events: a state has
+// converged (store it, start the next from the second Ritz vector, S1.4),
+// the low-precision stage has ended (re-sync X = H x in FP64), a cap.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,8 +22,12 @@
 #include <string>
 #include <vector>
 
+#include <cstddef>
+
 #include "../../include/sbci.h"
+#include "ctl.h"
 #include "sbci_internal.h"
+#include "step.h"
 
 namespace sbci {
 static thread_local std::string g_err;
@@ -68,24 +74,21 @@ struct Solver {
   bool active = false, done = false;
   int k = 0;
   sbci_params p{};
-  int alpha = 0;
-  int prec = SBCI_FP64;  // precision of the sigma in use
   // device vectors [ndet] each
   double *x = nullptr, *X = nullptr, *y = nullptr, *Y = nullptr, *w = nullptr;
   double *z[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr};
   double *xc = nullptr;  // [k][ndet]
-  int cur = 0;
-  // host scalars of the current state
-  double E = 0.0;        // E_t
-  int t = 0;
-  bool first = true;     // next step takes the first-step (2x2) path
-  double sx_pending = 1.0;
-  bool proj = false;     // projection kernel in use (alpha > 0 or sector)
-  double dots[S_COUNT];
+  CtlState *d_ctl = nullptr;  // device controller state
+  CtlState *h_ctl = nullptr;  // pinned host mirror
+  unsigned int *d_counters = nullptr;
+  int verified = 0;  // the current state passed its FP64 residual check
   std::vector<double> Ec;
   std::vector<sbci_report> rep;
   std::vector<sbci_trace_record> trace;
   int any_unconverged = 0;
+  // while-loop graphs, one per sigma precision
+  cudaGraph_t graph[4] = {};
+  cudaGraphExec_t gexec[4] = {};
 };
 
 }  // namespace
@@ -109,6 +112,7 @@ struct sbci_ctx {
   double *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
   int *d_status = nullptr, *h_status = nullptr;  // device error word (bounded waits)
   int nsm = 1;
+  int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
   size_t tmp_elems = 0;
   std::vector<double> W_host;
@@ -189,7 +193,7 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
     int Kp, Np;
     uint32_t cols;
     size_t smem;
-    if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) return SBCI_OK;
+    if (tc_dims(c->npair, &Kp, &Np, &cols, &smem) && c->tc_grid > 0) return SBCI_OK;
     set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14); use SBCI_FP32");
     return SBCI_ERR_INVALID;
   }
@@ -223,10 +227,10 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.dot_slot[1] = S_HYZ;
   a.dot_slot[2] = S_HZZ;
   a.partials = c->d_partials;
-  a.grid = c->grid;
+  a.grid = scatter_grid(c->ndet, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   if (prec == SBCI_TF32X3)
-    RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->nsm, c->stream); }));
+    RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
   else
     RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
   RET(timed(c, K_SC, [&] { return launch_scatter(a, p32, c->stream); }));
@@ -265,238 +269,251 @@ sbci_status lincomb(sbci_ctx *c, double *out, std::vector<const double *> in, st
 }
 
 // ---------------------------------------------------------------------------
-// SBCI1 controller
+// SBCI1 driver around the device controller
 
-double Epre_of(const sbci_ctx *c) {
-  const Solver &s = c->s;
-  return s.alpha == 0 ? s.E : s.Ec[0];  // newest ground-state Rayleigh quotient (Eqs. 6-7)
+double shift_for(const sbci_ctx *c, int alpha, double E) {
+  return alpha == 0 ? E : c->s.Ec[0];  // newest ground-state Rayleigh quotient (Eqs. 6-7)
 }
 
-// update sweep with the given parameters, then projection and sigma of the
-// next z, reductions and one synchronisation.  E is E_{t+1}, Epre the shift
-// of the preconditioner.
-sbci_status advance(sbci_ctx *c, double sx, double sy, double b, double cc, double E, double kinv,
-                    double Epre) {
+// Copies the controller header (and any committed trace records) to the host.
+sbci_status ctl_read(sbci_ctx *c) {
   Solver &s = c->s;
-  const int nxt = s.cur ^ 1;
-  UpdateArgs u{};
-  u.x = s.x;
-  u.X = s.X;
-  u.y = s.y;
-  u.Y = s.Y;
-  u.z = s.z[s.cur];
-  u.Z = s.Z[s.cur];
-  u.w = s.proj ? s.w : s.z[nxt];
-  u.diag = c->d_diag;
-  u.n = c->ndet;
-  u.sx = sx;
-  u.sy = sy;
-  u.b = b;
-  u.c = cc;
-  u.E = E;
-  u.kinv = kinv;
-  u.Epre = Epre;
-  u.guard = s.p.guard;
-  u.w_is_z = s.proj ? 0 : 1;
-  u.nxc = s.proj ? s.alpha : 0;
-  for (int i = 0; i < u.nxc; ++i) u.xc[i] = s.xc + (size_t)i * c->ndet;
-  u.partials = c->d_partials;
-  u.grid = c->grid;
-  RET(timed(c, K_UPD, [&] { return launch_update(u, c->stream); }));
-  if (s.proj) {
-    if (u.nxc > 0)
-      RET(timed(c, K_RED, [&] {
-        return launch_reduce(c->d_partials, c->grid, S_XCW0, S_XCW0 + u.nxc, c->d_result, c->stream);
-      }));
-    ProjectArgs pa{};
-    pa.w = s.w;
-    pa.z = s.z[nxt];
-    pa.x = s.x;
-    pa.y = s.y;
-    pa.nxc = u.nxc;
-    for (int i = 0; i < pa.nxc; ++i) pa.xc[i] = u.xc[i];
-    pa.coef = c->d_result + S_XCW0;
-    pa.sector = s.p.sector;
-    pa.na = c->Na;
-    pa.nb = c->Nb;
-    pa.n = c->ndet;
-    pa.partials = c->d_partials;
-    pa.grid = c->grid;
-    RET(timed(c, K_PROJ, [&] { return launch_project(pa, c->stream); }));
+  const size_t hdr = offsetof(CtlState, trace);
+  CK(cudaMemcpyAsync(s.h_ctl, s.d_ctl, hdr, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (*c->h_status != 0) {
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    return SBCI_ERR_TIMEOUT;
   }
-  s.cur = nxt;
-  RET(run_sigma(c, s.z[nxt], s.Z[nxt], s.prec, s.x, s.y, s.z[nxt]));
-  return reduce_and_fetch(c, 0, S_XCW0);
-}
-
-// Begin state alpha from x, X (normalised, orthogonal to the stored states) and E.
-sbci_status start_state(sbci_ctx *c) {
-  Solver &s = c->s;
-  s.proj = (s.alpha > 0) || (s.p.sector != 0);
-  s.t = 0;
-  s.first = true;
-  s.sx_pending = 1.0;
-  // residual z'_0 = X_0 - E_0 x_0 and w = M^-1 z'_0: an update with b = c = 0, y = 0
-  return advance(c, 1.0, 0.0, 0.0, 0.0, s.E, 1.0, Epre_of(c));
-}
-
-struct StepOut {
-  double E, b, c, k;
-  double r[3];  // second Ritz vector on (x_new, y_new, z_t)
-  double E2;
-  double sx, sy;
-};
-
-// First-step path (Eqs. S10-S24) on x_0 = sx * x (|x_0| = 1).
-void first_step(const Solver &s, StepOut &o) {
-  const double *d = s.dots;
-  const double sx = s.sx_pending;
-  const double Hxx = sx * sx * d[S_HXX];
-  const double Nxz = sx * d[S_NXZ], Hxz = sx * d[S_HXZ];
-  const double Nzz = d[S_NZZ], Hzz = d[S_HZZ];
-  o.sx = sx;
-  o.sy = 0.0;
-  o.b = 1.0;
-  const double g = Nzz - Nxz * Nxz;
-  if (!(g > 0.0) || g < s.p.gs_tol * Nzz) {  // z inside span{x}: no move
-    o.E = Hxx;
-    o.c = 0.0;
-    o.k = 1.0;
-    o.E2 = Hxx;
-    o.r[0] = 0.0;
-    o.r[1] = 0.0;
-    o.r[2] = 0.0;
-    return;
+  const int n = std::min(s.h_ctl->ntrace, kTraceCap);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(s.h_ctl->trace, s.d_ctl->trace, sizeof(sbci_trace_record) * n,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(&s.d_ctl->ntrace, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    s.trace.insert(s.trace.end(), s.h_ctl->trace, s.h_ctl->trace + n);
+    s.h_ctl->ntrace = 0;
   }
-  const double Bz = 1.0 / std::sqrt(g);  // S12
-  const double Bx = -Nxz * Bz;           // S13
-  double V[4], w[2], U[4];
-  V[0] = Hxx;
-  V[1] = V[2] = Bx * Hxx + Bz * Hxz;
-  V[3] = Bx * Bx * Hxx + Bz * Bz * Hzz + 2.0 * Bx * Bz * Hxz;
-  jacobi_eigh(2, V, w, U);
-  const double vx = U[0], vz = U[2];
-  o.E = w[0];
-  o.k = 1.0 / (vx + vz * Bx);            // S23
-  o.c = -vz * Bz / (vx + vz * Bx);       // S24
-  const double wx = U[1], wz = U[3];
-  const double A = wx + wz * Bx;         // coefficient on x_0 = x_new - y_new
-  o.r[0] = A;
-  o.r[1] = -A;
-  o.r[2] = wz * Bz;
-  o.E2 = w[1];
-}
-
-// Later-step path (Eqs. S33-S55).
-void later_step(const Solver &s, StepOut &o) {
-  const double *d = s.dots;
-  const double Nxx = d[S_NXX], Nxy = d[S_NXY], Nxz = d[S_NXZ];
-  const double Nyy = d[S_NYY], Nyz = d[S_NYZ], Nzz = d[S_NZZ];
-  const double Hxx = d[S_HXX], Hxy = d[S_HXY], Hxz = d[S_HXZ];
-  const double Hyy = d[S_HYY], Hyz = d[S_HYZ], Hzz = d[S_HZZ];
-  o.sx = 1.0;
-  o.sy = 1.0;
-  const double Ax = 1.0 / std::sqrt(Nxx);             // S34
-  const double By = 1.0 / std::sqrt(Nyy - Nxy * Nxy / Nxx);  // S36
-  const double Bx = -Nxy / Nxx * By;                   // S37
-  const double P = Bx * Nxz + By * Nyz;                // S42
-  const double gz = Nzz - Nxz * Nxz / Nxx - P * P;
-  if (!(gz > 0.0) || gz < s.p.gs_tol * Nzz) {          // z inside span{x, y}: c = 0
-    double V[4], w[2], U[4];
-    V[0] = Ax * Ax * Hxx;
-    V[1] = V[2] = Ax * (Bx * Hxx + By * Hxy);
-    V[3] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;
-    jacobi_eigh(2, V, w, U);
-    const double vx = U[0], vy = U[2];
-    o.k = 1.0 / (vx * Ax + vy * Bx);
-    o.b = vy * By * o.k;
-    o.c = 0.0;
-    o.E = w[0];
-    const double wx = U[1], wy = U[3];
-    const double cx = wx * Ax + wy * Bx, cy = wy * By;
-    o.r[0] = cx;
-    o.r[1] = cy - cx * o.b;
-    o.r[2] = 0.0;
-    o.E2 = w[1];
-    return;
-  }
-  const double Cz = 1.0 / std::sqrt(gz);               // S39
-  const double Cy = -P * By * Cz;                      // S40
-  const double Cx = -(Nxz / Nxx + P * Bx) * Cz;        // S41
-  const double hx = Cx * Hxx + Cy * Hxy + Cz * Hxz;
-  const double hy = Cx * Hxy + Cy * Hyy + Cz * Hyz;
-  double V[9], w[3], U[9];
-  V[0] = Ax * Ax * Hxx;                                        // S44a
-  V[1] = V[3] = Ax * (Bx * Hxx + By * Hxy);                    // S44b
-  V[2] = V[6] = Ax * hx;                                       // S44c
-  V[4] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;  // S44d
-  V[5] = V[7] = Bx * hx + By * hy;                             // S44e
-  V[8] = Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz + 2.0 * Cx * Cy * Hxy +
-         2.0 * Cx * Cz * Hxz + 2.0 * Cy * Cz * Hyz;            // S44f
-  jacobi_eigh(3, V, w, U);
-  const double vx = U[0], vy = U[3], vz = U[6];
-  const double den = vx * Ax + vy * Bx + vz * Cx;
-  o.E = w[0];
-  o.k = 1.0 / den;                                     // S53
-  o.b = (vy * By + vz * Cy) / den;                     // S54
-  o.c = -vz * Cz / (vy * By + vz * Cy);                // S55
-  const double wx = U[1], wy = U[4], wz = U[7];
-  const double cx = wx * Ax + wy * Bx + wz * Cx, cy = wy * By + wz * Cy, cz = wz * Cz;
-  // pre-update vectors: y_t = y_new + c z_t, x_t = x_new - b y_new
-  o.r[0] = cx;
-  o.r[1] = cy - cx * o.b;
-  o.r[2] = cy * o.c + cz;
-  o.E2 = w[1];
-}
-
-// End of the low-precision stage of a state: X <- H x in FP64 (the exact
-// H-image replaces the recurrence-carried one), E <- x.X / x.x, and the state
-// restarts from x/|x| on the first-step path with FP64 sigma until Eq. S61.
-sbci_status switch_to_fp64(sbci_ctx *c) {
-  Solver &s = c->s;
-  s.prec = SBCI_FP64;
-  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
-  RET(gen_dots(c, {s.x, s.x}, {s.x, s.X}));
-  const double xx = c->h_result[S_GEN0], xX = c->h_result[S_GEN0 + 1];
-  s.E = xX / xx;
-  s.rep[s.alpha].n_sigma += 1;
-  s.rep[s.alpha].n_sigma_fp64 += 1;
-  RET(advance(c, 1.0 / std::sqrt(xx), 0.0, 0.0, 0.0, s.E, 1.0, Epre_of(c)));
-  s.first = true;
-  s.sx_pending = 1.0;
-  s.t = 0;
   return SBCI_OK;
 }
 
-sbci_status finalize_state(sbci_ctx *c, bool converged, const StepOut *o) {
+sbci_status ctl_write(sbci_ctx *c) {
   Solver &s = c->s;
-  const double nx = std::sqrt(s.dots[S_NXX]);
-  double *xca = s.xc + (size_t)s.alpha * c->ndet;
+  s.h_ctl->ntrace = 0;
+  CK(cudaMemcpyAsync(s.d_ctl, s.h_ctl, offsetof(CtlState, trace), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SBCI_OK;
+}
+
+StepArgs step_args(sbci_ctx *c, unsigned long long cond) {
+  Solver &s = c->s;
+  StepArgs a{};
+  a.ctl = s.d_ctl;
+  a.x = s.x;
+  a.X = s.X;
+  a.y = s.y;
+  a.Y = s.Y;
+  a.w = s.w;
+  a.diag = c->d_diag;
+  a.xc = s.xc;
+  a.n = c->ndet;
+  a.sector = s.p.sector;
+  a.na = c->Na;
+  a.nb = c->Nb;
+  a.partials = c->d_partials;
+  a.counter = s.d_counters;
+  a.cond = cond;
+  return a;
+}
+
+SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
+  Solver &s = c->s;
+  SigmaArgs a{};
+  ctx_sigma_args(c, &a, nullptr);
+  a.G = c->d_G;
+  a.dot_u[0] = s.x;
+  a.dot_u[1] = s.y;
+  a.dot_u[2] = nullptr;  // the controller's next z
+  a.dot_slot[0] = S_HXZ;
+  a.dot_slot[1] = S_HYZ;
+  a.dot_slot[2] = S_HZZ;
+  a.partials = c->d_partials;
+  a.grid = scatter_grid(c->ndet, c->nsm);
+  a.ctl = s.d_ctl;
+  a.counter = s.d_counters + 2;
+  a.cond = cond;
+  (void)prec;
+  return a;
+}
+
+// One step body: update -> projection -> sigma (gather+contract, scatter).
+// timing = 1: each launch is counted and bracketed with events (not in capture).
+sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool timing) {
+  const StepArgs st = step_args(c, cond);
+  const SigmaArgs sa = sigma_ctl_args(c, prec, cond);
+  const int g = step_grid(c->ndet, c->nsm);
+  const int p32 = (prec == SBCI_FP64) ? 0 : 1;
+  auto L = [&](int kid, auto &&f) -> sbci_status {
+    if (timing) return timed(c, kid, f);
+    CK(f());
+    return SBCI_OK;
+  };
+  RET(L(K_UPD, [&] { return launch_update_ctl(st, g, c->stream); }));
+  RET(L(K_PROJ, [&] { return launch_project_ctl(st, g, c->stream); }));
+  if (prec == SBCI_TF32X3)
+    RET(L(K_GCTC, [&] { return launch_gather_contract_tc(sa, c->d_status, c->tc_grid, c->stream); }));
+  else
+    RET(L(K_GC, [&] { return launch_gather_contract(sa, p32, c->stream); }));
+  RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
+  return SBCI_OK;
+}
+
+// While-loop graph over the step body for one sigma precision.
+sbci_status build_graph(sbci_ctx *c, int prec) {
+  Solver &s = c->s;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  sbci_status st = launch_body(c, prec, (unsigned long long)h, false);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
+  if (st != SBCI_OK) return st;
+  CK(e);
+  CK(cudaGraphInstantiate(&s.gexec[prec], g, 0));
+  s.graph[prec] = g;
+  return SBCI_OK;
+}
+
+bool use_graphs(const sbci_ctx *c) {
+  if (c->prof.on) return false;  // per-kernel event timing needs separate launches
+  const char *e = std::getenv("SBCI_NO_GRAPH");
+  return !(e && e[0] == '1');
+}
+
+// Runs step bodies until the controller halts.
+sbci_status run_until_halt(sbci_ctx *c) {
+  Solver &s = c->s;
+  const int prec = s.h_ctl->prec;
+  if (use_graphs(c)) {
+    if (!s.gexec[prec]) RET(build_graph(c, prec));
+    CK(cudaGraphLaunch(s.gexec[prec], c->stream));
+    RET(ctl_read(c));
+    // kernels the graph ran: four per body
+    const long long bodies = s.h_ctl->iters;
+    Prof &pf = c->prof;
+    pf.launches[K_UPD] += bodies;
+    pf.launches[K_PROJ] += bodies;
+    pf.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
+    pf.launches[K_SC] += bodies;
+    s.h_ctl->iters = 0;
+    CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
+    return SBCI_OK;
+  }
+  for (;;) {  // chunks of bodies; bodies after a halt do no work
+    for (int i = 0; i < 8; ++i) RET(launch_body(c, prec, 0, true));
+    RET(ctl_read(c));
+    if (s.h_ctl->halt) return SBCI_OK;
+  }
+}
+
+// (Re)starts the SB iteration of the current state from x, X with |x| = 1/sx.
+sbci_status start_iteration(sbci_ctx *c, double sx, double E, int stage) {
+  Solver &s = c->s;
+  CtlState &h = *s.h_ctl;
+  h.halt = H_RUN;
+  h.pending_check = 0;
+  h.first = 1;
+  h.sx_pending = 1.0;
+  h.t = 0;
+  h.E = E;
+  h.stage = stage;
+  h.prec = s.p.prec;
+  h.up.sx = sx;
+  h.up.sy = 0.0;
+  h.up.b = 0.0;
+  h.up.c = 0.0;
+  h.up.E = E;
+  h.up.kinv = 1.0;
+  h.up.Epre = shift_for(c, h.alpha, E);
+  h.iters = 0;
+  h.iter_cap = 4 * s.p.max_sigma + 256;
+  h.zc = s.z[0];
+  h.Zc = s.Z[0];
+  h.zn = s.z[1];
+  h.Zn = s.Z[1];
+  return ctl_write(c);
+}
+
+sbci_status start_state(sbci_ctx *c, int alpha, double E0) {
+  Solver &s = c->s;
+  CtlState &h = *s.h_ctl;
+  h.alpha = alpha;
+  h.Ec0 = alpha > 0 ? s.Ec[0] : 0.0;
+  h.n_sigma = h.n_sigma_fp64 = h.n_step = h.n_stage1 = 0;
+  for (int i = 0; i < 4; ++i) h.n_restart[i] = 0;
+  s.verified = 0;
+  return start_iteration(c, 1.0, E0, s.p.prec == SBCI_FP64 ? 1 : 0);
+}
+
+// X <- H x in FP64; returns x.x, x.X and X.X.
+sbci_status resync(sbci_ctx *c, double *xx, double *xX, double *XX) {
+  Solver &s = c->s;
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(gen_dots(c, {s.x, s.x, s.X}, {s.x, s.X, s.X}));
+  *xx = c->h_result[S_GEN0];
+  *xX = c->h_result[S_GEN0 + 1];
+  *XX = c->h_result[S_GEN0 + 2];
+  s.h_ctl->n_sigma += 1;
+  s.h_ctl->n_sigma_fp64 += 1;
+  return SBCI_OK;
+}
+
+sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residual) {
+  Solver &s = c->s;
+  CtlState &h = *s.h_ctl;
+  const int alpha = h.alpha;
+  const double nx = std::sqrt(h.dots[S_NXX]);
+  double *xca = s.xc + (size_t)alpha * c->ndet;
   RET(lincomb(c, xca, {s.x}, {1.0 / nx}));
-  s.Ec.push_back(s.E);
-  sbci_report &r = s.rep[s.alpha];
-  r.energy = s.E + c->e_core;
-  r.residual = std::sqrt(s.dots[S_ZPZP]);
+  s.Ec.push_back(E);
+  sbci_report &r = s.rep[alpha];
+  r.energy = E + c->e_core;
+  r.residual = residual;
   r.converged = converged ? 1 : 0;
+  r.n_sigma = h.n_sigma;
+  r.n_sigma_fp64 = h.n_sigma_fp64;
+  r.n_step = h.n_step;
+  for (int i = 0; i < 4; ++i) r.n_restart[i] = h.n_restart[i];
   if (!converged) s.any_unconverged = 1;
-  if (s.alpha + 1 >= s.k) {
+  if (alpha + 1 >= s.k) {
     s.done = true;
     return SBCI_OK;
   }
   // next state's start: second Ritz vector of the last subspace (S1.4)
-  const int prev = s.cur ^ 1;  // z_t, Z_t of the step that ended the state
-  RET(lincomb(c, s.x, {s.x, s.y, s.z[prev]}, {o->r[0], o->r[1], o->r[2]}));
-  RET(lincomb(c, s.X, {s.X, s.Y, s.Z[prev]}, {o->r[0], o->r[1], o->r[2]}));
+  const double *r3 = h.second;
+  RET(lincomb(c, s.x, {s.x, s.y, h.zc}, {r3[0], r3[1], r3[2]}));
+  RET(lincomb(c, s.X, {s.X, s.Y, h.Zc}, {r3[0], r3[1], r3[2]}));
   // Eqs. S4-S7: project against every stored state, X via H x_c = E_c x_c
   std::vector<const double *> u, v;
-  for (int i = 0; i <= s.alpha; ++i) {
+  for (int i = 0; i <= alpha; ++i) {
     u.push_back(s.xc + (size_t)i * c->ndet);
     v.push_back(s.x);
   }
   RET(gen_dots(c, u, v));
-  std::vector<double> ov(s.alpha + 1);
-  for (int i = 0; i <= s.alpha; ++i) ov[i] = c->h_result[S_GEN0 + i];
-  for (int i = 0; i <= s.alpha; ++i) {
+  std::vector<double> ov(alpha + 1);
+  for (int i = 0; i <= alpha; ++i) ov[i] = c->h_result[S_GEN0 + i];
+  for (int i = 0; i <= alpha; ++i) {
     const double *xci = s.xc + (size_t)i * c->ndet;
     RET(lincomb(c, s.x, {s.x, xci}, {1.0, -ov[i]}));
     RET(lincomb(c, s.X, {s.X, xci}, {1.0, -s.Ec[i] * ov[i]}));
@@ -509,19 +526,64 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, const StepOut *o) {
   }
   RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
   RET(lincomb(c, s.X, {s.X}, {1.0 / nrm}));
-  s.E = o->E2;
-  s.alpha += 1;
-  s.prec = s.p.prec;
-  return start_state(c);
+  return start_state(c, alpha + 1, h.E2);
+}
+
+// Acts on a halted controller.
+sbci_status handle_halt(sbci_ctx *c) {
+  Solver &s = c->s;
+  CtlState &h = *s.h_ctl;
+  switch (h.halt) {
+    case H_RUN:
+      return SBCI_OK;
+    case H_NUMERIC:
+      set_error("non-finite values in the SB step");
+      return SBCI_ERR_NUMERIC;
+    case H_SWITCH: {  // end of the low-precision stage: exact H-image, then stage 1
+      double xx, xX, XX;
+      RET(resync(c, &xx, &xX, &XX));
+      return start_iteration(c, 1.0 / std::sqrt(xx), xX / xx, 1);
+    }
+    case H_CAP:
+      s.h_ctl->halt = H_RUN;
+      set_error("state reached its H-product cap without converging");
+      RET(finalize_state(c, false, h.E, std::sqrt(h.dots[S_ZPZP])));
+      return SBCI_ERR_NOT_CONVERGED;
+    case H_CONVERGED: {
+      if (s.p.prec == SBCI_FP64)
+        return finalize_state(c, true, h.E, std::sqrt(h.dots[S_ZPZP]));
+      // FP64 residual check of the low-precision result: exact X = H x,
+      // Rayleigh quotient and |H x - E x| / |x|
+      double xx, xX, XX;
+      RET(resync(c, &xx, &xX, &XX));
+      const double Erq = xX / xx;
+      const double r = std::sqrt(std::max(XX / xx - Erq * Erq, 0.0));
+      if (r < s.p.r0 && std::fabs(Erq - h.E) < s.p.eps0) return finalize_state(c, true, Erq, r);
+      return start_iteration(c, 1.0 / std::sqrt(xx), Erq, 1);
+    }
+  }
+  return SBCI_OK;
 }
 
 void free_solver(sbci_ctx *c) {
   Solver &s = c->s;
+  for (int i = 0; i < 4; ++i) {
+    if (s.gexec[i]) cudaGraphExecDestroy(s.gexec[i]);
+    if (s.graph[i]) cudaGraphDestroy(s.graph[i]);
+    s.gexec[i] = nullptr;
+    s.graph[i] = nullptr;
+  }
   double **ptrs[] = {&s.x, &s.X, &s.y, &s.Y, &s.w, &s.z[0], &s.z[1], &s.Z[0], &s.Z[1], &s.xc};
   for (double **p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  if (s.d_ctl) cudaFree(s.d_ctl);
+  if (s.h_ctl) cudaFreeHost(s.h_ctl);
+  if (s.d_counters) cudaFree(s.d_counters);
+  s.d_ctl = nullptr;
+  s.h_ctl = nullptr;
+  s.d_counters = nullptr;
   s.active = false;
 }
 
@@ -535,11 +597,16 @@ sbci_status alloc_solver(sbci_ctx *c, int k) {
   }
   RET(dmalloc(&s.xc, (size_t)k * c->ndet));
   CK(cudaMemsetAsync(s.xc, 0, sizeof(double) * (size_t)k * c->ndet, c->stream));
+  CK(cudaMalloc((void **)&s.d_ctl, sizeof(CtlState)));
+  CK(cudaMemsetAsync(s.d_ctl, 0, sizeof(CtlState), c->stream));
+  CK(cudaMallocHost((void **)&s.h_ctl, sizeof(CtlState)));
+  std::memset(s.h_ctl, 0, sizeof(CtlState));
+  CK(cudaMalloc((void **)&s.d_counters, 4 * sizeof(unsigned int)));
+  CK(cudaMemsetAsync(s.d_counters, 0, 4 * sizeof(unsigned int), c->stream));
   return SBCI_OK;
 }
-
 // S1.1: lowest-diagonal determinants -> GS -> H in the subspace -> x_0, X_0, E_0.
-sbci_status initial_guess(sbci_ctx *c, int k) {
+sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   Solver &s = c->s;
   const int n_init = s.p.n_init > 0 ? s.p.n_init : std::max(k, 2);
   std::vector<double> D(c->ndet);
@@ -637,11 +704,11 @@ sbci_status initial_guess(sbci_ctx *c, int k) {
   RET(lincomb(c, s.X, in, co));
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaFree(tmp));
-  s.E = w[0];
+  *E0 = w[0];
   return SBCI_OK;
 }
 
-sbci_status init_from_vector(sbci_ctx *c, const double *c0) {
+sbci_status init_from_vector(sbci_ctx *c, const double *c0, double *E0) {
   Solver &s = c->s;
   std::vector<double> v(c0, c0 + c->ndet);
   RET(check_finite(v.data(), v.size(), "c0"));
@@ -663,11 +730,55 @@ sbci_status init_from_vector(sbci_ctx *c, const double *c0) {
   RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
   RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
   RET(gen_dots(c, {s.x}, {s.X}));
-  s.E = c->h_result[S_GEN0];
+  *E0 = c->h_result[S_GEN0];
   return SBCI_OK;
 }
 
 }  // namespace
+
+// Asynchronous rounds of a solve, for the serving layer: launch the graph loop
+// on the context stream (no wait), then, once the stream has passed it, read
+// the controller and act on the halt.
+sbci_status sbci::solve_round_launch(sbci_ctx *c) {
+  Solver &s = c->s;
+  if (!s.active || s.done) return SBCI_ERR_INVALID;
+  const int prec = s.h_ctl->prec;
+  if (!s.gexec[prec]) RET(build_graph(c, prec));
+  CK(cudaGraphLaunch(s.gexec[prec], c->stream));
+  return SBCI_OK;
+}
+
+sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done) {
+  Solver &s = c->s;
+  RET(ctl_read(c));
+  const long long bodies = s.h_ctl->iters;
+  const int prec = s.h_ctl->prec;
+  c->prof.launches[K_UPD] += bodies;
+  c->prof.launches[K_PROJ] += bodies;
+  c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
+  c->prof.launches[K_SC] += bodies;
+  s.h_ctl->iters = 0;
+  CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
+  const sbci_status st = handle_halt(c);
+  *done = s.done ? 1 : 0;
+  return st;
+}
+
+cudaStream_t sbci::ctx_stream(const sbci_ctx *c) { return c->stream; }
+
+size_t sbci::ctx_device_bytes(int norb, int nalpha, int nbeta, int k) {
+  auto binom = [](int n, int r) {
+    long long v = 1;
+    for (int i = 1; i <= r; ++i) v = v * (n - r + i) / i;
+    return v;
+  };
+  const long long na = binom(norb, nalpha), nb = binom(norb, nbeta), nd = na * nb;
+  const long long npair = norb * (norb + 1) / 2;
+  const long long vec = (9LL + k) * nd * 8;     // x X y Y w z0 z1 Z0 Z1 + stored states
+  const long long G = npair * nd * 8;            // sigma scratch (FP64 size, shared by FP32 modes)
+  const long long tab = (na * nalpha * (norb - nalpha + 1) + nb * nbeta * (norb - nbeta + 1)) * 4;
+  return (size_t)(vec + G + tab + nd * 8 + (1 << 20));
+}
 
 bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream) {
   if (!c) return false;
@@ -817,8 +928,9 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   };
   TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
   TRY(cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"));
-  c->grid = 4 * std::max(nsm, 1);
   c->nsm = std::max(nsm, 1);
+  c->grid = 8 * c->nsm;  // upper bound of every kernel's block count that writes partials
+  TRY(cuda_ok(prepare_sigma_kernels(), "kernel attributes"));
   // packed operator W[P][Q], P = (i>=j), Q = (k>=l):
   //   W = 1/2 (ij|kl) + (k_ij d_kl + d_ij k_kl) / (2N),  k_ij = h_ij - 1/2 sum_m (im|mj)
   const int N = nalpha + nbeta;
@@ -886,6 +998,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   *c->h_status = 0;
   TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
+  c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
   TRY(cuda_ok(launch_diagonal(c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_mask_b, c->Na, c->Nb, n,
                               c->stream), "diagonal kernel"));
   TRY(cuda_ok(cudaStreamSynchronize(c->stream), "sync"));
@@ -998,19 +1111,35 @@ sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const doub
     return SBCI_ERR_INVALID;
   }
   RET(alloc_solver(c, k));
+  RET(ensure_G(c, SBCI_FP64));
+  if (s.p.prec != SBCI_FP64) RET(ensure_G(c, s.p.prec));
   s.k = k;
-  s.alpha = 0;
   s.done = false;
-  s.cur = 0;
-  s.prec = s.p.prec;
   s.Ec.clear();
   s.trace.clear();
   s.rep.assign(k, sbci_report{});
   s.any_unconverged = 0;
   s.active = true;
-  if (s.p.init == 1) RET(init_from_vector(c, c0));
-  else RET(initial_guess(c, k));
-  return start_state(c);
+  CtlState &h = *s.h_ctl;
+  h.p.eps0 = s.p.eps0;
+  h.p.r0 = s.p.r0;
+  h.p.b_th = s.p.b_th;
+  h.p.eps1 = s.p.eps1;
+  h.p.x_th1 = s.p.x_th1;
+  h.p.x_th2 = s.p.x_th2;
+  h.p.r1 = s.p.r1;
+  h.p.guard = s.p.guard;
+  h.p.gs_tol = s.p.gs_tol;
+  h.p.mixed_eps = s.p.mixed_eps;
+  h.p.mixed_r = s.p.mixed_r;
+  h.p.max_cycle = s.p.max_cycle;
+  h.p.max_sigma = s.p.max_sigma;
+  h.p.refine_max_sigma = s.p.refine_max_sigma;
+  h.p.user_prec = s.p.prec;
+  double E0 = 0.0;
+  if (s.p.init == 1) RET(init_from_vector(c, c0, &E0));
+  else RET(initial_guess(c, k, &E0));
+  return start_state(c, 0, E0);
 }
 
 sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
@@ -1021,80 +1150,19 @@ sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
   Solver &s = c->s;
   if (done) *done = s.done ? 1 : 0;
   if (s.done) return SBCI_OK;
-  std::memcpy(s.dots, c->h_result, sizeof(s.dots));
-  sbci_report &r = s.rep[s.alpha];
-  StepOut o{};
-  if (s.first) first_step(s, o);
-  else later_step(s, o);
-  if (!std::isfinite(o.E) || !std::isfinite(o.k) || !std::isfinite(o.b) || !std::isfinite(o.c)) {
-    set_error("non-finite SB parameters");
-    return SBCI_ERR_NUMERIC;
-  }
-  const double Eold = s.E;
-  const int t_now = s.t;
-  r.n_sigma += 1;
-  if (s.prec == SBCI_FP64) r.n_sigma_fp64 += 1;
-  r.n_step += 1;
-  s.E = o.E;
-  RET(advance(c, o.sx, o.sy, o.b, o.c, o.E, 1.0 / o.k, Epre_of(c)));
-  s.first = false;
-  std::memcpy(s.dots, c->h_result, sizeof(s.dots));
-  const double dz = std::sqrt(s.dots[S_ZPZP]);
-  const double dE = std::fabs(o.E - Eold);
-  sbci_trace_record tr{};
-  tr.state = s.alpha;
-  tr.t = t_now;
-  tr.energy = o.E;
-  tr.b = o.b;
-  tr.c = o.c;
-  tr.k = o.k;
-  tr.dE = dE;
-  tr.dz = dz;
-  tr.prec = s.prec;
+  const size_t n0 = s.trace.size();
   sbci_status ret = SBCI_OK;
-  const bool low = (tr.prec != SBCI_FP64);
-  if (low && ((dE < s.p.mixed_eps && dz < s.p.mixed_r) || r.n_sigma >= s.p.max_sigma / 2)) {
-    // the low-precision stage has done its part: refine in FP64
-    tr.event = 6;
-    s.trace.push_back(tr);
-    if (rec) *rec = tr;
-    RET(switch_to_fp64(c));
-  } else if (!low && dE < s.p.eps0 && dz < s.p.r0) {  // Eq. S61
-    tr.event = 1;
-    s.trace.push_back(tr);
-    if (rec) *rec = tr;
-    RET(finalize_state(c, true, &o));
-  } else {
-    int cause = 0;  // S62a, S62b, S62c, max_cycle
-    if (s.alpha > 0 && std::fabs(o.b) < s.p.b_th && dE < s.p.eps1) cause = 1;
-    else if (std::fabs(o.k) < s.p.x_th1 || std::fabs(o.k) > s.p.x_th2) cause = 2;
-    else if (dz > s.p.r1 && t_now > 0) cause = 3;
-    else if (t_now + 1 >= s.p.max_cycle) cause = 4;
-    tr.event = cause ? cause + 1 : 0;
-    s.trace.push_back(tr);
-    if (rec) *rec = tr;
-    if (cause) {
-      r.n_restart[cause - 1] += 1;
-      s.first = true;
-      s.sx_pending = 1.0 / std::sqrt(s.dots[S_NXX]);
-      s.t = 0;
-    } else {
-      s.t += 1;
-      // Gram-Schmidt breakdown of y (y inside span{x}): take the first-step path
-      const double gy = s.dots[S_NYY] - s.dots[S_NXY] * s.dots[S_NXY] / s.dots[S_NXX];
-      if (gy < s.p.gs_tol * s.dots[S_NYY]) {
-        s.first = true;
-        s.sx_pending = 1.0 / std::sqrt(s.dots[S_NXX]);
-        s.t = 0;
-      }
-    }
-    if (r.n_sigma >= s.p.max_sigma ||
-        (s.p.prec != SBCI_FP64 && r.n_sigma_fp64 >= s.p.refine_max_sigma)) {
-      ret = SBCI_ERR_NOT_CONVERGED;
-      set_error("state reached max_sigma without converging");
-      RET(finalize_state(c, false, &o));
+  // bodies until one SB step has been recorded (the first body after a
+  // (re)start only prepares the first subspace solve)
+  for (int guard = 0; guard < 4 && s.trace.size() == n0 && !s.done; ++guard) {
+    RET(launch_body(c, s.h_ctl->prec, 0, true));
+    RET(ctl_read(c));
+    if (s.h_ctl->halt) {
+      ret = handle_halt(c);
+      if (ret != SBCI_OK && ret != SBCI_ERR_NOT_CONVERGED) return ret;
     }
   }
+  if (rec && s.trace.size() > n0) *rec = s.trace.back();
   if (done) *done = s.done ? 1 : 0;
   return ret;
 }
@@ -1124,9 +1192,10 @@ sbci_status sbci_finish(sbci_ctx *c, double *energies, double *vecs, sbci_report
 sbci_status sbci_solve(sbci_ctx *c, int k, const sbci_params *params, const double *c0,
                        double *energies, double *vecs, sbci_report *rep) {
   RET(sbci_begin(c, k, params, c0));
-  int done = 0;
-  while (!done) {
-    sbci_status st = sbci_step(c, nullptr, &done);
+  Solver &s = c->s;
+  while (!s.done) {
+    RET(run_until_halt(c));
+    const sbci_status st = handle_halt(c);
     if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
   }
   return sbci_finish(c, energies, vecs, rep);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ctl.h"
 #include "sbci_internal.h"
 
 namespace sbci {
@@ -113,6 +114,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int npair = a.npair;
+  const double *cin = a.c;
+  if (a.ctl) {
+    if (a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
+    cin = a.ctl->zn;
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -156,18 +162,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (valid) {
       const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
       const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-      for (int e = 0; e < a.nlink_a; ++e) {
-        const uint32_t v = __ldg(la + e);
-        const float cv = (float)__ldg(a.c + (size_t)link_J(v) * a.nb + ib);
-        A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -cv : cv;
-      }
+      const double *ccol = cin + ib;
+      for_links<8, double>(
+          la, a.nlink_a, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+          [&](uint32_t v, double cv) {
+            const float f = (float)cv;
+            A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
       const uint32_t *lb = a.link_b + (size_t)ib * a.nlink_b;
-      const double *crow = a.c + (size_t)ia * a.nb;
-      for (int e = 0; e < a.nlink_b; ++e) {
-        const uint32_t v = __ldg(lb + e);
-        const float cv = (float)__ldg(crow + link_J(v));
-        A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -cv : cv;
-      }
+      const double *crow = cin + (size_t)ia * a.nb;
+      for_links<8, double>(
+          lb, a.nlink_b, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+          [&](uint32_t v, double cv) {
+            const float f = (float)cv;
+            A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
     }
     // 2. split in place: A <- tf32(D), Alo <- tf32(D - tf32(D))
     for (int q = 0; q < Kp; q += 4) {
@@ -249,24 +258,35 @@ bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
   return np <= 256 && bytes <= 227 * 1024;
 }
 
-cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int num_sms, cudaStream_t s) {
+// Grid of the persistent tensor-core kernel (resident CTAs, capped by TMEM
+// columns), computed outside any stream capture.  0 if the shape is unsupported.
+int tc_grid(int npair, long long ndet, int num_sms) {
   int Kp, Np;
   uint32_t cols;
   size_t smem;
-  if (!tc_dims(a.npair, &Kp, &Np, &cols, &smem)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
+  if (!tc_dims(npair, &Kp, &Np, &cols, &smem)) return 0;
+  if (cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem);
-  if (e != cudaSuccess) return e;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem) !=
+      cudaSuccess)
+    return 0;
   if (per_sm < 1) per_sm = 1;
   if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
-  const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
+  const long long ntiles = (ndet + kTcM - 1) / kTcM;
   long long grid = (long long)num_sms * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  k_gather_contract_tc<<<(int)grid, kTcThreads, smem, s>>>(a, Kp, Np, cols, status);
+  return (int)grid;
+}
+
+cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!tc_dims(a.npair, &Kp, &Np, &cols, &smem) || grid < 1) return cudaErrorInvalidValue;
+  k_gather_contract_tc<<<grid, kTcThreads, smem, s>>>(a, Kp, Np, cols, status);
   return cudaGetLastError();
 }
 

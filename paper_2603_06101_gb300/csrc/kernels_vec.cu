@@ -1,7 +1,6 @@
-// FP64 vector kernels of the SBCI1 step: the fused symplectic-Euler update
-// sweep (Eqs. 10-11 with the H-image recurrences S56-S59, the residual S60
-// and the preconditioner of Eqs. 6-7), the projection against the stored
-// states (Eq. S31), the diagonal of H, and deterministic reductions.
+// FP64 helper kernels: linear combinations and dot products for the rare
+// host-driven events (initial guess, state transitions), the diagonal of H,
+// and deterministic reductions.
 //
 // Every dot product is reduced in two fixed-order stages (block partials,
 // then one pass per slot), so results do not depend on scheduling.
@@ -36,78 +35,6 @@ __device__ __forceinline__ void block_store(double (&v)[NV], const int *slots, d
     for (int i = 0; i < kVecThreads / 32; ++i) s += red[j][i];
     if (slots[j] >= 0) partials[(size_t)slots[j] * grid + blockIdx.x] = s;
   }
-}
-
-__device__ __forceinline__ double guarded(double d, double g) {
-  if (fabs(d) < g) return d < 0.0 ? -g : g;
-  return d;
-}
-
-// y <- sy*y - c*z ; Y <- sy*Y - c*Z ; x <- sx*x + b*y ; X <- sx*X + b*Y
-// z' = (X - E x) * kinv ; w = z' / guarded(D - Epre)
-// dots: Nxx Nxy Nyy Hxx Hxy Hyy |z'|^2 [Nxw Nyw Nww] [x_c^i . w]
-__global__ void __launch_bounds__(kVecThreads) k_update(UpdateArgs a) {
-  constexpr int NV = 10 + kMaxStates;
-  double acc[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const double zi = a.z[i], Zi = a.Z[i];
-    const double y = a.sy * a.y[i] - a.c * zi;
-    const double Y = a.sy * a.Y[i] - a.c * Zi;
-    const double x = a.sx * a.x[i] + a.b * y;
-    const double X = a.sx * a.X[i] + a.b * Y;
-    a.y[i] = y;
-    a.Y[i] = Y;
-    a.x[i] = x;
-    a.X[i] = X;
-    const double zp = (X - a.E * x) * a.kinv;
-    const double w = zp / guarded(a.diag[i] - a.Epre, a.guard);
-    a.w[i] = w;
-    acc[0] += x * x;
-    acc[1] += x * y;
-    acc[2] += y * y;
-    acc[3] += x * X;
-    acc[4] += x * Y;
-    acc[5] += y * Y;
-    acc[6] += zp * zp;
-    if (a.w_is_z) {
-      acc[7] += x * w;
-      acc[8] += y * w;
-      acc[9] += w * w;
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxStates; ++j)
-      if (j < a.nxc) acc[10 + j] += a.xc[j][i] * w;
-  }
-  int slots[NV];
-  for (int j = 0; j < 7; ++j) slots[j] = S_NXX + j;
-  for (int j = 7; j < 10; ++j) slots[j] = a.w_is_z ? (S_NXZ + j - 7) : -1;
-  for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < a.nxc) ? S_XCW0 + j : -1;
-  block_store<NV>(acc, slots, a.partials, a.grid);
-}
-
-// z = sym(w) - sum_i coef_i x_c^i ; dots Nxz Nyz Nzz.
-__global__ void __launch_bounds__(kVecThreads) k_project(ProjectArgs a) {
-  double acc[3] = {0.0, 0.0, 0.0};
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    double v = a.w[i];
-    if (a.sector) {
-      const int ia = (int)(i / a.nb), ib = (int)(i - (long long)ia * a.nb);
-      v = 0.5 * (v + a.w[(size_t)ib * a.nb + ia]);
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxStates; ++j)
-      if (j < a.nxc) v -= __ldg(a.coef + j) * a.xc[j][i];
-    a.z[i] = v;
-    acc[0] += a.x[i] * v;
-    acc[1] += a.y[i] * v;
-    acc[2] += v * v;
-  }
-  const int slots[3] = {S_NXZ, S_NYZ, S_NZZ};
-  block_store<3>(acc, slots, a.partials, a.grid);
 }
 
 struct LinComb {
@@ -197,16 +124,6 @@ static int grid_for(long long n, int cap) {
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
-}
-
-cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s) {
-  k_update<<<a.grid, kVecThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s) {
-  k_project<<<a.grid, kVecThreads, 0, s>>>(a);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_lincomb(double *out, const double *const *in, const double *coef, int nin,

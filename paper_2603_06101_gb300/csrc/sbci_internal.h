@@ -8,7 +8,11 @@
 #include <string>
 #include <vector>
 
+#include "../../include/sbci.h"
+
 namespace sbci {
+
+struct CtlState;
 
 // ---------------------------------------------------------------------------
 // Packed excitation-table entry.  For string I, entry e encodes
@@ -22,6 +26,30 @@ constexpr uint32_t kSignBit = 1u << 31;
 __host__ __device__ inline int link_J(uint32_t v) { return (int)(v & kJMask); }
 __host__ __device__ inline int link_pair(uint32_t v) { return (int)((v >> kPairShift) & kPairMask); }
 __host__ __device__ inline bool link_neg(uint32_t v) { return (v & kSignBit) != 0u; }
+
+#ifdef __CUDACC__
+// Visits the links of one string U at a time: the U list entries, then the U
+// gathered values (independent loads, all in flight), then the U updates.
+// load(v) returns the gathered value of link word v; use(v, x) consumes it.
+template <int U, typename T, typename Load, typename Use>
+__device__ __forceinline__ void for_links(const uint32_t *lst, int n, Load load, Use use) {
+  int e = 0;
+  for (; e + U <= n; e += U) {
+    uint32_t v[U];
+    T x[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) v[j] = __ldg(lst + e + j);
+#pragma unroll
+    for (int j = 0; j < U; ++j) x[j] = load(v[j]);
+#pragma unroll
+    for (int j = 0; j < U; ++j) use(v[j], x[j]);
+  }
+  for (; e < n; ++e) {
+    const uint32_t v = __ldg(lst + e);
+    use(v, load(v));
+  }
+}
+#endif
 
 constexpr int kMaxOrb = 16;
 constexpr int kMaxPair = kMaxOrb * (kMaxOrb + 1) / 2;  // 136
@@ -61,48 +89,27 @@ struct SigmaArgs {
   int dot_slot[3];
   double *partials;      // [S_COUNT][grid]
   int grid;
+  // device-controlled mode (ctl != nullptr): input z and output Z come from the
+  // controller, the scatter's dots are against (dot_u[0], dot_u[1], ctl->zn),
+  // and its last block runs the subspace solve
+  struct CtlState *ctl;
+  unsigned int *counter;       // last-block counter of the scatter
+  unsigned long long cond;     // graph while-loop handle (0: none)
 };
 
 // Launchers (kernels_sigma.cu)
 // prec: 0 = FP64 scratch and contraction, 1 = FP32 (SIMT) contraction
 cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
+int scatter_grid(long long ndet, int nsm);
+cudaError_t prepare_sigma_kernels();
 // tcgen05 TF32x3 gather + contract (kernels_tc.cu); writes FP32 G like prec 1.
 bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
-cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int num_sms, cudaStream_t s);
+int tc_grid(int npair, long long ndet, int num_sms);
+cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
-// Vector kernels (kernels_vec.cu)
-struct UpdateArgs {
-  double *x, *X, *y, *Y;
-  const double *z, *Z;
-  double *w;              // out: next preconditioned residual (z' / guarded(D - Epre))
-  const double *diag;
-  long long n;
-  double sx, sy, b, c, E, kinv, Epre, guard;
-  int w_is_z;             // 1: w is used directly as the next z (slots NXZ.. from w)
-  const double *xc[kMaxStates];
-  int nxc;                // number of x_c dots (x_c^i . w) to produce
-  double *partials;
-  int grid;
-};
-cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s);
-
-struct ProjectArgs {
-  const double *w;
-  double *z;
-  const double *x, *y;
-  const double *xc[kMaxStates];
-  const double *coef;     // device [nxc]: z = sym(w) - sum coef_i x_c^i
-  int nxc;
-  int sector;             // 1: symmetrise w over the Ia <-> Ib swap
-  int na, nb;
-  long long n;
-  double *partials;
-  int grid;
-};
-cudaError_t launch_project(const ProjectArgs &a, cudaStream_t s);
-
+// Helper kernels (kernels_vec.cu)
 // out = sum_i coef_i in_i (out may alias in[0]); up to 8 inputs.
 cudaError_t launch_lincomb(double *out, const double *const *in, const double *coef, int nin,
                            long long n, cudaStream_t s);
@@ -131,5 +138,10 @@ namespace sbci {
 // Fills the sigma arguments of a context without allocating anything (G and
 // the dot outputs are left null).  Returns false on a null context.
 bool ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream);
+// Serving support (api.cpp): asynchronous rounds of an active solve.
+sbci_status solve_round_launch(sbci_ctx *c);
+sbci_status solve_round_finish(sbci_ctx *c, int *done);
+cudaStream_t ctx_stream(const sbci_ctx *c);
+size_t ctx_device_bytes(int norb, int nalpha, int nbeta, int k);
 
 }  // namespace sbci

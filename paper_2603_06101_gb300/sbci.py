@@ -69,7 +69,8 @@ _lib = None
 EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_table",
            "sbci_diagonal", "sbci_sigma", "sbci_begin", "sbci_step", "sbci_finish", "sbci_solve",
            "sbci_trace", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
-           "sbci_last_error", "sbci_destroy"]
+           "sbci_server_create", "sbci_server_submit", "sbci_server_progress", "sbci_server_poll",
+           "sbci_server_destroy", "sbci_last_error", "sbci_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -95,6 +96,12 @@ def load(path: str = LIB_PATH):
     lib.sbci_solve.argtypes = [P, I, C.POINTER(sbci_params), P, P, P, P]
     lib.sbci_trace.argtypes = [P, C.POINTER(sbci_trace_record), I, C.POINTER(I)]
     lib.sbci_sigma_noalloc.argtypes = [P, P, P, P]
+    lib.sbci_server_create.argtypes = [C.POINTER(P), C.c_size_t, I]
+    lib.sbci_server_submit.argtypes = [P, I, I, I, P, P, D, I, C.POINTER(sbci_params), C.POINTER(LL)]
+    lib.sbci_server_progress.argtypes = [P, C.POINTER(I), C.POINTER(I)]
+    lib.sbci_server_poll.argtypes = [P, LL, C.POINTER(I), P, P, P]
+    lib.sbci_server_destroy.argtypes = [P]
+    lib.sbci_server_destroy.restype = None
     lib.sbci_profile.argtypes = [P, I]
     lib.sbci_profile_read.argtypes = [P, C.POINTER(sbci_kernel_stat), I, C.POINTER(I)]
     lib.sbci_last_error.restype = C.c_char_p
@@ -102,7 +109,7 @@ def load(path: str = LIB_PATH):
     lib.sbci_destroy.argtypes = [P]
     lib.sbci_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("sbci_last_error", "sbci_destroy"):
+        if name not in ("sbci_last_error", "sbci_destroy", "sbci_server_destroy"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -271,3 +278,55 @@ class Context:
         buf = (sbci_trace_record * max(n.value, 1))()
         _check(self._lib.sbci_trace(self._h, buf, n.value, C.byref(n)))
         return list(buf)[: n.value]
+
+
+class Server:
+    """Continuous-batching request loop (sbci_server_*), one host thread."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int):
+        lib = load()
+        self._lib = lib
+        self._h = C.c_void_p()
+        _check(lib.sbci_server_create(C.byref(self._h), C.c_size_t(int(mem_budget_bytes)), int(max_slots)))
+        self._k = {}
+
+    def submit(self, I, k: int, p: sbci_params | None = None) -> int:
+        h1 = np.ascontiguousarray(I.h1, dtype=np.float64)
+        eri = np.ascontiguousarray(I.eri, dtype=np.float64)
+        t = C.c_longlong()
+        _check(self._lib.sbci_server_submit(self._h, I.norb, I.nalpha, I.nbeta,
+                                            h1.ctypes.data_as(C.c_void_p), eri.ctypes.data_as(C.c_void_p),
+                                            float(I.e_core), int(k), C.byref(p) if p is not None else None,
+                                            C.byref(t)))
+        self._k[t.value] = k
+        return t.value
+
+    def progress(self):
+        a, q = C.c_int(), C.c_int()
+        _check(self._lib.sbci_server_progress(self._h, C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def poll(self, ticket: int):
+        """None while running, else (energies, reports, (queue_s, latency_s), status)."""
+        k = self._k[ticket]
+        done = C.c_int()
+        E = np.zeros(k)
+        R = (sbci_report * k)()
+        T = np.zeros(2)
+        st = self._lib.sbci_server_poll(self._h, C.c_longlong(ticket), C.byref(done),
+                                        E.ctypes.data_as(C.c_void_p), R, T.ctypes.data_as(C.c_void_p))
+        if not done.value:
+            _check(st)
+            return None
+        return E, list(R), (float(T[0]), float(T[1])), st
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.sbci_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
