@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--sigma-only", default=None, choices=["h10", "h12", "n14", "n16"],
                     help="only run sigma products of one workload (for ncu captures)")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serving", action="store_true",
+                    help="serving stream: batched mixed precision vs sequential FP64, p50/p99")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=16)
     return ap.parse_args()
 
 
@@ -385,8 +389,103 @@ def run_ncu_solve(args):
                       "sigma": sum(r.n_sigma for r in R)}))
 
 
+def run_serving(args):
+    """Serving stream over H6/H8/H10/H12 chains (1-4 states, spacing 0.7-3.0 A).
+
+    1. saturation run of the batched mixed-precision server (all arrivals at
+       t = 0) -> capacity;  2. Poisson arrivals at 0.7 x capacity through the
+    server -> p50/p99 latency;  3. the same Poisson trace served by plain FP64
+    one solve at a time (each solve alone, in arrival order) -> p50/p99 and
+    solves/s.  Latency = completion - arrival.
+    """
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    n = args.requests
+    base = inputs.serving_trace(n, seed=4, rate_per_s=float("inf"))
+    ints = [inputs.h_chain(r.natoms, r.spacing_angstrom) for r in base]
+    ks = [r.nstates for r in base]
+    # a seeded full-symmetry component in every start (start_noise): symmetric
+    # chains would otherwise let rounding decide which symmetry a state search
+    # explores, and the two precisions could meet different states
+    p_mixed = sbci.params(prec=sbci.SBCI_TF32X3, start_noise=1e-2, noise_seed=2603)
+    p_fp64 = sbci.params(prec=sbci.SBCI_FP64, start_noise=1e-2, noise_seed=2603)
+    budget = 64 << 30
+
+    def serve(arrivals, p, slots):
+        server = sbci.Server(budget, slots)
+        t0 = time.perf_counter()
+        tickets, done, lat = {}, {}, {}
+        order = np.argsort(arrivals, kind="stable")
+        nxt = 0
+        while len(done) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[order[nxt]] <= now:
+                i = int(order[nxt])
+                tickets[i] = server.submit(ints[i], ks[i], p)
+                nxt += 1
+            server.progress()
+            for i, t in tickets.items():
+                if i in done:
+                    continue
+                r = server.poll(t)
+                if r is not None:
+                    done[i] = r
+                    lat[i] = (time.perf_counter() - t0) - arrivals[i]
+        makespan = time.perf_counter() - t0
+        server.close()
+        return makespan, np.array([lat[i] for i in range(n)]), done
+
+    # warm-up: one of each size through the server (graph builds, module loads)
+    warm = sbci.Server(budget, 4)
+    for sz in (6, 8, 10, 12):
+        t = warm.submit(inputs.h_chain(sz, 1.0), 1, p_mixed)
+        while warm.poll(t) is None:
+            warm.progress()
+    warm.close()
+    torch.cuda.synchronize()
+    sat_span, sat_lat, _ = serve(np.zeros(n), p_mixed, args.slots)
+    capacity = n / sat_span
+    rate = 0.7 * capacity
+    gaps = np.random.default_rng(4).exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    span_m, lat_m, done_m = serve(arrivals, p_mixed, args.slots)
+    # plain FP64, one solve per launch, in arrival order
+    t0 = time.perf_counter()
+    lat_f = np.zeros(n)
+    E_f = {}
+    for i in np.argsort(arrivals, kind="stable"):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        ctx = sbci.Context.from_integrals(ints[i])
+        E, _, _, st = ctx.solve(ks[i], p_fp64)
+        ctx.close()
+        E_f[int(i)] = E
+        lat_f[i] = (time.perf_counter() - t0) - arrivals[i]
+    span_f = time.perf_counter() - t0
+    err = max(float(np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max()) for i in range(n))
+    err0 = max(float(abs(done_m[i][0][0] - E_f[i][0])) for i in range(n))
+    nbad = sum(1 for i in range(n) if np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max() > 1e-6)
+    line = {
+        "serving": f"{n} requests, H6/H8/H10/H12 STO-3G, spacing U(0.7, 3.0) A, 1-4 states (seed 4)",
+        "saturation_solves_per_s": capacity, "poisson_rate_per_s": rate,
+        "batched_tf32x3": {"solves_per_s": n / span_m, "p50_s": float(np.percentile(lat_m, 50)),
+                           "p99_s": float(np.percentile(lat_m, 99)), "slots": args.slots},
+        "sequential_fp64": {"solves_per_s": n / span_f, "p50_s": float(np.percentile(lat_f, 50)),
+                            "p99_s": float(np.percentile(lat_f, 99))},
+        "max_energy_diff_mixed_vs_fp64_hartree": err, "max_ground_state_diff_hartree": err0,
+        "requests_differing_by_more_than_1e-6": nbad,
+        "sizes": {str(sz): int(sum(1 for r in base if r.natoms == sz)) for sz in (6, 8, 10, 12)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serving:
+        run_serving(args)
+        return
     if args.sigma_only:
         sigma_only(args)
         return

@@ -79,7 +79,16 @@ typedef struct {
                        X by an FP64 H x and continues in FP64 to Eq. S61. */
   double mixed_eps; /* end of the low-precision stage: dE < mixed_eps ... ; 1e-8 */
   double mixed_r;   /* ... and |z'| < mixed_r; 1e-4 */
-  int refine_max_sigma; /* cap on FP64 H-products per state in refinement; 30 */
+  int refine_max_sigma; /* cap on H-products of the refinement stage per state; 300 */
+  double start_noise; /* eta >= 0: every state's start becomes x0/|x0| + eta r/|r| with
+                         r a seeded SplitMix64 vector in [-1,1) (X by one FP64 sigma of
+                         r) and E_0 its Rayleigh quotient, before the projection of Eqs.
+                         S4-S7.  SBCI1 keeps the spatial symmetry of its start; a small
+                         full-symmetry part lets it reach the lowest remaining state in
+                         symmetric molecules.  0 = the paper's starts.  0 */
+  long long noise_seed; /* seed of r: element I of state alpha's vector is the SplitMix64
+                           output of seed + 0x9E3779B97F4A7C15*(alpha*2^40 + I + 1),
+                           top 53 bits mapped to [-1, 1).  0 */
 } sbci_params;
 
 typedef struct {

@@ -36,6 +36,13 @@ R8  Initial determinants: the n_init lowest diagonal elements ordered by
 R9  X_0 of an excited state uses H x_c = E_c x_c (Eq. S5), no extra H-product.
 R10 sector = 1 keeps c = c^T (Ia <-> Ib swap, n_alpha = n_beta): initial
     vectors and every z are symmetrised, z <- (z + z^T)/2.
+R11 start_noise = eta > 0 adds eta * r_alpha / |r_alpha| to the (unit) start
+    vector of every state, r_alpha a seeded SplitMix64 vector (``splitmix_vector``),
+    with X += eta * H r_alpha / |r_alpha| and E_0 = the Rayleigh quotient, before
+    the projection of Eqs. S4-S7.  An SBCI1 search keeps the spatial symmetry
+    of its start vector; the small full-symmetry component lets it reach the
+    lowest state of the orthogonal complement in symmetric molecules.  The
+    default eta = 0 is the paper's choice (S1.1 / S1.4 starts as stated).
 """
 from __future__ import annotations
 
@@ -59,6 +66,8 @@ class SBCIParams:
     gs_tol: float = 1e-14  # S1.1 and R7
     sector: int = 0  # R10
     n_init: int | None = None  # R8
+    start_noise: float = 0.0  # R11
+    noise_seed: int = 0
 
 
 @dataclass
@@ -82,6 +91,24 @@ class StateResult:
     n_sigma: int
     n_step: int
     restarts: dict = field(default_factory=dict)
+
+
+_M64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix_vector(seed: int, alpha: int, n: int) -> np.ndarray:
+    """Counter-based pseudo-random vector in [-1, 1): the SplitMix64 output
+    function (Steele, Lea & Flood 2014; Vigna's splitmix64) applied to
+    seed + GOLDEN * (alpha * 2^40 + I + 1) for I = 0..n-1, top 53 bits -> [0, 1)."""
+    idx = (np.arange(n, dtype=np.uint64) + np.uint64(1)) + np.uint64((alpha << 40) & _M64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _M64) + idx * np.uint64(_GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return 2.0 * u - 1.0
 
 
 def _guarded(d: np.ndarray, guard: float) -> np.ndarray:
@@ -136,6 +163,7 @@ class SBCI1:
         Xm = [self.H(u) for u in basis]
         A = np.array([[u @ Xv for Xv in Xm] for u in basis])
         w, U = np.linalg.eigh(0.5 * (A + A.T))
+        self.init_space = (basis, U, w)
         x0 = sum(U[i, 0] * basis[i] for i in range(len(basis)))
         X0 = sum(U[i, 0] * Xm[i] for i in range(len(basis)))
         return x0, X0, float(w[0])
@@ -290,10 +318,24 @@ class SBCI1:
         sec = (wx * Ax + wy * Bx + wz * Cx, wy * By + wz * Cy, wz * Cz, float(lam[1]))
         return float(lam[0]), float(b), float(c), float(k), sec
 
+    def _mix_noise(self, x0, X0, alpha):
+        """R11: x0 <- x0/|x0| + eta r/|r|, X0 likewise with H r, E0 = RQ."""
+        r = splitmix_vector(self.p.noise_seed, alpha, x0.size)
+        if self.p.sector:
+            r = _sym(r, self.shape)
+        nr = np.linalg.norm(r)
+        R = self.H(r)
+        nx = np.linalg.norm(x0)
+        eta = self.p.start_noise
+        x = x0 / nx + (eta / nr) * r
+        X = X0 / nx + (eta / nr) * R
+        return x, X, float(x @ X) / float(x @ x)
+
     # -- driver ---------------------------------------------------------------
     def solve(self, nstates: int, c0: np.ndarray | None = None):
         """States 0..nstates-1 in sequence (Fig. 1A)."""
         xc, Ec, results = [], [], []
+        self.init_space = None
         if c0 is None:
             x0, X0, E0 = self.initial_guess(nstates)
         else:
@@ -303,6 +345,8 @@ class SBCI1:
             x0 /= np.linalg.norm(x0)
             X0 = self.H(x0)
             E0 = float(x0 @ X0)
+        if self.p.start_noise > 0.0:
+            x0, X0, E0 = self._mix_noise(x0, X0, 0)
         for alpha in range(nstates):
             res, second = self.solve_state(alpha, x0, X0, E0, xc, Ec)
             results.append(res)
@@ -310,4 +354,6 @@ class SBCI1:
             Ec.append(res.energy)
             if alpha + 1 < nstates:
                 x0, X0, E0 = second  # S1.4
+                if self.p.start_noise > 0.0:
+                    x0, X0, E0 = self._mix_noise(x0, X0, alpha + 1)
         return results

@@ -479,6 +479,24 @@ sbci_status resync(sbci_ctx *c, double *xx, double *xX, double *XX) {
   return SBCI_OK;
 }
 
+// Start of state alpha with a seeded full-symmetry component:
+// x <- x/|x| + eta r/|r|, X <- X/|x| + eta (H r)/|r|, E0 = x.X / x.x.
+// y and Y serve as scratch (the next start zeroes them).
+sbci_status mix_noise(sbci_ctx *c, int alpha, double *E0) {
+  Solver &s = c->s;
+  CK(launch_splitmix(s.y, c->ndet, (unsigned long long)s.p.noise_seed, alpha, c->stream));
+  if (s.p.sector) CK(launch_symmetrize(s.y, c->Na, c->stream));
+  RET(run_sigma(c, s.y, s.Y, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(gen_dots(c, {s.y, s.x}, {s.y, s.x}));
+  const double nr = std::sqrt(c->h_result[S_GEN0]), nx = std::sqrt(c->h_result[S_GEN0 + 1]);
+  const double eta = s.p.start_noise;
+  RET(lincomb(c, s.x, {s.x, s.y}, {1.0 / nx, eta / nr}));
+  RET(lincomb(c, s.X, {s.X, s.Y}, {1.0 / nx, eta / nr}));
+  RET(gen_dots(c, {s.x, s.x}, {s.x, s.X}));
+  *E0 = c->h_result[S_GEN0 + 1] / c->h_result[S_GEN0];
+  return SBCI_OK;
+}
+
 sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residual) {
   Solver &s = c->s;
   CtlState &h = *s.h_ctl;
@@ -500,10 +518,12 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residua
     s.done = true;
     return SBCI_OK;
   }
+  double E_next = h.E2;
   // next state's start: second Ritz vector of the last subspace (S1.4)
   const double *r3 = h.second;
   RET(lincomb(c, s.x, {s.x, s.y, h.zc}, {r3[0], r3[1], r3[2]}));
   RET(lincomb(c, s.X, {s.X, s.Y, h.Zc}, {r3[0], r3[1], r3[2]}));
+  if (s.p.start_noise > 0.0) RET(mix_noise(c, alpha + 1, &E_next));
   // Eqs. S4-S7: project against every stored state, X via H x_c = E_c x_c
   std::vector<const double *> u, v;
   for (int i = 0; i <= alpha; ++i) {
@@ -526,7 +546,7 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residua
   }
   RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
   RET(lincomb(c, s.X, {s.X}, {1.0 / nrm}));
-  return start_state(c, alpha + 1, h.E2);
+  return start_state(c, alpha + 1, E_next);
 }
 
 // Acts on a halted controller.
@@ -826,7 +846,9 @@ sbci_status sbci_params_init(sbci_params *p) {
   p->prec = SBCI_FP64;
   p->mixed_eps = 1e-8;
   p->mixed_r = 1e-4;
-  p->refine_max_sigma = 30;
+  p->refine_max_sigma = 300;
+  p->start_noise = 0.0;
+  p->noise_seed = 0;
   return SBCI_OK;
 }
 
@@ -1139,6 +1161,13 @@ sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const doub
   double E0 = 0.0;
   if (s.p.init == 1) RET(init_from_vector(c, c0, &E0));
   else RET(initial_guess(c, k, &E0));
+  if (s.p.start_noise > 0.0) {
+    RET(mix_noise(c, 0, &E0));
+    RET(gen_dots(c, {s.x}, {s.x}));  // x0 must be a unit vector
+    const double nx = std::sqrt(c->h_result[S_GEN0]);
+    RET(lincomb(c, s.x, {s.x}, {1.0 / nx}));
+    RET(lincomb(c, s.X, {s.X}, {1.0 / nx}));
+  }
   return start_state(c, 0, E0);
 }
 

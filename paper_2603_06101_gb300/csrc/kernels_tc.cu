@@ -1,14 +1,17 @@
 // Tensor-core (tcgen05) gather + contract of the sigma build in 3-term TF32
 // split precision, for sm_103a.
 //
-// Per tile of 128 determinants (one per thread, one per TMEM lane):
+// Per tile of 128 determinants (one per TMEM lane, two threads each):
 //   1. gather   D[I, Q] = sum_{links of I} sign * c[J]   into shared memory,
 //               FP32, laid out as the K-major no-swizzle canonical operand A
-//               (8-row x 16-byte core matrices);
-//   2. split    D = D_hi + D_lo, both rounded to TF32, in place;
+//               (8-row x 16-byte core matrices); thread r gathers the alpha
+//               links of row r into A, thread r + 128 the beta links into the
+//               A_lo buffer, so every element has one writer;
+//   2. split    D = alpha + beta part = D_hi + D_lo, both TF32, in place;
 //   3. MMA      G^T = D_hi W_hi + D_hi W_lo + D_lo W_hi  (M=128, N=Np, K=8 per
 //               instruction), issued by one thread, accumulated in TMEM (FP32);
-//   4. epilogue tcgen05.ld of the thread's lane -> G[P][I] (FP32) in global.
+//   4. epilogue tcgen05.ld: warps w and w + 4 read the lanes of quadrant w,
+//               half of the columns each -> G[P][I] (FP32) in global.
 // W (symmetric, packed pairs) is split once per CTA into TF32 hi/lo operand
 // B and stays in shared memory.  The dropped D_lo W_lo term and the TF32
 // rounding of the lo parts leave a relative error of about 2^-21 per product.
@@ -25,7 +28,7 @@
 namespace sbci {
 
 constexpr int kTcM = 128;         // determinants per tile = MMA M = TMEM lanes
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two threads per determinant (alpha / beta links)
 constexpr long long kWaitIters = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -153,35 +156,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
   uint32_t phase = 0;
   bool ok = true;
+  const int row = tid & (kTcM - 1);  // determinant row of this thread
+  const int half = tid >> 7;         // 0: alpha links / first half, 1: beta links / second half
+  const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long I = tile * kTcM + tid;
+    const long long I = tile * kTcM + row;
     const bool valid = I < a.ndet;
-    // 1. gather this thread's row of D (FP32) into A
+    // 1. gather this row of D (FP32): the alpha part into A, the beta part
+    //    into Alo (free until the split), each row owned by one thread
+    float *mine = half ? Alo : A;
     for (int q = 0; q < Kp; q += 4)
-      *reinterpret_cast<float4 *>(A + opnd_off(tid, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4 *>(mine + opnd_off(row, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
       const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
-      const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-      const double *ccol = cin + ib;
-      for_links<8, double>(
-          la, a.nlink_a, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
-          [&](uint32_t v, double cv) {
-            const float f = (float)cv;
-            A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -f : f;
-          });
-      const uint32_t *lb = a.link_b + (size_t)ib * a.nlink_b;
-      const double *crow = cin + (size_t)ia * a.nb;
-      for_links<8, double>(
-          lb, a.nlink_b, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-          [&](uint32_t v, double cv) {
-            const float f = (float)cv;
-            A[opnd_off(tid, link_pair(v), Kp)] += link_neg(v) ? -f : f;
-          });
+      if (half == 0) {
+        const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+        const double *ccol = cin + ib;
+        for_links<8, double>(
+            la, a.nlink_a, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+            [&](uint32_t v, double cv) {
+              const float f = (float)cv;
+              mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+            });
+      } else {
+        const uint32_t *lb = a.link_b + (size_t)ib * a.nlink_b;
+        const double *crow = cin + (size_t)ia * a.nb;
+        for_links<8, double>(
+            lb, a.nlink_b, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+            [&](uint32_t v, double cv) {
+              const float f = (float)cv;
+              mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+            });
+      }
     }
-    // 2. split in place: A <- tf32(D), Alo <- tf32(D - tf32(D))
-    for (int q = 0; q < Kp; q += 4) {
-      float4 *p = reinterpret_cast<float4 *>(A + opnd_off(tid, q, Kp));
-      const float4 v = *p;
+    __syncthreads();
+    // 2. D = alpha part + beta part, split in place: A <- tf32(D), Alo <- tf32(D - tf32(D));
+    //    each thread half a row
+    for (int q = q_lo; q < q_hi; q += 4) {
+      float4 *p = reinterpret_cast<float4 *>(A + opnd_off(row, q, Kp));
+      float4 *pl = reinterpret_cast<float4 *>(Alo + opnd_off(row, q, Kp));
+      const float4 va = *p, vb = *pl;
+      const float4 v = make_float4(va.x + vb.x, va.y + vb.y, va.z + vb.z, va.w + vb.w);
       float4 h, l;
       h.x = __uint_as_float(tf32_bits(v.x));
       h.y = __uint_as_float(tf32_bits(v.y));
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       l.z = __uint_as_float(tf32_bits(v.z - h.z));
       l.w = __uint_as_float(tf32_bits(v.w - h.w));
       *p = h;
-      *reinterpret_cast<float4 *>(Alo + opnd_off(tid, q, Kp)) = l;
+      *pl = l;
     }
     fence_async_smem();
     fence_before();
@@ -217,9 +232,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (!ok) break;
     phase ^= 1u;
     fence_after();
-    // 4. epilogue: lane tid holds row tid of G^T
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < Np; c0 += 16) {
+    // 4. epilogue: warp w reads lane quadrant (w % 4), column half (w / 4)
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int ncol16 = Np / 16;
+    const int c_begin = (warp >> 2) * ((ncol16 + 1) / 2) * 16;
+    const int c_end = (warp >> 2) ? Np : ((ncol16 + 1) / 2) * 16;
+    for (int c0 = c_begin; c0 < c_end; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(lane_addr + (uint32_t)c0, r);
       if (valid) {

@@ -119,6 +119,22 @@ __global__ void k_symmetrize(double *v, int n) {
   }
 }
 
+// SplitMix64 output function (Steele, Lea & Flood 2014) on a counter.
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_splitmix(double *r, long long n, unsigned long long seed, int alpha) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long ctr = ((unsigned long long)alpha << 40) + (unsigned long long)i + 1ull;
+    const unsigned long long z = splitmix(seed + 0x9E3779B97F4A7C15ull * ctr);
+    r[i] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+  }
+}
+
 static int grid_for(long long n, int cap) {
   long long g = (n + kVecThreads - 1) / kVecThreads;
   if (g > cap) g = cap;
@@ -161,6 +177,11 @@ cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, co
                             const uint32_t *mask_b, int na, int nb, int norb, cudaStream_t s) {
   k_diagonal<<<grid_for((long long)na * nb, 8192), kVecThreads, 0, s>>>(diag, ea, eb, ja, mask_b,
                                                                         na, nb, norb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s) {
+  k_splitmix<<<grid_for(n, 8192), kVecThreads, 0, s>>>(r, n, seed, alpha);
   return cudaGetLastError();
 }
 

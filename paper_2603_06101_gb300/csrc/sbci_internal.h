@@ -123,6 +123,8 @@ cudaError_t launch_reduce(const double *partials, int grid, int s0, int s1, doub
 cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, const double *ja,
                             const uint32_t *mask_b, int na, int nb, int norb, cudaStream_t s);
 cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s);
+// r[I] = SplitMix64 vector of (seed, alpha) in [-1, 1)
+cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small dense symmetric eigen-solver (cyclic Jacobi), ascending eigenvalues,

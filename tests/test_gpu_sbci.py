@@ -137,3 +137,22 @@ def test_random_df_n14_two_states_residual_rows():
         res = hx - E[j] * V[j][rows]
         assert np.abs(res).max() < 1e-5
     assert abs(float(V[0] @ V[1])) < 1e-8
+
+
+@pytest.mark.parametrize("key,k,kw", [(("chain", 6, 1.0), 4, {}), (("chain", 10, 1.2), 3, {"sector": 1}),
+                                       (("chain", 8, 1.3), 3, {})])
+def test_start_noise_matches_oracle(key, k, kw):
+    """start_noise (reading R11): the same seeded SplitMix64 vector on both sides;
+    the states found must agree with the oracle and be the lowest ones."""
+    sbci = require_lib()
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    E, _, R, st = ctx.solve(k, sbci.params(start_noise=1e-2, noise_seed=7, **kw))
+    assert st == sbci.SBCI_OK
+    _, res = _oracle_run(key, k, start_noise=1e-2, noise_seed=7, **kw)
+    Eo = np.array([r.energy for r in res]) + I.e_core
+    assert np.abs(np.sort(E) - np.sort(Eo)).max() < 1e-8
+    if not kw:
+        H = sc.dense_hamiltonian(I.h1, I.eri, I.nalpha, I.nbeta)
+        w = np.linalg.eigvalsh(H)[:k] + I.e_core
+        assert np.abs(np.sort(E) - w).max() < 1e-8

@@ -50,6 +50,33 @@ def test_sbci1_four_states(h6):
     assert np.abs(X.T @ X - np.eye(4)).max() < 1e-8
 
 
+def test_splitmix_vector_reference_values():
+    """SplitMix64 output function against values computed by hand from its
+    definition (bit operations on Python integers)."""
+    def ref(seed, alpha, i):
+        M = (1 << 64) - 1
+        z = (seed + 0x9E3779B97F4A7C15 * ((alpha << 40) + i + 1)) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        return 2.0 * ((z >> 11) * 2.0 ** -53) - 1.0
+    v = sbci.splitmix_vector(12345, 2, 50)
+    assert all(v[i] == ref(12345, 2, i) for i in range(50))
+    assert abs(v.mean()) < 0.3 and v.min() >= -1.0 and v.max() < 1.0
+
+
+def test_sbci1_start_noise_reaches_the_lowest_states(h6):
+    """R11: with a small full-symmetry component in every start, SBCI1 meets
+    the four lowest eigenvalues of the symmetric H6 chain (as a set)."""
+    I, sig, H, D = h6
+    w = np.linalg.eigvalsh(H)
+    run = sbci.SBCI1(sig.apply, D, (20, 20), sbci.SBCIParams(start_noise=1e-2, noise_seed=7))
+    res = run.solve(4)
+    E = np.sort([r.energy for r in res])
+    assert all(r.converged for r in res)
+    assert np.abs(E - w[:4]).max() < 1e-8
+
+
 def test_sbci1_singlet_sector():
     I = inputs.h_chain(6, 1.4)
     sig = sg.StringSigma(I.h1, I.eri, 3, 3)
