@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu", action="store_true",
@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: batched mixed precision vs sequential FP64, p50/p99")
     ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=16,
+                    help="H10 solves per step, solved together by the batched persistent kernels "
+                         "(1: one solve per step through its own graph loop)")
     ap.add_argument("--slots", type=int, default=16)
     return ap.parse_args()
 
@@ -223,10 +226,18 @@ def run_gb300(args, rank, world, local_rank):
     ctx = sbci.Context.from_integrals(I, stream=stream.cuda_stream)
     p = sbci.params(sector=1, prec=prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    B = max(1, args.batch) if args.prec == "tf32x3" else 1
+    batch_ctx = [ctx] + [sbci.Context.from_integrals(I, stream=stream.cuda_stream) for _ in range(B - 1)]
 
     def one_solve():
-        E, _, R, st = ctx.solve(NSTATES, p)
-        return E, R, st
+        if B == 1:
+            E, _, R, st = ctx.solve(NSTATES, p)
+            return E, R, st
+        E, R, st = sbci.solve_batch(batch_ctx, NSTATES, p)
+        one_solve.launches += sbci.solve_batch.last_launches
+        return E[0], R[:NSTATES], st
+
+    one_solve.launches = 0
 
     for _ in range(max(args.warmup, 3)):
         E, R, st = one_solve()
@@ -240,6 +251,7 @@ def run_gb300(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    one_solve.launches = 0
     t_ms = 0.0
     wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -258,26 +270,53 @@ def run_gb300(args, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     stats = ctx.profile_read()
-    launches = sum(v[0] for v in stats.values())
+    launches = sum(v[0] for v in stats.values()) if B == 1 else one_solve.launches
     t_max = t_ms
     if dist:
         t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = world * args.steps / (t_max / 1000.0)
+    value = world * B * args.steps / (t_max / 1000.0)
+    # ---------------- one solve alone (latency), same event timing
+    single = None
+    if B > 1:
+        ts = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.solve(NSTATES, p)
+            e1.record(stream)
+            e1.synchronize()
+            ts += e0.elapsed_time(e1)
+        single = {"solves_per_s": args.steps / (ts / 1000.0), "ms_per_solve": ts / args.steps,
+                  "engine": "one graph loop per solve"}
     # ---------------- kernel timing pass: the same solves with each step kernel
-    # launched on its own and bracketed by CUDA events on the library stream
-    ctx.profile(True)
+    # launched on its own and bracketed by CUDA events on the launching stream
     kt0 = torch.cuda.Event(enable_timing=True)
     kt1 = torch.cuda.Event(enable_timing=True)
-    kt0.record(stream)
-    for _ in range(2):
-        one_solve()
-    kt1.record(stream)
-    kt1.synchronize()
-    kstats = ctx.profile_read()
-    ctx.profile(False)
-    kpass_ms = kt0.elapsed_time(kt1)
+    if B == 1:
+        ctx.profile(True)
+        kt0.record(stream)
+        for _ in range(2):
+            ctx.solve(NSTATES, p)
+        kt1.record(stream)
+        kt1.synchronize()
+        kstats = ctx.profile_read()
+        ctx.profile(False)
+        kpass_ms = kt0.elapsed_time(kt1)
+        units = 1
+    else:
+        sbci.batch_profile(True)
+        t0 = time.perf_counter()
+        sbci.solve_batch(batch_ctx, NSTATES, p)
+        torch.cuda.synchronize()
+        kpass_ms = (time.perf_counter() - t0) * 1000.0
+        kstats = sbci.batch_profile_read()
+        sbci.batch_profile(False)
+        units = B  # every batched launch serves the B solves (same Hamiltonian: they halt together)
     # ---------------- roofline of the dominant kernel
     pk, pk_kind = peaks()
     dom = max(kstats.items(), key=lambda kv: kv[1][1])
@@ -285,30 +324,32 @@ def run_gb300(args, rank, world, local_rank):
     npair, ndet = ctx.npair, ctx.ndet
     avg_s = ms / 1000.0 / max(nl, 1)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    flops = 2.0 * npair * npair * ndet
-    if name == "sigma_gather_contract_tc":
+    flops = 2.0 * npair * npair * ndet * units
+    base = name[len("batch_"):] if name.startswith("batch_") else name
+    base = {"update": "sb_update", "project": "sb_project", "scatter": "sigma_scatter"}.get(base, base)
+    if base == "gather_contract_tc" or base == "sigma_gather_contract_tc":
         peak = pk.get("bf16_tflops", 1900.0) * 0.5  # TF32 dense = half the BF16 rate (1.1 vs 2.25 PF)
         roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_kind": f"{pk_kind} bf16 x nominal TF32/BF16 ratio 0.5; achieved counts the "
-                             "algorithmic 2 npair^2 flops once (the 3-term split executes 3x)",
+                             "algorithmic 2 npair^2 flops per determinant once (the 3-term split executes 3x)",
                 "algorithmic_per_launch": flops}
-    elif name == "sigma_gather_contract" and args.prec == "fp64":
+    elif base == "sigma_gather_contract" and args.prec == "fp64":
         peak = 4.0 * 152 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA per clock per SM (1.25 TF/s at 2.07 GHz)
         roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_kind": "FP64: 152 SMs x 2 FMA/clk x 2 flop x median SM clock (the 1.25 TFLOP/s nominal)",
                 "algorithmic_per_launch": flops}
-    elif name == "sigma_gather_contract":
+    elif base == "sigma_gather_contract":
         peak = 2.0 * 152 * 128 * sm_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_kind": "FP32: 152 SMs x 128 lanes x 2 flop x median SM clock",
                 "algorithmic_per_launch": flops}
     else:
         gsz = 8 if args.prec == "fp64" else 4
-        per_det = {"sigma_scatter": npair * gsz + 8, "sb_update": 12 * 8, "sb_project": 4 * 8}.get(name, 16)
-        bytes_alg = float(per_det) * ndet
+        per_det = {"sigma_scatter": npair * gsz + 8, "sb_update": 12 * 8, "sb_project": 4 * 8}.get(base, 16)
+        bytes_alg = float(per_det) * ndet * units
         roof = {"bound": "hbm", "achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "peak_kind": pk_kind, "algorithmic_per_launch": bytes_alg,
-                "algorithmic_note": f"{per_det} B per determinant"}
+                "algorithmic_note": f"{per_det} B per determinant x {units} solves"}
     roof["kernel"] = name
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_for(name)
@@ -321,15 +362,23 @@ def run_gb300(args, rank, world, local_rank):
         eri = np.ascontiguousarray(I.eri)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        d2h = 0
         for _ in range(args.steps):
-            c2 = sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=stream.cuda_stream)
-            E2, V2, _, _ = c2.solve(NSTATES, p, want_vectors=True)
-            c2.close()
+            cs = [sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=stream.cuda_stream)
+                  for _ in range(B)]
+            if B == 1:
+                E2, V2, _, _ = cs[0].solve(NSTATES, p, want_vectors=True)
+                d2h = E2.nbytes + V2.nbytes
+            else:
+                E2, _, _ = sbci.solve_batch(cs, NSTATES, p)
+                d2h = E2.nbytes
+            for c2 in cs:
+                c2.close()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": args.steps / te, "unit": "solves/s",
-               "h2d_bytes_per_step": int(h1.nbytes + eri.nbytes),
-               "d2h_bytes_per_step": int(E2.nbytes + V2.nbytes)}
+        e2e = {"value": B * args.steps / te, "unit": "solves/s",
+               "h2d_bytes_per_step": int(B * (h1.nbytes + eri.nbytes)),
+               "d2h_bytes_per_step": int(d2h)}
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,10 +393,16 @@ def run_gb300(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "norb": 10, "ndet": ndet, "states": NSTATES,
+                       "solves_per_step": B, "engine": "batched persistent kernels, one graph loop" if B > 1
+                       else "one graph loop per solve",
                        "sector": "c=c^T", "sigma_precision": args.prec, "l2": "flushed (256 MB write) between steps",
                        "parallelism": f"replicas x{world}", "sigma_per_solve": nsig,
+                       "sigma_per_state": [int(r.n_sigma) for r in R],
+                       "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R],
                        "energies": [float(e) for e in E]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "single_solve": single,
+            "autotuner": sbci.batch_classes() if B > 1 else None,
             "launches_timed": {k: v[0] for k, v in stats.items() if v[0]},
             "kernels_timing_pass": {k: {"launches": v[0], "ms": v[1]} for k, v in kstats.items() if v[0]},
             "clocks": clocks, "wall_s_timed": wall,
@@ -383,9 +438,16 @@ def run_ncu_solve(args):
     I = workload()
     ctx = sbci.Context.from_integrals(I)
     prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
-    E, _, R, st = ctx.solve(NSTATES, sbci.params(sector=1, prec=prec))
+    p = sbci.params(sector=1, prec=prec)
+    B = max(1, args.batch) if args.prec == "tf32x3" else 1
+    if B == 1:
+        E, _, R, st = ctx.solve(NSTATES, p)
+    else:
+        ctxs = [ctx] + [sbci.Context.from_integrals(I) for _ in range(B - 1)]
+        EB, RB, st = sbci.solve_batch(ctxs, NSTATES, p)
+        E, R = EB[0], RB[:NSTATES]
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_solve": WORKLOAD, "energies": [float(e) for e in E],
+    print(json.dumps({"ncu_solve": WORKLOAD, "solves": B, "energies": [float(e) for e in E],
                       "sigma": sum(r.n_sigma for r in R)}))
 
 
@@ -454,7 +516,7 @@ def run_serving(args):
     # plain FP64, one solve per launch, in arrival order
     t0 = time.perf_counter()
     lat_f = np.zeros(n)
-    E_f = {}
+    E_f, st_f = {}, {}
     for i in np.argsort(arrivals, kind="stable"):
         while time.perf_counter() - t0 < arrivals[i]:
             pass
@@ -462,11 +524,18 @@ def run_serving(args):
         E, _, _, st = ctx.solve(ks[i], p_fp64)
         ctx.close()
         E_f[int(i)] = E
+        st_f[int(i)] = int(st)
         lat_f[i] = (time.perf_counter() - t0) - arrivals[i]
     span_f = time.perf_counter() - t0
     err = max(float(np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max()) for i in range(n))
     err0 = max(float(abs(done_m[i][0][0] - E_f[i][0])) for i in range(n))
-    nbad = sum(1 for i in range(n) if np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max() > 1e-6)
+    bad = [i for i in range(n) if np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max() > 1e-6]
+    nbad = len(bad)
+    details = [{"request": i, "natoms": base[i].natoms, "spacing": base[i].spacing_angstrom, "k": ks[i],
+                "E_mixed": [float(e) for e in done_m[i][0]], "status_mixed": int(done_m[i][3]),
+                "converged_mixed": [int(r.converged) for r in done_m[i][1]],
+                "n_sigma_mixed": [int(r.n_sigma) for r in done_m[i][1]],
+                "E_fp64": [float(e) for e in E_f[i]], "status_fp64": st_f[i]} for i in bad]
     line = {
         "serving": f"{n} requests, H6/H8/H10/H12 STO-3G, spacing U(0.7, 3.0) A, 1-4 states (seed 4)",
         "saturation_solves_per_s": capacity, "poisson_rate_per_s": rate,
@@ -475,7 +544,7 @@ def run_serving(args):
         "sequential_fp64": {"solves_per_s": n / span_f, "p50_s": float(np.percentile(lat_f, 50)),
                             "p99_s": float(np.percentile(lat_f, 99))},
         "max_energy_diff_mixed_vs_fp64_hartree": err, "max_ground_state_diff_hartree": err0,
-        "requests_differing_by_more_than_1e-6": nbad,
+        "requests_differing_by_more_than_1e-6": nbad, "differing": details,
         "sizes": {str(sz): int(sum(1 for r in base if r.natoms == sz)) for sz in (6, 8, 10, 12)},
     }
     print(json.dumps(line), flush=True)

@@ -79,7 +79,9 @@ typedef struct {
                        X by an FP64 H x and continues in FP64 to Eq. S61. */
   double mixed_eps; /* end of the low-precision stage: dE < mixed_eps ... ; 1e-8 */
   double mixed_r;   /* ... and |z'| < mixed_r; 1e-4 */
-  int refine_max_sigma; /* cap on H-products of the refinement stage per state; 300 */
+  int refine_max_sigma; /* H-products of the low-precision refinement stage per
+                           state; when spent, the state continues with FP64
+                           sigma up to max_sigma; 300 */
   double start_noise; /* eta >= 0: every state's start becomes x0/|x0| + eta r/|r| with
                          r a seeded SplitMix64 vector in [-1,1) (X by one FP64 sigma of
                          r) and E_0 its Rayleigh quotient, before the projection of Eqs.
@@ -108,7 +110,9 @@ typedef struct {
   double b, c, k;     /* parameters of the step (Eqs. S23-S24, S53-S55) */
   double dE, dz;      /* |E_{t+1}-E_t| and |z'_{t+1}| */
   int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle,
-                         6 low-precision stage ended: switch to FP64 refinement */
+                         6 low-precision stage ended: switch to FP64 refinement,
+                         7 refinement budget spent: the state continues with
+                           FP64 sigma from an exact X (host record) */
   int prec;           /* sbci_precision of the sigma used in the step */
 } sbci_trace_record;
 
@@ -195,6 +199,17 @@ sbci_status sbci_finish(sbci_ctx *ctx, double *energies, double *vecs, sbci_repo
 sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const double *c0,
                        double *energies, double *vecs, sbci_report *rep);
 
+/* Solves n contexts (1 <= n <= 64) for their k lowest states together: the
+ * solves with a TF32x3 sigma and n_orb <= 12 advance in one CUDA-graph loop of
+ * batched persistent kernels over a device job table (see sbci_server_*);
+ * others are solved one after the other.  params as in sbci_solve (init must
+ * be 0).  energies: host [n][k] totals; rep: host [n][k] or NULL; launches
+ * (nullable): kernels this call launched (five per batched loop body plus the
+ * host-driven ones).  Each context afterwards holds its finished solve
+ * (sbci_finish, sbci_trace). */
+sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
+                             sbci_report *rep, long long *launches);
+
 /* Copies up to cap trace records of the last solve; *n = records available. */
 sbci_status sbci_trace(const sbci_ctx *ctx, sbci_trace_record *buf, int cap, int *n);
 
@@ -213,6 +228,32 @@ sbci_status sbci_profile(sbci_ctx *ctx, int enable);
 
 /* Waits for the recorded events and copies up to cap entries; *n = families. */
 sbci_status sbci_profile_read(sbci_ctx *ctx, sbci_kernel_stat *out, int cap, int *n);
+
+/* Kernel timing of the batch engine that sbci_solve_batch uses on the current
+ * device (no counterpart in the paper).  Resets its statistics; enable = 1
+ * makes later sbci_solve_batch calls on this device launch the five kernels of
+ * every batched loop body one by one, each bracketed by CUDA events on the
+ * engine's stream, instead of through the graph loop (same arithmetic). */
+sbci_status sbci_batch_profile(int enable);
+
+/* Waits for the recorded events and copies up to cap entries (families
+ * "batch_update", "batch_project", "batch_gather_contract_tc",
+ * "batch_scatter", "batch_end"); *n = 5. */
+sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n);
+
+/* Launch shapes of the batch engine on the current device, one record per
+ * operand class met so far (no counterpart in the paper).  The autotuner
+ * fills ctas[] once it has timed every candidate (tuned = 1). */
+typedef struct {
+  int Kp, Np;            /* tensor-core operand class (padded pair counts) */
+  int smem_bytes;        /* dynamic shared memory of a tensor-core CTA */
+  int tc_per_sm_max;     /* tensor-core CTAs that fit one SM */
+  int tuned;             /* 1 once the autotuner has chosen */
+  int ctas[5];           /* update, projection, tensor core, scatter, end */
+} sbci_batch_class;
+
+/* Copies up to cap records; *n = classes. */
+sbci_status sbci_batch_classes(sbci_batch_class *out, int cap, int *n);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of solves on one GPU (no counterpart in the
@@ -246,6 +287,13 @@ sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued);
  * completion} are written (each nullable) and the solve's status returned. */
 sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, double *energies,
                              sbci_report *rep, double *times);
+
+/* on = 1 (the default): admitted solves with a TF32x3 sigma and n <= 12 are
+ * advanced together by one CUDA-graph loop of batched persistent kernels that
+ * walk a device job table (a work queue of (solve, block) items); on = 0: every
+ * solve runs its own graph loop on its own stream.  Only while no solve is
+ * admitted. */
+sbci_status sbci_server_set_batching(sbci_server *sv, int on);
 
 /* Waits for in-flight rounds and frees every slot.  NULL is a no-op. */
 void sbci_server_destroy(sbci_server *sv);

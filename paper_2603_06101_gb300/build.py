@@ -21,6 +21,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# The SB step loop is compiled without multiply-add contraction: every fused
+# multiply-add there is an explicit fma(), so the one-solve and the batched
+# kernels round identically whatever the compiler inlines or schedules.
+FILE_FLAGS = {"kernels_loop.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -36,7 +40,7 @@ def sources():
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *COMMON, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-O3"]
     r = subprocess.run(cmd, capture_output=True, text=True)

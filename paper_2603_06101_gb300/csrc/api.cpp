@@ -26,6 +26,7 @@
 
 #include "../../include/sbci.h"
 #include "ctl.h"
+#include "batch.h"
 #include "sbci_internal.h"
 #include "step.h"
 
@@ -78,6 +79,7 @@ struct Solver {
   double *x = nullptr, *X = nullptr, *y = nullptr, *Y = nullptr, *w = nullptr;
   double *z[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr};
   double *xc = nullptr;  // [k][ndet]
+  float *zf = nullptr;   // FP32 copy of the next z (split and FP32 sigma modes)
   CtlState *d_ctl = nullptr;  // device controller state
   CtlState *h_ctl = nullptr;  // pinned host mirror
   unsigned int *d_counters = nullptr;
@@ -103,8 +105,10 @@ struct sbci_ctx {
   bool own_stream = false;
   int grid = 0;
   uint32_t *d_link_a = nullptr, *d_link_b = nullptr, *d_mask_b = nullptr;
+  uint32_t *d_link_bT = nullptr;  // beta lists transposed, [nlink_b][Nb]
   double *d_W = nullptr;
   float *d_Wf = nullptr;
+  uint32_t *d_Wtc = nullptr;  // TF32 hi/lo operand B of the tensor-core sigma (nullptr: unsupported)
   double *d_diag = nullptr;
   double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
   void *d_G = nullptr;
@@ -211,8 +215,10 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.G = c->d_G;
   a.link_a = c->d_link_a;
   a.link_b = c->d_link_b;
+  a.link_bT = c->d_link_bT;
   a.W = c->d_W;
   a.Wf = c->d_Wf;
+  a.Wtc = c->d_Wtc;
   a.na = c->Na;
   a.nb = c->Nb;
   a.nlink_a = c->sa.nlink;
@@ -420,15 +426,18 @@ sbci_status run_until_halt(sbci_ctx *c) {
     CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
     return SBCI_OK;
   }
-  for (;;) {  // chunks of bodies; bodies after a halt do no work
-    for (int i = 0; i < 8; ++i) RET(launch_body(c, prec, 0, true));
+  // chunks of bodies (bodies after a halt do no work); one body per chunk
+  // under kernel timing, so that no empty launch enters the statistics
+  const int chunk = c->prof.on ? 1 : 8;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) RET(launch_body(c, prec, 0, true));
     RET(ctl_read(c));
     if (s.h_ctl->halt) return SBCI_OK;
   }
 }
 
 // (Re)starts the SB iteration of the current state from x, X with |x| = 1/sx.
-sbci_status start_iteration(sbci_ctx *c, double sx, double E, int stage) {
+sbci_status start_iteration(sbci_ctx *c, double sx, double E, int stage, int prec = -1) {
   Solver &s = c->s;
   CtlState &h = *s.h_ctl;
   h.halt = H_RUN;
@@ -438,7 +447,8 @@ sbci_status start_iteration(sbci_ctx *c, double sx, double E, int stage) {
   h.t = 0;
   h.E = E;
   h.stage = stage;
-  h.prec = s.p.prec;
+  h.prec = prec >= 0 ? prec : s.p.prec;
+  h.zf = h.prec != SBCI_FP64 ? s.zf : nullptr;
   h.up.sx = sx;
   h.up.sy = 0.0;
   h.up.b = 0.0;
@@ -565,12 +575,25 @@ sbci_status handle_halt(sbci_ctx *c) {
       return start_iteration(c, 1.0 / std::sqrt(xx), xX / xx, 1);
     }
     case H_CAP:
+      if (h.prec != SBCI_FP64 && h.n_sigma < s.p.max_sigma) {
+        // the low-precision refinement used its budget without reaching the
+        // paper's thresholds: finish the state with FP64 sigma from the exact X
+        double xx, xX, XX;
+        RET(resync(c, &xx, &xX, &XX));
+        sbci_trace_record r{};
+        r.state = h.alpha;
+        r.energy = xX / xx;
+        r.event = 7;
+        r.prec = SBCI_FP64;
+        s.trace.push_back(r);
+        return start_iteration(c, 1.0 / std::sqrt(xx), xX / xx, 1, SBCI_FP64);
+      }
       s.h_ctl->halt = H_RUN;
       set_error("state reached its H-product cap without converging");
       RET(finalize_state(c, false, h.E, std::sqrt(h.dots[S_ZPZP])));
       return SBCI_ERR_NOT_CONVERGED;
     case H_CONVERGED: {
-      if (s.p.prec == SBCI_FP64)
+      if (s.p.prec == SBCI_FP64 || h.prec == SBCI_FP64)  // FP64 sigma throughout (or after a fallback)
         return finalize_state(c, true, h.E, std::sqrt(h.dots[S_ZPZP]));
       // FP64 residual check of the low-precision result: exact X = H x,
       // Rayleigh quotient and |H x - E x| / |x|
@@ -598,6 +621,8 @@ void free_solver(sbci_ctx *c) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  if (s.zf) cudaFree(s.zf);
+  s.zf = nullptr;
   if (s.d_ctl) cudaFree(s.d_ctl);
   if (s.h_ctl) cudaFreeHost(s.h_ctl);
   if (s.d_counters) cudaFree(s.d_counters);
@@ -616,6 +641,7 @@ sbci_status alloc_solver(sbci_ctx *c, int k) {
     CK(cudaMemsetAsync(*p, 0, sizeof(double) * c->ndet, c->stream));
   }
   RET(dmalloc(&s.xc, (size_t)k * c->ndet));
+  if (s.p.prec != SBCI_FP64) RET(dmalloc(&s.zf, (size_t)c->ndet));
   CK(cudaMemsetAsync(s.xc, 0, sizeof(double) * (size_t)k * c->ndet, c->stream));
   CK(cudaMalloc((void **)&s.d_ctl, sizeof(CtlState)));
   CK(cudaMemsetAsync(s.d_ctl, 0, sizeof(CtlState), c->stream));
@@ -768,15 +794,17 @@ sbci_status sbci::solve_round_launch(sbci_ctx *c) {
   return SBCI_OK;
 }
 
-sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done) {
+sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
   Solver &s = c->s;
   RET(ctl_read(c));
   const long long bodies = s.h_ctl->iters;
   const int prec = s.h_ctl->prec;
-  c->prof.launches[K_UPD] += bodies;
-  c->prof.launches[K_PROJ] += bodies;
-  c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
-  c->prof.launches[K_SC] += bodies;
+  if (own_graph) {  // the solve's own graph ran four kernels per body
+    c->prof.launches[K_UPD] += bodies;
+    c->prof.launches[K_PROJ] += bodies;
+    c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
+    c->prof.launches[K_SC] += bodies;
+  }
   s.h_ctl->iters = 0;
   CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
   const sbci_status st = handle_halt(c);
@@ -786,6 +814,29 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done) {
 
 cudaStream_t sbci::ctx_stream(const sbci_ctx *c) { return c->stream; }
 
+bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
+  Solver &s = c->s;
+  if (!s.active || s.done || s.p.prec != SBCI_TF32X3 || s.h_ctl->prec != SBCI_TF32X3 ||
+      c->npair > kBatchMaxPair)
+    return false;
+  uint32_t cols;
+  size_t smem;
+  if (!tc_dims(c->npair, &j->Kp, &j->Np, &cols, &smem)) return false;
+  j->step = step_args(c, 0);
+  j->sig = sigma_ctl_args(c, SBCI_TF32X3, 0);
+  return true;
+}
+
+int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_grid(c->ndet, c->nsm); }
+int sbci::ctx_scatter_blocks(const sbci_ctx *c) { return scatter_grid(c->ndet, c->nsm); }
+long long sbci::ctx_ndet(const sbci_ctx *c) { return c->ndet; }
+
+long long sbci::ctx_launch_count(const sbci_ctx *c) {
+  long long n = 0;
+  for (int i = 0; i < K_COUNT; ++i) n += c->prof.launches[i];
+  return n;
+}
+
 size_t sbci::ctx_device_bytes(int norb, int nalpha, int nbeta, int k) {
   auto binom = [](int n, int r) {
     long long v = 1;
@@ -794,7 +845,7 @@ size_t sbci::ctx_device_bytes(int norb, int nalpha, int nbeta, int k) {
   };
   const long long na = binom(norb, nalpha), nb = binom(norb, nbeta), nd = na * nb;
   const long long npair = norb * (norb + 1) / 2;
-  const long long vec = (9LL + k) * nd * 8;     // x X y Y w z0 z1 Z0 Z1 + stored states
+  const long long vec = (9LL + k) * nd * 8 + nd * 4;  // x X y Y w z0 z1 Z0 Z1 + stored states + FP32 z
   const long long G = npair * nd * 8;            // sigma scratch (FP64 size, shared by FP32 modes)
   const long long tab = (na * nalpha * (norb - nalpha + 1) + nb * nbeta * (norb - nbeta + 1)) * 4;
   return (size_t)(vec + G + tab + nd * 8 + (1 << 20));
@@ -805,8 +856,10 @@ bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream)
   *a = SigmaArgs{};
   a->link_a = c->d_link_a;
   a->link_b = c->d_link_b;
+  a->link_bT = c->d_link_bT;
   a->W = c->d_W;
   a->Wf = c->d_Wf;
+  a->Wtc = c->d_Wtc;
   a->na = c->Na;
   a->nb = c->Nb;
   a->nlink_a = c->sa.nlink;
@@ -856,7 +909,7 @@ void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {c->d_link_a, c->d_mask_b, c->d_W, c->d_Wf, c->d_diag, c->d_ea, c->d_eb,
+  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_diag, c->d_ea, c->d_eb,
                   c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in, c->d_tmp_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -1005,6 +1058,12 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(up((void **)&c->d_link_a, c->sa.links.data(), c->sa.links.size() * 4));
   if (nbeta == nalpha) c->d_link_b = c->d_link_a;
   else TRY(up((void **)&c->d_link_b, c->sb.links.data(), c->sb.links.size() * 4));
+  {
+    std::vector<uint32_t> bT((size_t)c->sb.nlink * c->Nb);
+    for (int e = 0; e < c->sb.nlink; ++e)
+      for (int ib = 0; ib < c->Nb; ++ib) bT[(size_t)e * c->Nb + ib] = c->sb.links[(size_t)ib * c->sb.nlink + e];
+    TRY(up((void **)&c->d_link_bT, bT.data(), bT.size() * 4));
+  }
   TRY(up((void **)&c->d_mask_b, c->sb.masks.data(), c->sb.masks.size() * 4));
   TRY(up((void **)&c->d_W, c->W_host.data(), c->W_host.size() * 8));
   TRY(up((void **)&c->d_Wf, Wf.data(), Wf.size() * 4));
@@ -1021,6 +1080,15 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
+  {
+    int Kp, Np;
+    uint32_t cols;
+    size_t smem;
+    if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) {
+      TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
+      TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
+    }
+  }
   TRY(cuda_ok(launch_diagonal(c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_mask_b, c->Na, c->Nb, n,
                               c->stream), "diagonal kernel"));
   TRY(cuda_ok(cudaStreamSynchronize(c->stream), "sync"));

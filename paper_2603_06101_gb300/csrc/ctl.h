@@ -40,6 +40,10 @@ struct CtlState {
   CtlParams p;
   // ping-pong z / Z: the update reads (zc, Zc), projection/sigma write (zn, Zn)
   double *zc, *Zc, *zn, *Zn;
+  // FP32 copy of zn written by its producer (update or projection) when the
+  // sigma runs in a split/FP32 mode (nullptr in FP64 mode): the low-precision
+  // gather reads it instead of converting zn element by element
+  float *zf;
   int alpha, t, first, pending_check, prec, halt;
   int stage;       // 0: low-precision stage (ends with H_SWITCH); 1: to Eq. S61
   int n_stage1;    // H-products spent in stage 1 of this state
@@ -56,6 +60,150 @@ struct CtlState {
   double dots[S_COUNT];
   sbci_trace_record trace[kTraceCap];
 };
+
+// FP64 reciprocal and reciprocal square root from an FP32 estimate refined by
+// Newton steps: a handful of FP64 FMAs instead of the long FP64 division and
+// square-root sequences, which the single controller thread pays serially on
+// GB300's narrow FP64 pipe.
+__host__ __device__ inline double f_recip(double d) {
+#ifdef __CUDA_ARCH__
+  double r = (double)__frcp_rn((float)d);
+#else
+  double r = (double)(1.0f / (float)d);
+#endif
+  r = r * fma(-d, r, 2.0);
+  r = r * fma(-d, r, 2.0);
+  return r;
+}
+
+__host__ __device__ inline double f_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+  double r = (double)rsqrtf((float)x);
+#else
+  double r = (double)(1.0f / sqrtf((float)x));
+#endif
+  for (int i = 0; i < 3; ++i) r = r * fma(-0.5 * x * r, r, 1.5);  // r <- r (3 - x r^2) / 2
+  return r;
+}
+
+// Symmetric eigen-solver in FP32 (cyclic Jacobi), ascending.
+__host__ __device__ inline void eigh_f32(int n, const double *Ain, float *w, float *V) {
+  float A[9];
+  for (int i = 0; i < n * n; ++i) A[i] = (float)Ain[i];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0f : 0.0f;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    float off = 0.0f, dg = 0.0f;
+    for (int i = 0; i < n; ++i) {
+      dg += A[i * n + i] * A[i * n + i];
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    }
+    if (off <= 1e-14f * (dg + 1e-30f)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const float apq = A[p * n + q];
+        if (apq == 0.0f) continue;
+        const float theta = (A[q * n + q] - A[p * n + p]) / (2.0f * apq);
+        const float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+        const float c = 1.0f / sqrtf(t * t + 1.0f), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const float akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const float apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const float vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+  for (int i = 0; i < n; ++i) {
+    int m = i;
+    for (int j = i + 1; j < n; ++j)
+      if (w[j] < w[m]) m = j;
+    if (m != i) {
+      const float tw = w[i];
+      w[i] = w[m];
+      w[m] = tw;
+      for (int k = 0; k < n; ++k) {
+        const float tv = V[k * n + i];
+        V[k * n + i] = V[k * n + m];
+        V[k * n + m] = tv;
+      }
+    }
+  }
+}
+
+// One Rayleigh-quotient-iteration step in FP64 for a 2x2 / 3x3 symmetric V
+// from an FP32 eigenpair (lam, v): v <- adj(V - lam I) v, normalised, and
+// lam <- v^T V v.  Cubically convergent, so FP32 accuracy becomes FP64
+// accuracy in one step for separated eigenvalues.  Returns the residual
+// |V v - lam v| for the caller's acceptance test.
+__host__ __device__ inline double rqi_refine(int n, const double *V, double &lam, double *v) {
+  double w[3];
+  if (n == 2) {
+    const double a = V[0] - lam, b = V[1], d = V[3] - lam;
+    // adj [[a, b], [b, d]] = [[d, -b], [-b, a]]
+    w[0] = d * v[0] - b * v[1];
+    w[1] = -b * v[0] + a * v[1];
+  } else {
+    const double a = V[0] - lam, b = V[1], c = V[2], d = V[4] - lam, e = V[5], f = V[8] - lam;
+    const double A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
+    const double A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
+    w[0] = A00 * v[0] + A01 * v[1] + A02 * v[2];
+    w[1] = A01 * v[0] + A11 * v[1] + A12 * v[2];
+    w[2] = A02 * v[0] + A12 * v[1] + A22 * v[2];
+  }
+  double nn = 0.0;
+  for (int i = 0; i < n; ++i) nn = fma(w[i], w[i], nn);
+  if (!(nn > 0.0)) return 1e300;
+  const double inv = f_rsqrt(nn);
+  // keep the sign of the starting vector
+  double dot = 0.0;
+  for (int i = 0; i < n; ++i) dot = fma(w[i], v[i], dot);
+  const double sg = dot < 0.0 ? -inv : inv;
+  for (int i = 0; i < n; ++i) v[i] = w[i] * sg;
+  double Vv[3], l = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double t = 0.0;
+    for (int j = 0; j < n; ++j) t = fma(V[i * n + j], v[j], t);
+    Vv[i] = t;
+    l = fma(v[i], t, l);
+  }
+  lam = l;
+  double r = 0.0;
+  for (int i = 0; i < n; ++i) r = fma(Vv[i] - l * v[i], Vv[i] - l * v[i], r);
+  return r;
+}
+
+__host__ __device__ inline void ctl_eigh(int n, const double *Ain, double *w, double *V);
+
+// Lowest two eigenpairs of a 2x2 / 3x3 symmetric V to FP64 accuracy: FP32
+// Jacobi, then one FP64 Rayleigh-quotient step each; falls back to the FP64
+// Jacobi solver when a refined residual is not at rounding level.
+__host__ __device__ inline void ctl_eigh_fast(int n, const double *V, double *w, double *U) {
+  float wf[3], Uf[9];
+  eigh_f32(n, V, wf, Uf);
+  double scale = 0.0;
+  for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(V[i]));
+  bool ok = true;
+  for (int j = 0; j < 2 && j < n; ++j) {
+    double v[3], lam = (double)wf[j];
+    for (int i = 0; i < n; ++i) v[i] = (double)Uf[i * n + j];
+    const double r = rqi_refine(n, V, lam, v);
+    if (!(r <= 1e-26 * scale * scale)) ok = false;
+    w[j] = lam;
+    for (int i = 0; i < n; ++i) U[i * n + j] = v[i];
+  }
+  if (!ok || (n > 1 && !(w[0] <= w[1]))) ctl_eigh(n, V, w, U);
+}
 
 __host__ __device__ inline void ctl_eigh(int n, const double *Ain, double *w, double *V) {
   double A[9];
@@ -136,17 +284,18 @@ __host__ __device__ inline void ctl_first_step(const CtlState &s, StepOut &o) {
     o.r[0] = o.r[1] = o.r[2] = 0.0;
     return;
   }
-  const double Bz = 1.0 / sqrt(g);  // S12
+  const double Bz = f_rsqrt(g);  // S12
   const double Bx = -Nxz * Bz;      // S13
   double V[4], w[2], U[4];
   V[0] = Hxx;
   V[1] = V[2] = Bx * Hxx + Bz * Hxz;
   V[3] = Bx * Bx * Hxx + Bz * Bz * Hzz + 2.0 * Bx * Bz * Hxz;
-  ctl_eigh(2, V, w, U);
+  ctl_eigh_fast(2, V, w, U);
   const double vx = U[0], vz = U[2];
   o.E = w[0];
-  o.k = 1.0 / (vx + vz * Bx);       // S23
-  o.c = -vz * Bz / (vx + vz * Bx);  // S24
+  const double den = f_recip(vx + vz * Bx);
+  o.k = den;                        // S23
+  o.c = -vz * Bz * den;             // S24
   const double A = U[1] + U[3] * Bx;
   o.r[0] = A;  // x_0 = x_new - y_new
   o.r[1] = -A;
@@ -163,19 +312,20 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
   const double Hyy = d[S_HYY], Hyz = d[S_HYZ], Hzz = d[S_HZZ];
   o.sx = 1.0;
   o.sy = 1.0;
-  const double Ax = 1.0 / sqrt(Nxx);                         // S34
-  const double By = 1.0 / sqrt(Nyy - Nxy * Nxy / Nxx);       // S36
-  const double Bx = -Nxy / Nxx * By;                         // S37
+  const double iNxx = f_recip(Nxx);
+  const double Ax = f_rsqrt(Nxx);                            // S34
+  const double By = f_rsqrt(Nyy - Nxy * Nxy * iNxx);         // S36
+  const double Bx = -Nxy * iNxx * By;                        // S37
   const double P = Bx * Nxz + By * Nyz;                      // S42
-  const double gz = Nzz - Nxz * Nxz / Nxx - P * P;
+  const double gz = Nzz - Nxz * Nxz * iNxx - P * P;
   if (!(gz > 0.0) || gz < s.p.gs_tol * Nzz) {                // z inside span{x, y}: c = 0
     double V[4], w[2], U[4];
     V[0] = Ax * Ax * Hxx;
     V[1] = V[2] = Ax * (Bx * Hxx + By * Hxy);
     V[3] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;
-    ctl_eigh(2, V, w, U);
+    ctl_eigh_fast(2, V, w, U);
     const double vx = U[0], vy = U[2];
-    o.k = 1.0 / (vx * Ax + vy * Bx);
+    o.k = f_recip(vx * Ax + vy * Bx);
     o.b = vy * By * o.k;
     o.c = 0.0;
     o.E = w[0];
@@ -186,9 +336,9 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
     o.E2 = w[1];
     return;
   }
-  const double Cz = 1.0 / sqrt(gz);                          // S39
+  const double Cz = f_rsqrt(gz);                             // S39
   const double Cy = -P * By * Cz;                            // S40
-  const double Cx = -(Nxz / Nxx + P * Bx) * Cz;              // S41
+  const double Cx = -(Nxz * iNxx + P * Bx) * Cz;             // S41
   const double hx = Cx * Hxx + Cy * Hxy + Cz * Hxz;
   const double hy = Cx * Hxy + Cy * Hyy + Cz * Hyz;
   double V[9], w[3], U[9];
@@ -199,13 +349,13 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
   V[5] = V[7] = Bx * hx + By * hy;                             // S44e
   V[8] = Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz + 2.0 * Cx * Cy * Hxy +
          2.0 * Cx * Cz * Hxz + 2.0 * Cy * Cz * Hyz;            // S44f
-  ctl_eigh(3, V, w, U);
+  ctl_eigh_fast(3, V, w, U);
   const double vx = U[0], vy = U[3], vz = U[6];
-  const double den = vx * Ax + vy * Bx + vz * Cx;
+  const double iden = f_recip(vx * Ax + vy * Bx + vz * Cx);
   o.E = w[0];
-  o.k = 1.0 / den;                                           // S53
-  o.b = (vy * By + vz * Cy) / den;                           // S54
-  o.c = -vz * Cz / (vy * By + vz * Cy);                      // S55
+  o.k = iden;                                                // S53
+  o.b = (vy * By + vz * Cy) * iden;                          // S54
+  o.c = -vz * Cz * f_recip(vy * By + vz * Cy);               // S55
   const double cx = U[1] * Ax + U[4] * Bx + U[7] * Cx, cy = U[4] * By + U[7] * Cy, cz = U[7] * Cz;
   o.r[0] = cx;  // pre-update vectors: y_t = y_new + c z_t, x_t = x_new - b y_new
   o.r[1] = cy - cx * o.b;
@@ -224,7 +374,7 @@ __host__ __device__ inline void ctl_check(CtlState &s) {
   s.pending_check = 0;
   const double *d = s.dots;
   sbci_trace_record r = s.pending;
-  const double dz = sqrt(d[S_ZPZP]);
+  const double dz = d[S_ZPZP] > 0.0 ? d[S_ZPZP] * f_rsqrt(d[S_ZPZP]) : 0.0;
   const double dE = fabs(s.E_solve - s.E);
   r.dE = dE;
   r.dz = dz;
@@ -257,18 +407,19 @@ __host__ __device__ inline void ctl_check(CtlState &s) {
   if (cause) {
     s.n_restart[cause - 1] += 1;
     s.first = 1;
-    s.sx_pending = 1.0 / sqrt(d[S_NXX]);
+    s.sx_pending = f_rsqrt(d[S_NXX]);
     s.t = 0;
   } else {
     s.t += 1;
     const double gy = d[S_NYY] - d[S_NXY] * d[S_NXY] / d[S_NXX];
     if (gy < s.p.gs_tol * d[S_NYY]) {  // y inside span{x}: first-step path
       s.first = 1;
-      s.sx_pending = 1.0 / sqrt(d[S_NXX]);
+      s.sx_pending = f_rsqrt(d[S_NXX]);
       s.t = 0;
     }
   }
-  if (s.n_sigma >= s.p.max_sigma || (s.p.user_prec != SBCI_FP64 && s.n_stage1 >= s.p.refine_max_sigma))
+  if (s.n_sigma >= s.p.max_sigma ||
+      (s.p.user_prec != SBCI_FP64 && s.prec != SBCI_FP64 && s.n_stage1 >= s.p.refine_max_sigma))
     s.halt = H_CAP;
 }
 
@@ -308,7 +459,7 @@ __host__ __device__ inline void ctl_solve(CtlState &s) {
   s.up.b = o.b;
   s.up.c = o.c;
   s.up.E = o.E;
-  s.up.kinv = 1.0 / o.k;
+  s.up.kinv = f_recip(o.k);
   s.up.Epre = (s.alpha == 0) ? o.E : s.Ec0;  // newest ground-state Rayleigh quotient
   s.first = 0;
   s.pending_check = 1;

@@ -9,13 +9,15 @@
 
 namespace sbci {
 
-// Block partials of NV values per thread -> partials[slot * grid + blockIdx.x]
-// (slots[j] < 0: value j unused).  NT = threads per block.
+// Block partials of NV values per thread -> partials[slot * grid + block]
+// (slots[j] < 0: value j unused).  NT = threads per block; block is the
+// (virtual) block index within its grid of size grid.
 template <int NV, int NT>
 __device__ __forceinline__ void block_partials(const double (&v)[NV], const int (&slots)[NV],
-                                               double *partials, int grid) {
+                                               double *partials, int grid, int block) {
   __shared__ double buf[NT / 32][NV][33];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // a persistent block may come back with the buffer still in use
 #pragma unroll
   for (int j = 0; j < NV; ++j) buf[wid][j][lane] = v[j];
   __syncwarp();
@@ -29,17 +31,17 @@ __device__ __forceinline__ void block_partials(const double (&v)[NV], const int 
     const int j = threadIdx.x;
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += buf[w][j][32];
-    if (slots[j] >= 0) partials[(size_t)slots[j] * grid + blockIdx.x] = s;
+    if (slots[j] >= 0) partials[(size_t)slots[j] * grid + block] = s;
   }
 }
 
-// Returns true in exactly one block: the last one to arrive.  Its threads then
-// see every other block's partials.
-__device__ __forceinline__ bool last_block(unsigned int *counter) {
+// Returns true in exactly one of nblocks (virtual) blocks: the last one to
+// arrive.  Its threads then see every other block's partials.
+__device__ __forceinline__ bool last_block(unsigned int *counter, int nblocks) {
   __shared__ unsigned int s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1u) ? 1u : 0u;
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == (unsigned int)nblocks - 1u) ? 1u : 0u;
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0u;

@@ -1,0 +1,470 @@
+// The kernels of the SB step loop, in one translation unit: the one-solve
+// kernels (update, projection, tensor-core gather + contract, scatter) and the
+// batched persistent kernels that serve many solves per launch.  Both run the
+// same bodies (step_body.cuh, sigma_body.cuh, tc_body.cuh, ctl.h), and this
+// file is compiled without implicit multiply-add contraction (every fused
+// operation is an explicit fma()), so a solve run alone and the same solve run
+// in a batch round identically and give bitwise the same results.
+//
+// One-solve kernels: scalars come from the device controller state (ctl.h);
+// the last block of the update sweep finishes its dot products and runs the
+// convergence / restart test, the last block of the scatter solves the
+// subspace problem, so consecutive steps need no host round trip.  Every
+// kernel returns at once when the controller has halted, and then clears the
+// loop condition of the enclosing graph (if any), so a graph while-loop over
+// these kernels always ends.
+//
+// Tensor-core (tcgen05) gather + contract in 3-term TF32 split precision, per
+// tile of 128 determinants (one per TMEM lane, two threads each):
+//   1. gather   D[I, Q] = sum_{links of I} sign * c[J]   into shared memory,
+//               FP32, laid out as the K-major no-swizzle canonical operand A
+//               (8-row x 16-byte core matrices); thread r gathers the alpha
+//               links of row r into A, thread r + 128 the beta links into the
+//               A_lo buffer, so every element has one writer;
+//   2. split    D = alpha + beta part = D_hi + D_lo, both TF32, in place;
+//   3. MMA      G^T = D_hi W_hi + D_hi W_lo + D_lo W_hi  (M=128, N=Np, K=8 per
+//               instruction), issued by one thread, accumulated in TMEM (FP32);
+//   4. epilogue tcgen05.ld: warps w and w + 4 read the lanes of quadrant w,
+//               half of the columns each -> G[P][I] (FP32) in global.
+// W (symmetric, packed pairs) is split once per CTA into TF32 hi/lo operand B
+// that stays in shared memory.  The dropped D_lo W_lo term and the TF32
+// rounding of the lo parts leave a relative error of about 2^-21 per product.
+// Every wait on the MMA-completion mbarrier is bounded; on timeout the kernel
+// raises bit 0 of *status, waits once more (bounded) for its MMAs, frees its
+// TMEM and returns.
+//
+// Batched kernels: one launch of each serves every solve of a batch through
+// the device job table (batch.h), a work queue of (solve, virtual block)
+// items; the tensor-core kernel takes (solve, tile) items from an atomic
+// queue and reloads a solve's W operand when the solve changes.  A final
+// one-thread kernel ends the graph while-loop when any solve's controller has
+// halted, so the host can act on it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "batch.h"
+#include "ctl.h"
+#include "sbci_internal.h"
+#include "sigma_body.cuh"
+#include "step_body.cuh"
+#include "tc_body.cuh"
+
+namespace sbci {
+
+// Largest dynamic shared memory a launch of kernel f may opt into on the
+// current device: the per-block opt-in limit minus f's static shared memory.
+static cudaError_t max_dynamic_smem(const void *f, int *bytes) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  *bytes = optin - (int)fa.sharedSizeBytes;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- one solve
+
+__device__ __forceinline__ void halt_loop(unsigned long long cond) {
+  if (cond && blockIdx.x == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_update_ctl(StepArgs a) {
+  if (a.ctl->halt) {
+    halt_loop(a.cond);
+    return;
+  }
+  const bool halted = update_body(a, blockIdx.x, gridDim.x);
+  if (halted && a.cond && threadIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_project_ctl(StepArgs a) {
+  if (a.ctl->halt) {
+    halt_loop(a.cond);
+    return;
+  }
+  project_body(a, blockIdx.x, gridDim.x);
+}
+
+int step_grid(long long n, int nsm) {
+  long long g = (n + 4 * kStepThreads - 1) / (4 * kStepThreads);  // ~4 elements per thread
+  if (g > 2LL * nsm) g = 2LL * nsm;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_update_ctl(const StepArgs &a, int grid, cudaStream_t s) {
+  k_update_ctl<<<grid, kStepThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_ctl(const StepArgs &a, int grid, cudaStream_t s) {
+  k_project_ctl<<<grid, kStepThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(kScTile, 3) k_scatter(SigmaArgs a) {
+  if (a.ctl && a.ctl->halt) {
+    if (a.cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+    return;
+  }
+  const bool halted = scatter_body<AccT>(a, blockIdx.x, gridDim.x);
+  if (halted && a.cond && threadIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+}
+
+int scatter_grid(long long ndet, int nsm) {
+  long long g = (ndet + kScTile - 1) / kScTile;
+  if (g > 8LL * nsm) g = 8LL * nsm;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename AccT>
+static cudaError_t launch_sc_t(const SigmaArgs &a, cudaStream_t s) {
+  k_scatter<AccT><<<a.grid, kScTile, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s) {
+  return prec == 0 ? launch_sc_t<double>(a, s) : launch_sc_t<float>(a, s);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_gather_contract_tc(SigmaArgs a, int Kp, int Np, uint32_t tmem_cols, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  TcSmem sm;
+  sm.A = reinterpret_cast<float *>(smem);
+  sm.Alo = sm.A + kTcM * Kp;
+  sm.Bhi = reinterpret_cast<uint32_t *>(sm.Alo + kTcM * Kp);
+  sm.Blo = sm.Bhi + Np * Kp;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm.Blo + Np * Kp);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+  sm.sA = smem_u32(sm.A);
+  sm.sAlo = smem_u32(sm.Alo);
+  sm.sBhi = smem_u32(sm.Bhi);
+  sm.sBlo = smem_u32(sm.Blo);
+  sm.sbar = smem_u32(mbar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const double *cin = a.c;
+  const float *cinf = nullptr;
+  if (a.ctl) {
+    if (a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
+    cin = a.ctl->zn;
+    cinf = a.ctl->zf;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm.sbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_load_B(a, Kp, Np, sm);
+  const uint32_t tmem = *tmem_slot;
+  const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+    ok = cinf ? tc_tile(a, cinf, tile, Kp, Np, sm, tmem, phase) : tc_tile(a, cin, tile, Kp, Np, sm, tmem, phase);
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1);
+    mbar_wait(sm.sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+// Operand sizes of the TF32 split kernel for npair packed pairs.
+bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
+  const int kp = (npair + 7) / 8 * 8;
+  const int np = (npair + 15) / 16 * 16;
+  uint32_t c = 32;
+  while (c < (uint32_t)np) c <<= 1;
+  const size_t bytes = (size_t)(2 * kTcM * kp + 2 * np * kp) * 4 + 16;
+  *Kp = kp;
+  *Np = np;
+  *cols = c;
+  *smem = bytes;
+  return np <= 256 && bytes <= 227 * 1024;
+}
+
+// Grid of the persistent tensor-core kernel (resident CTAs, capped by TMEM
+// columns), computed outside any stream capture.  0 if the shape is unsupported.
+int tc_grid(int npair, long long ndet, int num_sms) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!tc_dims(npair, &Kp, &Np, &cols, &smem)) return 0;
+  // the opt-in limit is a property of the function shared by all contexts:
+  // always the largest, so that a context of another shape cannot lower it
+  int optin = 0;
+  if (max_dynamic_smem((const void *)k_gather_contract_tc, &optin) != cudaSuccess || (int)smem > optin ||
+      cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+          cudaSuccess)
+    return 0;
+  // all of the unified L1/shared storage as shared memory: two CTAs per SM
+  // whenever the operands fit twice
+  if (cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem) !=
+      cudaSuccess)
+    return 0;
+  if (per_sm < 1) per_sm = 1;
+  if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
+  const long long ntiles = (ndet + kTcM - 1) / kTcM;
+  long long grid = (long long)num_sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  return (int)grid;
+}
+
+__global__ void k_split_W(const double *W, int npair, int Kp, int Np, uint32_t *out) {
+  const int nb = Np * Kp;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb; idx += gridDim.x * blockDim.x) {
+    const int n = idx / Kp, k = idx - n * Kp;
+    split_W_elem(W, npair, n, k, &out[opnd_off(n, k, Kp)], &out[nb + opnd_off(n, k, Kp)]);
+  }
+}
+
+cudaError_t launch_split_W(const double *W, int npair, int Kp, int Np, uint32_t *out, cudaStream_t s) {
+  const int nb = Np * Kp;
+  k_split_W<<<(nb + 255) / 256, 256, 0, s>>>(W, npair, Kp, Np, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!tc_dims(a.npair, &Kp, &Np, &cols, &smem) || grid < 1) return cudaErrorInvalidValue;
+  k_gather_contract_tc<<<grid, kTcThreads, smem, s>>>(a, Kp, Np, cols, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched
+
+__device__ __forceinline__ int find_job(const int *off, int njobs, int item) {
+  int lo = 0, hi = njobs;  // off[lo] <= item < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_update_batch(BatchTable *bt) {
+  const int nj = bt->njobs;
+  const int total = bt->off_step[nj];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = find_job(bt->off_step, nj, item);
+    const int vb = item - bt->off_step[j], nvb = bt->off_step[j + 1] - bt->off_step[j];
+    if (update_body(bt->job[j].step, vb, nvb) && threadIdx.x == 0) bt->halted[j] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_project_batch(BatchTable *bt) {
+  const int nj = bt->njobs;
+  const int total = bt->off_step[nj];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = find_job(bt->off_step, nj, item);
+    const int vb = item - bt->off_step[j], nvb = bt->off_step[j + 1] - bt->off_step[j];
+    project_body(bt->job[j].step, vb, nvb);
+  }
+}
+
+// Items in reverse job order: the tensor-core kernel just wrote the G of the
+// last jobs, which are the ones still in L2.
+__global__ void __launch_bounds__(kScTile, 2) k_scatter_batch(BatchTable *bt) {
+  const int nj = bt->njobs;
+  const int total = bt->off_sc[nj];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int item = total - 1 - it;
+    const int j = find_job(bt->off_sc, nj, item);
+    const int vb = item - bt->off_sc[j], nvb = bt->off_sc[j + 1] - bt->off_sc[j];
+    if (scatter_body<float>(bt->job[j].sig, vb, nvb) && threadIdx.x == 0) bt->halted[j] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_tc_batch(BatchTable *bt, int Kpmax, int Npmax, uint32_t tmem_cols, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  TcSmem sm;
+  sm.A = reinterpret_cast<float *>(smem);
+  sm.Alo = sm.A + kTcM * Kpmax;
+  sm.Bhi = reinterpret_cast<uint32_t *>(sm.Alo + kTcM * Kpmax);
+  sm.Blo = sm.Bhi + Npmax * Kpmax;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm.Blo + Npmax * Kpmax);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+  __shared__ int s_item;
+  sm.sA = smem_u32(sm.A);
+  sm.sAlo = smem_u32(sm.Alo);
+  sm.sBhi = smem_u32(sm.Bhi);
+  sm.sBlo = smem_u32(sm.Blo);
+  sm.sbar = smem_u32(mbar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nj = bt->njobs;
+  const int total = bt->off_tc[nj];
+  if (total == 0) return;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm.sbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t phase = 0;
+  bool ok = true;
+  int cur = -1;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(&bt->tc_next, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    const int j = find_job(bt->off_tc, nj, item);
+    const BatchJob &J = bt->job[j];
+    if (J.step.ctl->halt) continue;  // block-uniform
+    if (j != cur) {
+      tc_load_B(J.sig, J.Kp, J.Np, sm);
+      cur = j;
+    }
+    const float *zf = J.step.ctl->zf;
+    const long long tile = item - bt->off_tc[j];
+    ok = zf ? tc_tile(J.sig, zf, tile, J.Kp, J.Np, sm, tmem, phase)
+            : tc_tile(J.sig, J.step.ctl->zn, tile, J.Kp, J.Np, sm, tmem, phase);
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1);
+    mbar_wait(sm.sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+// Ends a batched loop body (kMaxBatch threads, one per job): resets the tile
+// queue, counts the body, and ends the while-loop when a solve halted (or the
+// table is empty), so the host can act on it.
+__global__ void __launch_bounds__(kMaxBatch) k_batch_end(BatchTable *bt, unsigned long long cond) {
+  const int j = threadIdx.x, nj = bt->njobs;
+  int h = 0;
+  if (j < nj) {
+    if (bt->job[j].step.ctl->halt) bt->halted[j] = 1;
+    h = bt->halted[j];
+  }
+  const int stop = __syncthreads_or(h) || nj == 0;
+  if (j == 0) {
+    bt->tc_next = 0u;
+    bt->bodies += 1ull;
+    bt->stop = stop;
+    if (stop && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+  }
+}
+
+cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
+  if (Kp < 8 || Np < 16 || Kp % 8 || Np % 16 || Np > 256) return cudaErrorInvalidValue;
+  cfg->Kp = Kp;
+  cfg->Np = Np;
+  cfg->cols = 32;
+  while (cfg->cols < (uint32_t)Np) cfg->cols <<= 1;
+  cfg->smem = (size_t)(2 * kTcM * Kp + 2 * Np * Kp) * 4 + 16;
+  if (cfg->smem > 227 * 1024) return cudaErrorInvalidValue;
+  // the opt-in limit is a property of the function, shared by every class and
+  // context: always the largest the device allows (minus the kernel's static
+  // shared memory), so no later setting can fail a launch
+  int optin = 0;
+  cudaError_t e = max_dynamic_smem((const void *)k_tc_batch, &optin);
+  if (e != cudaSuccess) return e;
+  if ((int)cfg->smem > optin) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tc_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_batch, kTcThreads, cfg->smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if ((uint32_t)per_sm * cfg->cols > 512) per_sm = (int)(512 / cfg->cols);
+  cfg->tc_per_sm_max = per_sm;
+  // defaults until the autotuner has measured this class
+  cfg->ctas[BK_UPDATE] = 2 * num_sms;
+  cfg->ctas[BK_PROJECT] = 4 * num_sms;
+  cfg->ctas[BK_TC] = num_sms * per_sm;
+  cfg->ctas[BK_SCATTER] = 3 * num_sms;
+  cfg->ctas[BK_END] = 1;
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch_kernel(int which, const BatchConfig &cfg, BatchTable *d_table, int *status,
+                                unsigned long long cond, cudaStream_t s) {
+  switch (which) {
+    case BK_UPDATE: k_update_batch<<<cfg.ctas[BK_UPDATE], kStepThreads, 0, s>>>(d_table); break;
+    case BK_PROJECT: k_project_batch<<<cfg.ctas[BK_PROJECT], kStepThreads, 0, s>>>(d_table); break;
+    case BK_TC:
+      k_tc_batch<<<cfg.ctas[BK_TC], kTcThreads, cfg.smem, s>>>(d_table, cfg.Kp, cfg.Np, cfg.cols, status);
+      break;
+    case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, 0, s>>>(d_table); break;
+    case BK_END: k_batch_end<<<1, kMaxBatch, 0, s>>>(d_table, cond); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t build_batch_graph(const BatchConfig &cfg, BatchTable *d_table, int *status, cudaStream_t s,
+                              cudaGraph_t *graph, cudaGraphExec_t *exec) {
+  cudaError_t e;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return e;
+  for (int k = 0; k < BK_COUNT; ++k) launch_batch_kernel(k, cfg, d_table, status, (unsigned long long)h, s);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(s, &captured);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) return e;
+  *graph = g;
+  return cudaSuccess;
+}
+
+}  // namespace sbci

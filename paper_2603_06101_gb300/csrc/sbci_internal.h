@@ -30,23 +30,36 @@ __host__ __device__ inline bool link_neg(uint32_t v) { return (v & kSignBit) != 
 #ifdef __CUDACC__
 // Visits the links of one string U at a time: the U list entries, then the U
 // gathered values (independent loads, all in flight), then the U updates.
+// Entry e of the list is lst[e * stride] (stride 1: a row of a [N][nlink]
+// table; stride N: a column of the transposed [nlink][N] table, whose loads
+// coalesce across threads that hold consecutive strings).
 // load(v) returns the gathered value of link word v; use(v, x) consumes it.
 template <int U, typename T, typename Load, typename Use>
-__device__ __forceinline__ void for_links(const uint32_t *lst, int n, Load load, Use use) {
+__device__ __forceinline__ void for_links(const uint32_t *lst, int n, long long stride, Load load, Use use) {
   int e = 0;
   for (; e + U <= n; e += U) {
     uint32_t v[U];
     T x[U];
 #pragma unroll
-    for (int j = 0; j < U; ++j) v[j] = __ldg(lst + e + j);
+    for (int j = 0; j < U; ++j) v[j] = __ldg(lst + (e + j) * stride);
 #pragma unroll
     for (int j = 0; j < U; ++j) x[j] = load(v[j]);
 #pragma unroll
     for (int j = 0; j < U; ++j) use(v[j], x[j]);
   }
-  for (; e < n; ++e) {
-    const uint32_t v = __ldg(lst + e);
-    use(v, load(v));
+  if (e < n) {  // the partial last batch: predicated, its loads still issued together
+    const int m = n - e;
+    uint32_t v[U];
+    T x[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (j < m) v[j] = __ldg(lst + (e + j) * stride);
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (j < m) x[j] = load(v[j]);
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (j < m) use(v[j], x[j]);
   }
 }
 #endif
@@ -80,8 +93,11 @@ struct SigmaArgs {
   double *sigma;         // [Na*Nb]
   void *G;               // [npair][ndet] FP64 or FP32 scratch
   const uint32_t *link_a, *link_b;
+  const uint32_t *link_bT;  // beta lists transposed, [nlink_b][nb]
   const double *W;       // [npair_pad][npair] FP64 (rows padded with zeros)
   const float *Wf;       // FP32 copy (same layout), SBCI_FP32 mode
+  const uint32_t *Wtc;   // TF32 hi then lo of W in the tensor-core operand layout
+                         // ([2][Np*Kp], see tc_body.cuh), or nullptr
   int na, nb, nlink_a, nlink_b, npair, npair_pad;
   long long ndet;
   // epilogue dots of sigma against up to three vectors (nullptr = unused)
@@ -103,9 +119,11 @@ cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s)
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
 int scatter_grid(long long ndet, int nsm);
 cudaError_t prepare_sigma_kernels();
-// tcgen05 TF32x3 gather + contract (kernels_tc.cu); writes FP32 G like prec 1.
+// tcgen05 TF32x3 gather + contract (kernels_loop.cu); writes FP32 G like prec 1.
 bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
 int tc_grid(int npair, long long ndet, int num_sms);
+// Writes W (FP64 [npair_pad][npair]) as TF32 hi/lo operand B, [2][Np*Kp].
+cudaError_t launch_split_W(const double *W, int npair, int Kp, int Np, uint32_t *out, cudaStream_t s);
 cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
@@ -142,8 +160,16 @@ namespace sbci {
 bool ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream);
 // Serving support (api.cpp): asynchronous rounds of an active solve.
 sbci_status solve_round_launch(sbci_ctx *c);
-sbci_status solve_round_finish(sbci_ctx *c, int *done);
+sbci_status solve_round_finish(sbci_ctx *c, int *done, bool own_graph = true);
 cudaStream_t ctx_stream(const sbci_ctx *c);
+struct BatchJob;
+// Fills the batched-kernel view of an active TF32x3 solve with npair within the
+// batched kernels' limit; false if the solve cannot join a batch.
+bool ctx_batch_job(sbci_ctx *c, BatchJob *j);
+int ctx_step_blocks(const sbci_ctx *c);
+int ctx_scatter_blocks(const sbci_ctx *c);
+long long ctx_ndet(const sbci_ctx *c);
+long long ctx_launch_count(const sbci_ctx *c);
 size_t ctx_device_bytes(int norb, int nalpha, int nbeta, int k);
 
 }  // namespace sbci

@@ -10,16 +10,28 @@
 // reached the end of its graph round it handles the controller event (state
 // converged, stage switch, cap) and launches the next round, or retires the
 // finished solve and frees its slot and memory.
+//
+// Batched mode (the default): solves that can share the batched persistent
+// kernels (TF32x3 sigma, n <= 12) do not get a graph each; the server keeps a
+// device job table of them and runs ONE graph while-loop whose four step
+// kernels walk the table as a work queue, so a single launch of each kernel
+// advances every batched solve.  The loop ends when any solve's controller
+// halts; the server then acts on those solves, rebuilds the table (new
+// arrivals join, finished solves leave) and launches the next round.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/sbci.h"
+#include "batch.h"
 #include "sbci_internal.h"
 
 using namespace sbci;
@@ -47,8 +59,153 @@ struct SolveSlot {
   sbci_ctx *ctx = nullptr;
   cudaEvent_t ev = nullptr;
   bool in_flight = false;
+  bool batched = false;  // advanced by the batch graph instead of its own graph
   double t_admit = 0.0;
 };
+
+// Online autotuner of the batched kernels' launch shapes (CTAs per kernel),
+// one per operand class.  The first bodies of a class run one kernel at a
+// time bracketed by CUDA events, each kernel with the next of its candidate
+// CTA counts; once every candidate has kTuneSamples timings, the one with the
+// lowest median is kept for each kernel and the class's graph is built with
+// it.  CTA counts never change a solve's arithmetic (its virtual blocks and
+// tiles are fixed by the solve), so tuning changes timing only.
+constexpr int kTuneSamples = 3;
+
+struct ClassGraph {
+  BatchConfig cfg{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool tuned = false;
+  std::vector<int> cand[BK_COUNT];
+  std::vector<std::vector<float>> ms[BK_COUNT];
+  long long tune_bodies = 0;
+};
+
+void tune_init(ClassGraph &g, int nsm) {
+  g.cand[BK_UPDATE] = {nsm, 2 * nsm, 4 * nsm};
+  g.cand[BK_PROJECT] = {nsm, 2 * nsm, 4 * nsm, 8 * nsm};
+  for (int k = 1; k <= g.cfg.tc_per_sm_max; ++k) g.cand[BK_TC].push_back(k * nsm);
+  g.cand[BK_SCATTER] = {nsm, 2 * nsm, 3 * nsm, 6 * nsm};
+  g.cand[BK_END] = {1};
+  for (int k = 0; k < BK_COUNT; ++k) g.ms[k].assign(g.cand[k].size(), std::vector<float>());
+}
+
+bool tune_complete(const ClassGraph &g) {
+  for (int k = 0; k < BK_COUNT; ++k)
+    for (const auto &v : g.ms[k])
+      if ((int)v.size() < kTuneSamples) return false;
+  return true;
+}
+
+void tune_choose(ClassGraph &g) {
+  for (int k = 0; k < BK_COUNT; ++k) {
+    int best = 0;
+    float best_t = 0.f;
+    for (size_t c = 0; c < g.cand[k].size(); ++c) {
+      std::vector<float> v = g.ms[k][c];
+      std::sort(v.begin(), v.end());
+      const float med = v[v.size() / 2];
+      if (c == 0 || med < best_t) {
+        best = (int)c;
+        best_t = med;
+      }
+    }
+    g.cfg.ctas[k] = g.cand[k][best];
+  }
+  g.tuned = true;
+}
+
+// Event timing of single launches (kernel timing and tuning).
+struct KernelStats {
+  bool on = false;
+  long long launches[BK_COUNT] = {};
+  double ms[BK_COUNT] = {};
+};
+
+struct GraphCache {
+  std::map<int, ClassGraph> m;
+  cudaEvent_t ev[2 * BK_COUNT] = {};
+  int *h_stop = nullptr;  // pinned
+  ClassGraph *get(int Kp, int Np, int nsm) {
+    const int key = Np * 4096 + Kp;
+    auto it = m.find(key);
+    if (it != m.end()) return &it->second;
+    ClassGraph g;
+    if (batch_config(nsm, Kp, Np, &g.cfg) != cudaSuccess) return nullptr;
+    tune_init(g, nsm);
+    return &(m[key] = g);
+  }
+  void destroy() {
+    for (auto &kv : m) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    m.clear();
+    for (cudaEvent_t &e : ev)
+      if (e) cudaEventDestroy(e), e = nullptr;
+    if (h_stop) cudaFreeHost(h_stop);
+    h_stop = nullptr;
+  }
+};
+
+// One batch round of class cg on stream s: the class's graph loop once it is
+// tuned (unless kernel timing is on or SBCI_NO_GRAPH=1, for profilers that do
+// not follow graph loops); otherwise the same bodies launched kernel by
+// kernel, each bracketed by events, until a body ends with a halted solve.
+cudaError_t run_round(GraphCache &gc, ClassGraph &cg, BatchTable *d_table, int *d_status, cudaStream_t s,
+                      KernelStats *stats) {
+  const char *env = std::getenv("SBCI_NO_GRAPH");
+  const bool no_graph = env && env[0] == '1';
+  const bool timing = stats && stats->on;
+  cudaError_t e = cudaSuccess;
+  if (cg.tuned && !cg.exec && (e = build_batch_graph(cg.cfg, d_table, d_status, s, &cg.graph, &cg.exec)) != cudaSuccess)
+    return e;
+  if (cg.tuned && !timing && !no_graph) return cudaGraphLaunch(cg.exec, s);
+  for (cudaEvent_t &x : gc.ev)
+    if (!x && (e = cudaEventCreate(&x)) != cudaSuccess) return e;
+  if (!gc.h_stop && (e = cudaMallocHost((void **)&gc.h_stop, sizeof(int))) != cudaSuccess) return e;
+  for (;;) {
+    BatchConfig cfg = cg.cfg;
+    int ci[BK_COUNT];
+    for (int k = 0; k < BK_COUNT; ++k) {
+      ci[k] = cg.tuned ? -1 : (int)(cg.tune_bodies % (long long)cg.cand[k].size());
+      if (ci[k] >= 0) cfg.ctas[k] = cg.cand[k][ci[k]];
+    }
+    for (int k = 0; k < BK_COUNT; ++k) {
+      if ((e = cudaEventRecord(gc.ev[2 * k], s)) != cudaSuccess) return e;
+      if ((e = launch_batch_kernel(k, cfg, d_table, d_status, 0ull, s)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(gc.ev[2 * k + 1], s)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemcpyAsync(gc.h_stop, &d_table->stop, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return e;
+    for (int k = 0; k < BK_COUNT; ++k) {
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, gc.ev[2 * k], gc.ev[2 * k + 1])) != cudaSuccess) return e;
+      if (ci[k] >= 0) cg.ms[k][ci[k]].push_back(t);
+      if (timing) {
+        stats->launches[k] += 1;
+        stats->ms[k] += t;
+      }
+    }
+    if (!cg.tuned) {
+      cg.tune_bodies += 1;
+      if (tune_complete(cg)) tune_choose(cg);
+    }
+    if (*gc.h_stop) return cudaSuccess;
+  }
+}
+
+// Operand class of a table: the largest Kp and Np of its jobs.
+void table_class(const BatchTable &t, int *Kp, int *Np) {
+  *Kp = 8;
+  *Np = 16;
+  for (int j = 0; j < t.njobs; ++j) {
+    if (t.job[j].Kp > *Kp) *Kp = t.job[j].Kp;
+    if (t.job[j].Np > *Np) *Np = t.job[j].Np;
+  }
+}
 
 struct Result {
   int done = 0;
@@ -63,10 +220,21 @@ struct Result {
 struct sbci_server {
   size_t budget = 0, used = 0;
   int max_slots = 1;
+  int mode = 1;  // 1: batched persistent kernels for eligible solves; 0: a graph per solve
   std::deque<Request> queue;
   std::vector<SolveSlot> slots;
   std::map<long long, Result> results;
   long long next_ticket = 1;
+  // batch engine
+  cudaStream_t stream = nullptr;
+  cudaEvent_t batch_ev = nullptr;
+  BatchTable *d_table = nullptr, *h_table = nullptr;
+  int *d_status = nullptr;
+  GraphCache graphs;
+  bool batch_ok = false;  // the batch engine could be set up
+  bool batch_in_flight = false;
+  std::vector<int> batch_slots;  // table row -> slot index
+  int nsm = 1;
 };
 
 namespace {
@@ -124,7 +292,11 @@ sbci_status admit(sbci_server *sv) {
     sbci_status st = sbci_init_integrals(&sl.ctx, sl.req.norb, sl.req.nalpha, sl.req.nbeta,
                                          sl.req.h1.data(), sl.req.eri.data(), sl.req.e_core, nullptr);
     if (st == SBCI_OK) st = sbci_begin(sl.ctx, sl.req.k, &sl.req.p, nullptr);
-    if (st == SBCI_OK) st = launch_round(sl);
+    if (st == SBCI_OK) {
+      BatchJob probe;
+      sl.batched = sv->mode == 1 && sv->batch_ok && ctx_batch_job(sl.ctx, &probe);
+      if (!sl.batched) st = launch_round(sl);
+    }
     if (st != SBCI_OK) {
       if (sl.ctx) {
         retire(sv, sl, st);
@@ -144,7 +316,302 @@ sbci_status admit(sbci_server *sv) {
 
 }  // namespace
 
+namespace {
+
+// Rebuilds the job table from the batched slots and launches one round.
+sbci_status launch_batch_round(sbci_server *sv) {
+  BatchTable &t = *sv->h_table;
+  sv->batch_slots.clear();
+  int nj = 0;
+  t.off_step[0] = t.off_sc[0] = t.off_tc[0] = 0;
+  for (int i = 0; i < (int)sv->slots.size(); ++i) {
+    SolveSlot &sl = sv->slots[i];
+    if (!sl.used || !sl.batched || nj >= kMaxBatch) continue;
+    if (!ctx_batch_job(sl.ctx, &t.job[nj])) {
+      // no longer batchable (its state fell back to FP64 sigma): own graph loop from now on
+      sl.batched = false;
+      const sbci_status st = launch_round(sl);
+      if (st != SBCI_OK) retire(sv, sl, st);
+      continue;
+    }
+    t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(sl.ctx);
+    t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(sl.ctx);
+    t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(sl.ctx) + 127) / 128);
+    t.halted[nj] = 0;
+    sv->batch_slots.push_back(i);
+    ++nj;
+  }
+  t.njobs = nj;
+  t.tc_next = 0;
+  if (nj == 0) return SBCI_OK;
+  int Kp, Np;
+  table_class(t, &Kp, &Np);
+  ClassGraph *cg = sv->graphs.get(Kp, Np, sv->nsm);
+  if (!cg) {
+    set_error("server: no batch configuration for this operand class");
+    return SBCI_ERR_CUDA;
+  }
+  // (a round of a class still being tuned runs host-driven and returns when done)
+  if (cudaMemcpyAsync(sv->d_table, sv->h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, sv->stream) !=
+          cudaSuccess ||
+      run_round(sv->graphs, *cg, sv->d_table, sv->d_status, sv->stream, nullptr) != cudaSuccess ||
+      cudaEventRecord(sv->batch_ev, sv->stream) != cudaSuccess) {
+    set_error("server: batch launch failed");
+    return SBCI_ERR_CUDA;
+  }
+  sv->batch_in_flight = true;
+  return SBCI_OK;
+}
+
+// After a batch round: act on every halted solve, then launch the next round.
+sbci_status progress_batch(sbci_server *sv) {
+  if (sv->batch_in_flight) {
+    const cudaError_t q = cudaEventQuery(sv->batch_ev);
+    if (q == cudaErrorNotReady) return SBCI_OK;
+    sv->batch_in_flight = false;
+    if (q != cudaSuccess) {
+      set_error(std::string("server: ") + cudaGetErrorString(q));
+      return SBCI_ERR_CUDA;
+    }
+    int status = 0;
+    if (cudaMemcpy(&status, sv->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(sv->h_table->halted, sv->d_table->halted, sizeof(int) * kMaxBatch,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_error("server: reading the batch table failed");
+      return SBCI_ERR_CUDA;
+    }
+    if (status) {
+      set_error("a bounded device wait ran out (batched tensor-core kernel)");
+      return SBCI_ERR_TIMEOUT;
+    }
+    for (int j = 0; j < (int)sv->batch_slots.size(); ++j) {
+      if (!sv->h_table->halted[j]) continue;  // still running: stays in the next round as is
+      SolveSlot &sl = sv->slots[sv->batch_slots[j]];
+      int done = 0;
+      const sbci_status st = solve_round_finish(sl.ctx, &done, false);
+      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
+        retire(sv, sl, st);
+        continue;
+      }
+      if (done) retire(sv, sl, SBCI_OK);
+    }
+  }
+  return launch_batch_round(sv);
+}
+
+// The batch engine of sbci_solve_batch: one per device, made on first use and
+// kept (stream, job table, per-class graphs and tuning), so that a call pays
+// no set-up; calls on one device are serialised by its mutex.
+struct Engine {
+  std::mutex mu;
+  bool ready = false;
+  int nsm = 1;
+  cudaStream_t stream = nullptr;
+  BatchTable *d_table = nullptr, *h_table = nullptr;
+  int *d_status = nullptr;
+  GraphCache graphs;
+  KernelStats prof;  // sbci_batch_profile
+};
+
+constexpr int kMaxDevices = 64;
+Engine g_engines[kMaxDevices];
+const char *const kBatchKernelName[BK_COUNT] = {"batch_update", "batch_project", "batch_gather_contract_tc",
+                                                "batch_scatter", "batch_end"};
+
+cudaError_t engine_setup(Engine &eng, int dev) {
+  if (eng.ready) return cudaSuccess;
+  cudaError_t e = cudaDeviceGetAttribute(&eng.nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && !eng.stream) e = cudaStreamCreateWithFlags(&eng.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !eng.d_table) e = cudaMalloc((void **)&eng.d_table, sizeof(BatchTable));
+  if (e == cudaSuccess && !eng.h_table) e = cudaMallocHost((void **)&eng.h_table, sizeof(BatchTable));
+  if (e == cudaSuccess && !eng.d_status) e = cudaMalloc((void **)&eng.d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(eng.d_status, 0, sizeof(int));
+  eng.ready = e == cudaSuccess;
+  return e;
+}
+
+cudaError_t engine_round(Engine &eng) {
+  int Kp, Np;
+  table_class(*eng.h_table, &Kp, &Np);
+  ClassGraph *cg = eng.graphs.get(Kp, Np, eng.nsm);
+  if (!cg) return cudaErrorInvalidValue;
+  return run_round(eng.graphs, *cg, eng.d_table, eng.d_status, eng.stream, &eng.prof);
+}
+
+Engine *current_engine(std::string *why) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *why = "no usable CUDA device";
+    return nullptr;
+  }
+  return &g_engines[dev];
+}
+
+}  // namespace
+
 extern "C" {
+
+sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
+                             sbci_report *rep, long long *launches) {
+  if (!ctx || n < 1 || n > kMaxBatch || k < 1 || !energies) {
+    set_error("sbci_solve_batch: need 1 <= n <= 64 contexts, k >= 1 and energies");
+    return SBCI_ERR_INVALID;
+  }
+  std::string why;
+  Engine *pe = current_engine(&why);
+  int dev = 0;
+  if (!pe || cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("sbci_solve_batch: " + why);
+    return SBCI_ERR_CUDA;
+  }
+  Engine &eng = *pe;
+  std::lock_guard<std::mutex> lock(eng.mu);
+  if (engine_setup(eng, dev) != cudaSuccess) {
+    set_error("sbci_solve_batch: CUDA set-up failed");
+    return SBCI_ERR_CUDA;
+  }
+  std::vector<int> done(n, 0);
+  long long host_launches0 = 0;
+  for (int i = 0; i < n; ++i) host_launches0 += ctx_launch_count(ctx[i]);
+  for (int i = 0; i < n; ++i) {
+    const sbci_status st = sbci_begin(ctx[i], k, params, nullptr);
+    if (st != SBCI_OK) return st;
+  }
+  std::memset(eng.h_table, 0, sizeof(BatchTable));
+  if (cudaMemsetAsync(eng.d_status, 0, sizeof(int), eng.stream) != cudaSuccess) {
+    set_error("sbci_solve_batch: CUDA set-up failed");
+    return SBCI_ERR_CUDA;
+  }
+  unsigned long long bodies = 0;
+  sbci_status worst = SBCI_OK;
+  for (;;) {
+    BatchTable &t = *eng.h_table;
+    std::vector<int> row;
+    int nj = 0;
+    t.off_step[0] = t.off_sc[0] = t.off_tc[0] = 0;
+    for (int i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      if (!ctx_batch_job(ctx[i], &t.job[nj])) {  // not batchable: solve it on its own
+        double *E = energies + (size_t)i * k;
+        sbci_status st = SBCI_OK;
+        while (!done[i]) {
+          st = solve_round_launch(ctx[i]);
+          if (st != SBCI_OK) return st;
+          st = solve_round_finish(ctx[i], &done[i]);
+          if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
+        }
+        st = sbci_finish(ctx[i], E, nullptr, rep ? rep + (size_t)i * k : nullptr);
+        if (st != SBCI_OK) worst = st;
+        continue;
+      }
+      t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(ctx[i]);
+      t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(ctx[i]);
+      t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(ctx[i]) + 127) / 128);
+      t.halted[nj] = 0;
+      row.push_back(i);
+      ++nj;
+    }
+    if (nj == 0) break;
+    t.njobs = nj;
+    t.tc_next = 0;
+    t.bodies = 0;
+    int status = 0;
+    unsigned long long round_bodies = 0;
+    if (cudaMemcpyAsync(eng.d_table, eng.h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, eng.stream) !=
+            cudaSuccess ||
+        engine_round(eng) != cudaSuccess ||
+        cudaMemcpyAsync(t.halted, eng.d_table->halted, sizeof(int) * kMaxBatch, cudaMemcpyDeviceToHost,
+                        eng.stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, eng.d_status, sizeof(int), cudaMemcpyDeviceToHost, eng.stream) != cudaSuccess ||
+        cudaMemcpyAsync(&round_bodies, &eng.d_table->bodies, sizeof(round_bodies), cudaMemcpyDeviceToHost,
+                        eng.stream) != cudaSuccess ||
+        cudaStreamSynchronize(eng.stream) != cudaSuccess) {
+      set_error("sbci_solve_batch: batch round failed");
+      return SBCI_ERR_CUDA;
+    }
+    bodies += round_bodies;
+    if (status) {
+      set_error("a bounded device wait ran out (batched tensor-core kernel)");
+      return SBCI_ERR_TIMEOUT;
+    }
+    for (int j = 0; j < nj; ++j) {
+      if (!t.halted[j]) continue;
+      const int i = row[j];
+      const sbci_status st = solve_round_finish(ctx[i], &done[i], false);
+      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
+      if (done[i]) {
+        const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
+        if (fs != SBCI_OK) worst = fs;
+      }
+    }
+  }
+  if (launches) {
+    long long host_launches1 = 0;
+    for (int i = 0; i < n; ++i) host_launches1 += ctx_launch_count(ctx[i]);
+    *launches = (long long)(5 * bodies) + (host_launches1 - host_launches0);
+  }
+  return worst;
+}
+
+sbci_status sbci_batch_profile(int enable) {
+  std::string why;
+  Engine *pe = current_engine(&why);
+  if (!pe) {
+    set_error("sbci_batch_profile: " + why);
+    return SBCI_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(pe->mu);
+  for (int k = 0; k < BK_COUNT; ++k) {
+    pe->prof.launches[k] = 0;
+    pe->prof.ms[k] = 0.0;
+  }
+  pe->prof.on = enable != 0;
+  return SBCI_OK;
+}
+
+sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n) {
+  std::string why;
+  Engine *pe = current_engine(&why);
+  if (!pe) {
+    set_error("sbci_batch_profile_read: " + why);
+    return SBCI_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(pe->mu);
+  if (n) *n = BK_COUNT;
+  for (int k = 0; k < BK_COUNT && out && k < cap; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, kBatchKernelName[k], sizeof(out[k].name) - 1);
+    out[k].launches = pe->prof.launches[k];
+    out[k].total_ms = pe->prof.ms[k];
+  }
+  return SBCI_OK;
+}
+
+sbci_status sbci_batch_classes(sbci_batch_class *out, int cap, int *n) {
+  std::string why;
+  Engine *pe = current_engine(&why);
+  if (!pe) {
+    set_error("sbci_batch_classes: " + why);
+    return SBCI_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(pe->mu);
+  int i = 0;
+  for (const auto &kv : pe->graphs.m) {
+    if (out && i < cap) {
+      const ClassGraph &g = kv.second;
+      sbci_batch_class &r = out[i];
+      r.Kp = g.cfg.Kp;
+      r.Np = g.cfg.Np;
+      r.smem_bytes = (int)g.cfg.smem;
+      r.tc_per_sm_max = g.cfg.tc_per_sm_max;
+      r.tuned = g.tuned ? 1 : 0;
+      for (int k = 0; k < BK_COUNT; ++k) r.ctas[k] = g.cfg.ctas[k];
+    }
+    ++i;
+  }
+  if (n) *n = i;
+  return SBCI_OK;
+}
 
 sbci_status sbci_server_create(sbci_server **out, size_t mem_budget_bytes, int max_slots) {
   if (!out || max_slots < 1 || max_slots > 1024) {
@@ -155,6 +622,33 @@ sbci_status sbci_server_create(sbci_server **out, size_t mem_budget_bytes, int m
   sv->budget = mem_budget_bytes;
   sv->max_slots = max_slots;
   sv->slots.resize(max_slots);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sv->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sv->batch_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc((void **)&sv->d_table, sizeof(BatchTable)) != cudaSuccess ||
+      cudaMallocHost((void **)&sv->h_table, sizeof(BatchTable)) != cudaSuccess ||
+      cudaMalloc((void **)&sv->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(sv->d_table, 0, sizeof(BatchTable)) != cudaSuccess ||
+      cudaMemset(sv->d_status, 0, sizeof(int)) != cudaSuccess) {
+    set_error("sbci_server_create: CUDA allocation failed");
+    sbci_server_destroy(sv);
+    return SBCI_ERR_CUDA;
+  }
+  std::memset(sv->h_table, 0, sizeof(BatchTable));
+  // the class of the largest batchable solve: checks that the engine can be set up
+  {
+    int Kp, Np;
+    uint32_t cols;
+    size_t smem;
+    sv->batch_ok = tc_dims(kBatchMaxPair, &Kp, &Np, &cols, &smem) && sv->graphs.get(Kp, Np, sv->nsm) != nullptr;
+  }
+  if (!sv->batch_ok) {
+    set_error("sbci_server_create: building the batch graph failed");
+    sbci_server_destroy(sv);
+    return SBCI_ERR_CUDA;
+  }
   for (SolveSlot &sl : sv->slots) {
     if (cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
       set_error("sbci_server_create: cudaEventCreate failed");
@@ -205,7 +699,7 @@ sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued) 
   sbci_status st = admit(sv);
   if (st != SBCI_OK) return st;
   for (SolveSlot &sl : sv->slots) {
-    if (!sl.used || !sl.in_flight) continue;
+    if (!sl.used || sl.batched || !sl.in_flight) continue;
     const cudaError_t q = cudaEventQuery(sl.ev);
     if (q == cudaErrorNotReady) continue;
     sl.in_flight = false;
@@ -229,6 +723,10 @@ sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued) 
   }
   st = admit(sv);  // slots freed above
   if (st != SBCI_OK) return st;
+  if (sv->mode == 1) {
+    st = progress_batch(sv);
+    if (st != SBCI_OK) return st;
+  }
   int act = 0;
   for (const SolveSlot &sl : sv->slots) act += sl.used ? 1 : 0;
   if (n_active) *n_active = act;
@@ -261,8 +759,23 @@ sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, doubl
   return r.status;
 }
 
+sbci_status sbci_server_set_batching(sbci_server *sv, int on) {
+  if (!sv) {
+    set_error("sbci_server_set_batching: NULL server");
+    return SBCI_ERR_INVALID;
+  }
+  for (const SolveSlot &sl : sv->slots)
+    if (sl.used) {
+      set_error("sbci_server_set_batching: only while no solve is admitted");
+      return SBCI_ERR_INVALID;
+    }
+  sv->mode = on ? 1 : 0;
+  return SBCI_OK;
+}
+
 void sbci_server_destroy(sbci_server *sv) {
   if (!sv) return;
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
   for (SolveSlot &sl : sv->slots) {
     if (sl.ctx) {
       cudaStreamSynchronize(ctx_stream(sl.ctx));
@@ -270,6 +783,12 @@ void sbci_server_destroy(sbci_server *sv) {
     }
     if (sl.ev) cudaEventDestroy(sl.ev);
   }
+  sv->graphs.destroy();
+  if (sv->d_table) cudaFree(sv->d_table);
+  if (sv->h_table) cudaFreeHost(sv->h_table);
+  if (sv->d_status) cudaFree(sv->d_status);
+  if (sv->batch_ev) cudaEventDestroy(sv->batch_ev);
+  if (sv->stream) cudaStreamDestroy(sv->stream);
   delete sv;
 }
 

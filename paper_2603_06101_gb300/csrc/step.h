@@ -1,4 +1,4 @@
-// Arguments of the device-controlled step kernels (kernels_step.cu).
+// Arguments of the device-controlled step kernels (kernels_loop.cu).
 #pragma once
 
 #include <cuda_runtime.h>

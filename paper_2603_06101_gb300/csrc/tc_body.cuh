@@ -1,24 +1,9 @@
-// Tensor-core (tcgen05) gather + contract of the sigma build in 3-term TF32
-// split precision, for sm_103a.
-//
-// Per tile of 128 determinants (one per TMEM lane, two threads each):
-//   1. gather   D[I, Q] = sum_{links of I} sign * c[J]   into shared memory,
-//               FP32, laid out as the K-major no-swizzle canonical operand A
-//               (8-row x 16-byte core matrices); thread r gathers the alpha
-//               links of row r into A, thread r + 128 the beta links into the
-//               A_lo buffer, so every element has one writer;
-//   2. split    D = alpha + beta part = D_hi + D_lo, both TF32, in place;
-//   3. MMA      G^T = D_hi W_hi + D_hi W_lo + D_lo W_hi  (M=128, N=Np, K=8 per
-//               instruction), issued by one thread, accumulated in TMEM (FP32);
-//   4. epilogue tcgen05.ld: warps w and w + 4 read the lanes of quadrant w,
-//               half of the columns each -> G[P][I] (FP32) in global.
-// W (symmetric, packed pairs) is split once per CTA into TF32 hi/lo operand
-// B and stays in shared memory.  The dropped D_lo W_lo term and the TF32
-// rounding of the lo parts leave a relative error of about 2^-21 per product.
-//
-// Every wait on the MMA-completion mbarrier is bounded; on timeout the kernel
-// raises bit 0 of *status, waits once more (bounded) for its MMAs, frees its
-// TMEM and returns.
+// Tensor-core (tcgen05) pieces of the TF32x3 gather + contract, shared by the
+// one-solve kernel and the persistent batched kernel (kernels_loop.cu, which
+// describes the scheme).  The tile arithmetic is additions, conversions and
+// MMAs only (nothing a compiler could contract), so inlining cannot change it.
+#pragma once
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -106,60 +91,68 @@ __device__ __forceinline__ int opnd_off(int r, int q, int Kp) {
   return (r >> 3) * (Kp * 8) + (q >> 2) * 32 + (r & 7) * 4 + (q & 3);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_gather_contract_tc(SigmaArgs a, int Kp, int Np, uint32_t tmem_cols, int *status) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  float *A = reinterpret_cast<float *>(smem);                // hi (after split)
-  float *Alo = A + kTcM * Kp;
-  uint32_t *Bhi = reinterpret_cast<uint32_t *>(Alo + kTcM * Kp);
-  uint32_t *Blo = Bhi + Np * Kp;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(Blo + Np * Kp);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int npair = a.npair;
-  const double *cin = a.c;
-  if (a.ctl) {
-    if (a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
-    cin = a.ctl->zn;
-  }
+// Shared-memory operand buffers of one CTA.
+struct TcSmem {
+  float *A, *Alo;
+  uint32_t *Bhi, *Blo;
+  uint32_t sA, sAlo, sBhi, sBlo, sbar;
+};
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  // operand B: W split into TF32 hi/lo from FP64, zero-padded to Np x Kp
-  for (int idx = tid; idx < Np * Kp; idx += kTcThreads) {
-    const int n = idx / Kp, k = idx - n * Kp;
-    const double w = (n < npair && k < npair) ? a.W[(size_t)n * npair + k] : 0.0;
-    const uint32_t hi = tf32_bits((float)w);
-    const float lo = (float)(w - (double)__uint_as_float(hi));
-    Bhi[opnd_off(n, k, Kp)] = hi;
-    Blo[opnd_off(n, k, Kp)] = tf32_bits(lo);
+// Element (n, k) of operand B: W split into TF32 hi/lo from FP64, zero
+// outside npair x npair.
+__device__ __forceinline__ void split_W_elem(const double *W, int npair, int n, int k, uint32_t *hi,
+                                             uint32_t *lo) {
+  const double w = (n < npair && k < npair) ? W[(size_t)n * npair + k] : 0.0;
+  const uint32_t h = tf32_bits((float)w);
+  *hi = h;
+  *lo = tf32_bits((float)(w - (double)__uint_as_float(h)));
+}
+
+// Operand B into shared memory, zero-padded to Np x Kp: a copy of the
+// pre-split operand when the context has one (a.Wtc), else split here from
+// FP64 (same values); ends with the fences that publish it to the tensor core.
+__device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, const TcSmem &sm) {
+  const int nb = Np * Kp;
+  if (a.Wtc) {
+    const uint4 *src_hi = reinterpret_cast<const uint4 *>(a.Wtc);
+    const uint4 *src_lo = reinterpret_cast<const uint4 *>(a.Wtc + nb);
+    uint4 *dhi = reinterpret_cast<uint4 *>(sm.Bhi), *dlo = reinterpret_cast<uint4 *>(sm.Blo);
+    for (int i = threadIdx.x; i < nb / 4; i += blockDim.x) {
+      dhi[i] = __ldg(src_hi + i);
+      dlo[i] = __ldg(src_lo + i);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+      const int n = idx / Kp, k = idx - n * Kp;
+      split_W_elem(a.W, a.npair, n, k, &sm.Bhi[opnd_off(n, k, Kp)], &sm.Blo[opnd_off(n, k, Kp)]);
+    }
   }
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tmem_slot;
+}
+
+// One tile of 128 determinants: gather, split, three MMAs per K step, bounded
+// wait, epilogue into G.  256 threads.  Returns false (block-uniformly) if
+// the MMA-completion wait ran out.
+// cin: the input vector, FP64 or its FP32 copy (the gather rounds to FP32
+// either way, so both give the same D).
+template <typename T>
+__device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const T *cin, long long tile, int Kp, int Np,
+                                        const TcSmem &sm, uint32_t tmem, uint32_t &phase) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int npair = a.npair;
+  float *A = sm.A, *Alo = sm.Alo;
+  const uint32_t sA = sm.sA, sAlo = sm.sAlo, sBhi = sm.sBhi, sBlo = sm.sBlo, sbar = sm.sbar;
   const uint32_t idesc = idesc_tf32(kTcM, Np);
   const uint32_t LBO = 128, SBO = (uint32_t)Kp * 32;
-  const uint32_t sA = smem_u32(A), sAlo = smem_u32(Alo), sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
-  const uint32_t sbar = smem_u32(mbar);
   float *G = reinterpret_cast<float *>(a.G);
-  const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
-  uint32_t phase = 0;
   bool ok = true;
   const int row = tid & (kTcM - 1);  // determinant row of this thread
   const int half = tid >> 7;         // 0: alpha links / first half, 1: beta links / second half
   const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  {
     const long long I = tile * kTcM + row;
     const bool valid = I < a.ndet;
     // 1. gather this row of D (FP32): the alpha part into A, the beta part
@@ -171,19 +164,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
       if (half == 0) {
         const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-        const double *ccol = cin + ib;
-        for_links<8, double>(
-            la, a.nlink_a, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
-            [&](uint32_t v, double cv) {
+        const T *ccol = cin + ib;
+        for_links<8, T>(
+            la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+            [&](uint32_t v, T cv) {
               const float f = (float)cv;
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
             });
       } else {
-        const uint32_t *lb = a.link_b + (size_t)ib * a.nlink_b;
-        const double *crow = cin + (size_t)ia * a.nb;
-        for_links<8, double>(
-            lb, a.nlink_b, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-            [&](uint32_t v, double cv) {
+        const uint32_t *lb = a.link_bT + ib;
+        const T *crow = cin + (size_t)ia * a.nb;
+        for_links<8, T>(
+            lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+            [&](uint32_t v, T cv) {
               const float f = (float)cv;
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
             });
@@ -229,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     ok = mbar_wait(sbar, phase, kWaitIters);
     ok = __syncthreads_and(ok) != 0;
-    if (!ok) break;
+    if (!ok) return false;
     phase ^= 1u;
     fence_after();
     // 4. epilogue: warp w reads lane quadrant (w % 4), column half (w / 4)
@@ -250,62 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     fence_after();
   }
-  if (!ok) {
-    if (tid == 0) atomicOr(status, 1);
-    mbar_wait(sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
-                 : "memory");
-}
-
-// Operand sizes of the TF32 split kernel for npair packed pairs.
-bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
-  const int kp = (npair + 7) / 8 * 8;
-  const int np = (npair + 15) / 16 * 16;
-  uint32_t c = 32;
-  while (c < (uint32_t)np) c <<= 1;
-  const size_t bytes = (size_t)(2 * kTcM * kp + 2 * np * kp) * 4 + 16;
-  *Kp = kp;
-  *Np = np;
-  *cols = c;
-  *smem = bytes;
-  return np <= 256 && bytes <= 227 * 1024;
-}
-
-// Grid of the persistent tensor-core kernel (resident CTAs, capped by TMEM
-// columns), computed outside any stream capture.  0 if the shape is unsupported.
-int tc_grid(int npair, long long ndet, int num_sms) {
-  int Kp, Np;
-  uint32_t cols;
-  size_t smem;
-  if (!tc_dims(npair, &Kp, &Np, &cols, &smem)) return 0;
-  if (cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem) !=
-      cudaSuccess)
-    return 0;
-  if (per_sm < 1) per_sm = 1;
-  if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
-  const long long ntiles = (ndet + kTcM - 1) / kTcM;
-  long long grid = (long long)num_sms * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  if (grid < 1) grid = 1;
-  return (int)grid;
-}
-
-cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s) {
-  int Kp, Np;
-  uint32_t cols;
-  size_t smem;
-  if (!tc_dims(a.npair, &Kp, &Np, &cols, &smem) || grid < 1) return cudaErrorInvalidValue;
-  k_gather_contract_tc<<<grid, kTcThreads, smem, s>>>(a, Kp, Np, cols, status);
-  return cudaGetLastError();
+  return ok;
 }
 
 }  // namespace sbci

@@ -65,13 +65,19 @@ class sbci_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double)]
 
 
+class sbci_batch_class(C.Structure):
+    _fields_ = [("Kp", C.c_int), ("Np", C.c_int), ("smem_bytes", C.c_int), ("tc_per_sm_max", C.c_int),
+                ("tuned", C.c_int), ("ctas", C.c_int * 5)]
+
+
 _lib = None
 
 EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_table",
            "sbci_diagonal", "sbci_sigma", "sbci_begin", "sbci_step", "sbci_finish", "sbci_solve",
            "sbci_trace", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
            "sbci_server_create", "sbci_server_submit", "sbci_server_progress", "sbci_server_poll",
-           "sbci_server_destroy", "sbci_last_error", "sbci_destroy"]
+           "sbci_server_set_batching", "sbci_server_destroy", "sbci_solve_batch", "sbci_batch_profile",
+           "sbci_batch_profile_read", "sbci_batch_classes", "sbci_last_error", "sbci_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -101,6 +107,11 @@ def load(path: str = LIB_PATH):
     lib.sbci_server_submit.argtypes = [P, I, I, I, P, P, D, I, C.POINTER(sbci_params), C.POINTER(LL)]
     lib.sbci_server_progress.argtypes = [P, C.POINTER(I), C.POINTER(I)]
     lib.sbci_server_poll.argtypes = [P, LL, C.POINTER(I), P, P, P]
+    lib.sbci_server_set_batching.argtypes = [P, I]
+    lib.sbci_solve_batch.argtypes = [C.POINTER(P), I, I, C.POINTER(sbci_params), P, P, C.POINTER(LL)]
+    lib.sbci_batch_profile.argtypes = [I]
+    lib.sbci_batch_classes.argtypes = [C.POINTER(sbci_batch_class), I, C.POINTER(I)]
+    lib.sbci_batch_profile_read.argtypes = [C.POINTER(sbci_kernel_stat), I, C.POINTER(I)]
     lib.sbci_server_destroy.argtypes = [P]
     lib.sbci_server_destroy.restype = None
     lib.sbci_profile.argtypes = [P, I]
@@ -281,14 +292,57 @@ class Context:
         return list(buf)[: n.value]
 
 
+def solve_batch(contexts, k: int, p: sbci_params | None = None):
+    """sbci_solve_batch over a list of Context objects: energies [n][k], reports, status."""
+    lib = load()
+    n = len(contexts)
+    arr = (C.c_void_p * n)(*[c._h.value for c in contexts])
+    E = np.zeros((n, k))
+    R = (sbci_report * (n * k))()
+    nl = C.c_longlong()
+    st = lib.sbci_solve_batch(arr, n, int(k), C.byref(p) if p is not None else None,
+                              E.ctypes.data_as(C.c_void_p), R, C.byref(nl))
+    _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
+    for c in contexts:
+        c._k = k
+    solve_batch.last_launches = nl.value
+    return E, list(R), st
+
+
+def batch_profile(enable: bool):
+    """sbci_batch_profile: reset the batch engine's kernel statistics; enable
+    event timing of every batched kernel launch."""
+    _check(load().sbci_batch_profile(int(bool(enable))))
+
+
+def batch_profile_read() -> dict:
+    """sbci_batch_profile_read: {family: (launches, total_ms)}."""
+    buf = (sbci_kernel_stat * 8)()
+    n = C.c_int()
+    _check(load().sbci_batch_profile_read(buf, 8, C.byref(n)))
+    return {b.name.decode(): (int(b.launches), float(b.total_ms)) for b in list(buf)[: n.value]}
+
+
+def batch_classes() -> list:
+    """sbci_batch_classes: launch shapes of the batch engine per operand class."""
+    buf = (sbci_batch_class * 16)()
+    n = C.c_int()
+    _check(load().sbci_batch_classes(buf, 16, C.byref(n)))
+    return [{"Kp": b.Kp, "Np": b.Np, "smem_bytes": b.smem_bytes, "tc_per_sm_max": b.tc_per_sm_max,
+             "tuned": bool(b.tuned), "ctas": {"update": b.ctas[0], "project": b.ctas[1], "tensor_core": b.ctas[2],
+                                              "scatter": b.ctas[3], "end": b.ctas[4]}}
+            for b in list(buf)[: min(n.value, 16)]]
+
+
 class Server:
     """Continuous-batching request loop (sbci_server_*), one host thread."""
 
-    def __init__(self, mem_budget_bytes: int, max_slots: int):
+    def __init__(self, mem_budget_bytes: int, max_slots: int, batching: bool = True):
         lib = load()
         self._lib = lib
         self._h = C.c_void_p()
         _check(lib.sbci_server_create(C.byref(self._h), C.c_size_t(int(mem_budget_bytes)), int(max_slots)))
+        _check(lib.sbci_server_set_batching(self._h, int(batching)))
         self._k = {}
 
     def submit(self, I, k: int, p: sbci_params | None = None) -> int:

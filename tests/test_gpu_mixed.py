@@ -86,3 +86,42 @@ def test_mixed_solve_h10_singlet(prec):
     assert sum(r.n_sigma_fp64 for r in R) < sum(r.n_sigma for r in R)
     tr = ctx.trace()
     assert any(t.event == 6 for t in tr)
+
+
+def test_refinement_budget_falls_back_to_fp64():
+    """A state whose low-precision refinement spends its budget
+    (refine_max_sigma) continues with FP64 sigma from an exact X and meets the
+    FP64 target; the trace records the fallback (event 7)."""
+    sbci = require_lib()
+    I = make_integrals(("chain", 8, 1.3))
+    ctx = sbci.Context.from_integrals(I)
+    E64, _, _, st = ctx.solve(3, sbci.params(prec=sbci.SBCI_FP64))
+    assert st == sbci.SBCI_OK
+    p = sbci.params(prec=sbci.SBCI_TF32X3, refine_max_sigma=2)
+    E, _, R, st = ctx.solve(3, p)
+    assert st == sbci.SBCI_OK and all(r.converged for r in R)
+    assert np.abs(E - E64).max() < 1e-8
+    assert any(t.event == 7 for t in ctx.trace())
+    # the same through the batched engine and the batched server
+    ctxs = [sbci.Context.from_integrals(I) for _ in range(3)]
+    EB, RB, st = sbci.solve_batch(ctxs, 3, p)
+    assert st == sbci.SBCI_OK
+    for i in range(3):
+        assert np.array_equal(EB[i], E)
+    server = sbci.Server(4 << 30, 4, batching=True)
+    t = [server.submit(I, 3, p) for _ in range(2)]
+    done = {}
+    import time
+    t0 = time.time()
+    while len(done) < 2 and time.time() - t0 < 300:
+        server.progress()
+        for x in t:
+            r = server.poll(x)
+            if r is not None:
+                done[x] = r
+    assert len(done) == 2
+    for x in t:
+        assert done[x][3] == sbci.SBCI_OK and np.array_equal(done[x][0], E)
+    server.close()
+    for c in ctxs:
+        c.close()

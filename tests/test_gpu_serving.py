@@ -1,10 +1,11 @@
 """Serving layer (continuous batching): each result is the same alone and in the
 mix, admission respects the memory budget, oversize requests are refused.
 
-Tolerance: 1e-10 hartree between a solve run alone and the same solve run in
-the mix.  Each solve's arithmetic does not depend on what else runs (fixed
-grids, fixed-order reductions), so the two are expected to agree to the last
-bit; 1e-10 is the stated bound.
+Tolerance: none — a solve run alone and the same solve run in the mix agree
+bit for bit.  Each solve's arithmetic does not depend on what else runs (fixed
+virtual-block partitions, fixed-order reductions), and the one-solve and the
+batched kernels call the same compiled bodies, so the energies are compared
+for exact equality.
 """
 import time
 
@@ -34,8 +35,9 @@ def _drain(server, tickets, timeout_s=300.0):
     return out
 
 
-@pytest.mark.parametrize("prec", ["TF32X3", "FP64"])
-def test_same_alone_and_in_mix(prec):
+@pytest.mark.parametrize("prec,batching", [("TF32X3", True), ("TF32X3", False), ("FP64", True)])
+def test_same_alone_and_in_mix(prec, batching):
+    """batching = True and TF32X3: the solves share the batched persistent kernels."""
     sbci = require_lib()
     p = sbci.params(prec=getattr(sbci, "SBCI_" + prec))
     ints = [inputs.h_chain(n, R) for n, R, _ in MIX]
@@ -46,13 +48,13 @@ def test_same_alone_and_in_mix(prec):
         assert st == sbci.SBCI_OK
         alone.append(E)
         ctx.close()
-    server = sbci.Server(8 << 30, 4)
+    server = sbci.Server(8 << 30, 4, batching=batching)
     tickets = [server.submit(I, k, p) for I, (_, _, k) in zip(ints, MIX)]
     res = _drain(server, tickets)
     for t, Ea in zip(tickets, alone):
         E, R, times, st = res[t]
         assert st == sbci.SBCI_OK
-        assert np.abs(E - Ea).max() <= 1e-10
+        assert np.array_equal(E, Ea), np.abs(E - Ea).max()
         assert all(r.converged for r in R)
     server.close()
 
@@ -73,7 +75,7 @@ def test_admission_by_memory_budget():
     queue_times = [res[t][2][0] for t in tickets]
     assert queue_times[2] > 0.0 and queue_times[2] >= queue_times[0]
     for t in tickets:
-        assert np.abs(res[t][0] - Ea).max() <= 1e-10
+        assert np.array_equal(res[t][0], Ea)
     server.close()
 
 
@@ -84,3 +86,51 @@ def test_oversize_request_refused():
         server.submit(inputs.h_chain(8, 1.0), 1)
     assert e.value.status == sbci.SBCI_ERR_NOMEM
     server.close()
+
+
+def test_solve_batch_same_as_alone():
+    """sbci_solve_batch: solves of uneven sizes share the batched persistent
+    kernels; each result equals the solve run alone."""
+    sbci = require_lib()
+    p = sbci.params(prec=sbci.SBCI_TF32X3)
+    ints = [inputs.h_chain(n, R) for n, R in [(6, 1.0), (10, 1.2), (8, 1.3), (6, 2.0), (12, 1.2)]]
+    k = 2
+    alone = []
+    for I in ints:
+        ctx = sbci.Context.from_integrals(I)
+        E, _, _, st = ctx.solve(k, p)
+        assert st == sbci.SBCI_OK
+        alone.append(E)
+        ctx.close()
+    ctxs = [sbci.Context.from_integrals(I) for I in ints]
+    E, R, st = sbci.solve_batch(ctxs, k, p)
+    assert st == sbci.SBCI_OK
+    for i in range(len(ints)):
+        assert np.array_equal(E[i], alone[i]), np.abs(E[i] - alone[i]).max()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_profile_same_result():
+    """Kernel timing of the batch engine launches the same kernels one by one:
+    same energies as the graph loop, every family counted and timed."""
+    sbci = require_lib()
+    p = sbci.params(prec=sbci.SBCI_TF32X3)
+    ints = [inputs.h_chain(n, R) for n, R in [(8, 1.0), (10, 1.4), (6, 1.1)]]
+    ctxs = [sbci.Context.from_integrals(I) for I in ints]
+    E0, _, st = sbci.solve_batch(ctxs, 2, p)
+    assert st == sbci.SBCI_OK
+    n_graph = sbci.solve_batch.last_launches
+    sbci.batch_profile(True)
+    E1, _, st = sbci.solve_batch(ctxs, 2, p)
+    assert st == sbci.SBCI_OK
+    stats = sbci.batch_profile_read()
+    sbci.batch_profile(False)
+    assert np.array_equal(E1, E0)
+    assert set(stats) == {"batch_update", "batch_project", "batch_gather_contract_tc", "batch_scatter",
+                          "batch_end"}
+    bodies = stats["batch_end"][0]
+    assert bodies > 0 and all(v[0] == bodies and v[1] > 0.0 for v in stats.values())
+    assert n_graph >= 5 * bodies  # the graph loop ran the same bodies (plus host-driven kernels)
+    for c in ctxs:
+        c.close()
