@@ -149,7 +149,9 @@ sbci_status ensure_G(sbci_ctx *c, int prec) {
   if (c->d_G) CK(cudaFree(c->d_G));
   c->d_G = nullptr;
   c->G_bytes = 0;
-  CK(cudaMalloc(&c->d_G, need));
+  // slack after the last pair: the staged scatter's bulk copies move 16-byte
+  // aligned covers of their segments
+  CK(cudaMalloc(&c->d_G, need + 256));
   c->G_bytes = need;
   return SBCI_OK;
 }
@@ -233,7 +235,9 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.dot_slot[1] = S_HYZ;
   a.dot_slot[2] = S_HZZ;
   a.partials = c->d_partials;
-  a.grid = scatter_grid(c->ndet, c->nsm);
+  a.sc_rows = scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, prec == SBCI_FP64 ? 0 : 1);
+  a.status = c->d_status;
+  a.grid = scatter_grid(c->ndet, c->Na, a.sc_rows, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   if (prec == SBCI_TF32X3)
     RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
@@ -250,7 +254,7 @@ sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
     return SBCI_ERR_TIMEOUT;
   }
   for (int i = s0; i < s1; ++i)
@@ -289,7 +293,7 @@ sbci_status ctl_read(sbci_ctx *c) {
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
     return SBCI_ERR_TIMEOUT;
   }
   const int n = std::min(s.h_ctl->ntrace, kTraceCap);
@@ -345,11 +349,12 @@ SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
   a.dot_slot[1] = S_HYZ;
   a.dot_slot[2] = S_HZZ;
   a.partials = c->d_partials;
-  a.grid = scatter_grid(c->ndet, c->nsm);
+  a.sc_rows = scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, prec == SBCI_FP64 ? 0 : 1);
+  a.status = c->d_status;
+  a.grid = scatter_grid(c->ndet, c->Na, a.sc_rows, c->nsm);
   a.ctl = s.d_ctl;
   a.counter = s.d_counters + 2;
   a.cond = cond;
-  (void)prec;
   return a;
 }
 
@@ -828,7 +833,10 @@ bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
 }
 
 int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_grid(c->ndet, c->nsm); }
-int sbci::ctx_scatter_blocks(const sbci_ctx *c) { return scatter_grid(c->ndet, c->nsm); }
+int sbci::ctx_scatter_blocks(const sbci_ctx *c) {
+  // the batch engine serves TF32x3 solves only: FP32 G
+  return scatter_grid(c->ndet, c->Na, scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, 1), c->nsm);
+}
 long long sbci::ctx_ndet(const sbci_ctx *c) { return c->ndet; }
 
 long long sbci::ctx_launch_count(const sbci_ctx *c) {
@@ -857,6 +865,7 @@ bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream)
   a->link_a = c->d_link_a;
   a->link_b = c->d_link_b;
   a->link_bT = c->d_link_bT;
+  a->status = c->d_status;
   a->W = c->d_W;
   a->Wf = c->d_Wf;
   a->Wtc = c->d_Wtc;
@@ -1006,6 +1015,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   c->nsm = std::max(nsm, 1);
   c->grid = 8 * c->nsm;  // upper bound of every kernel's block count that writes partials
   TRY(cuda_ok(prepare_sigma_kernels(), "kernel attributes"));
+  TRY(cuda_ok(prepare_scatter_kernels(), "kernel attributes"));
   // packed operator W[P][Q], P = (i>=j), Q = (k>=l):
   //   W = 1/2 (ij|kl) + (k_ij d_kl + d_ij k_kl) / (2N),  k_ij = h_ij - 1/2 sum_m (im|mj)
   const int N = nalpha + nbeta;
@@ -1173,7 +1183,7 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
     return SBCI_ERR_TIMEOUT;
   }
   return SBCI_OK;

@@ -64,6 +64,29 @@ static cudaError_t max_dynamic_smem(const void *f, int *bytes) {
   return cudaSuccess;
 }
 
+// CTAs of kernel f (threads per CTA, dynamic shared memory dyn) that fit one
+// SM, from the device's shared-memory and register budgets and the kernel's
+// register count and static shared memory (the larger of this and the
+// runtime's occupancy answer is used: launching more CTAs than fit is legal,
+// they wait for a slot).
+static int resident_ctas(const void *f, int threads, size_t dyn) {
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, api = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, f) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, f, threads, dyn) != cudaSuccess) api = 0;
+  const size_t per_cta_smem = dyn + fa.sharedSizeBytes + (size_t)reserved;
+  const int by_smem = (int)((size_t)smem_sm / per_cta_smem);
+  const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocation unit: 256 registers per warp
+  const int by_regs = regs_sm / (warp_regs * ((threads + 31) / 32));
+  int n = by_smem < by_regs ? by_smem : by_regs;
+  if (api > n) n = api;
+  return n < 1 ? 1 : n;
+}
+
 // ---------------------------------------------------------------- one solve
 
 __device__ __forceinline__ void halt_loop(unsigned long long cond) {
@@ -118,8 +141,16 @@ __global__ void __launch_bounds__(kScTile, 3) k_scatter(SigmaArgs a) {
     cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
 }
 
-int scatter_grid(long long ndet, int nsm) {
-  long long g = (ndet + kScTile - 1) / kScTile;
+int scatter_rows(int npair, int na, int nb, int nlink_a, int prec) {
+  if (prec == 0 || nb > kScTile) return 0;  // staging is for FP32 G and rows of <= 256 strings
+  int rows = kScTile / nb;
+  if (rows > na) rows = na;
+  while (rows > 0 && scatter_stage_bytes(npair, nlink_a, rows, nb) + 8 > (size_t)kScStageBytes) --rows;
+  return rows;
+}
+
+int scatter_grid(long long ndet, int na, int rows, int nsm) {
+  long long g = rows > 0 ? (na + rows - 1) / rows : (ndet + kScTile - 1) / kScTile;
   if (g > 8LL * nsm) g = 8LL * nsm;
   if (g < 1) g = 1;
   return (int)g;
@@ -127,13 +158,16 @@ int scatter_grid(long long ndet, int nsm) {
 
 template <typename AccT>
 static cudaError_t launch_sc_t(const SigmaArgs &a, cudaStream_t s) {
-  k_scatter<AccT><<<a.grid, kScTile, 0, s>>>(a);
+  const size_t smem =
+      (sizeof(AccT) == 4 && a.sc_rows > 0) ? scatter_stage_bytes(a.npair, a.nlink_a, a.sc_rows, a.nb) + 8 : 0;
+  k_scatter<AccT><<<a.grid, kScTile, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s) {
   return prec == 0 ? launch_sc_t<double>(a, s) : launch_sc_t<float>(a, s);
 }
+
 
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_gather_contract_tc(SigmaArgs a, int Kp, int Np, uint32_t tmem_cols, int *status) {
@@ -221,11 +255,7 @@ int tc_grid(int npair, long long ndet, int num_sms) {
   if (cudaFuncSetAttribute(k_gather_contract_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_contract_tc, kTcThreads, smem) !=
-      cudaSuccess)
-    return 0;
-  if (per_sm < 1) per_sm = 1;
+  int per_sm = resident_ctas((const void *)k_gather_contract_tc, kTcThreads, smem);
   if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
   const long long ntiles = (ndet + kTcM - 1) / kTcM;
   long long grid = (long long)num_sms * per_sm;
@@ -410,10 +440,7 @@ cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
   e = cudaFuncSetAttribute(k_tc_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_batch, kTcThreads, cfg->smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  int per_sm = resident_ctas((const void *)k_tc_batch, kTcThreads, cfg->smem);
   if ((uint32_t)per_sm * cfg->cols > 512) per_sm = (int)(512 / cfg->cols);
   cfg->tc_per_sm_max = per_sm;
   // defaults until the autotuner has measured this class
@@ -433,7 +460,7 @@ cudaError_t launch_batch_kernel(int which, const BatchConfig &cfg, BatchTable *d
     case BK_TC:
       k_tc_batch<<<cfg.ctas[BK_TC], kTcThreads, cfg.smem, s>>>(d_table, cfg.Kp, cfg.Np, cfg.cols, status);
       break;
-    case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, 0, s>>>(d_table); break;
+    case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, kScStageBytes, s>>>(d_table); break;
     case BK_END: k_batch_end<<<1, kMaxBatch, 0, s>>>(d_table, cond); break;
     default: return cudaErrorInvalidValue;
   }
@@ -465,6 +492,14 @@ cudaError_t build_batch_graph(const BatchConfig &cfg, BatchTable *d_table, int *
   if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) return e;
   *graph = g;
   return cudaSuccess;
+}
+
+// Opts the staged-row scatter kernels into their dynamic shared memory (once
+// per process, outside any stream capture).
+cudaError_t prepare_scatter_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScStageBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_scatter_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kScStageBytes);
 }
 
 }  // namespace sbci

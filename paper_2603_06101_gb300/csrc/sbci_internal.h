@@ -105,6 +105,8 @@ struct SigmaArgs {
   int dot_slot[3];
   double *partials;      // [S_COUNT][grid]
   int grid;
+  int sc_rows;           // scatter work unit: whole alpha rows staged in shared memory (0: none)
+  int *status;           // device error word: bit 1 = a bulk-copy wait of the scatter ran out
   // device-controlled mode (ctl != nullptr): input z and output Z come from the
   // controller, the scatter's dots are against (dot_u[0], dot_u[1], ctl->zn),
   // and its last block runs the subspace solve
@@ -117,7 +119,11 @@ struct SigmaArgs {
 // prec: 0 = FP64 scratch and contraction, 1 = FP32 (SIMT) contraction
 cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
-int scatter_grid(long long ndet, int nsm);
+// Rows per work unit of the staged-row scatter for FP32 G (0: global gathers).
+int scatter_rows(int npair, int na, int nb, int nlink_a, int prec);
+// Virtual blocks of the scatter: min(work units, 8 x SMs).
+int scatter_grid(long long ndet, int na, int rows, int nsm);
+cudaError_t prepare_scatter_kernels();
 cudaError_t prepare_sigma_kernels();
 // tcgen05 TF32x3 gather + contract (kernels_loop.cu); writes FP32 G like prec 1.
 bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
