@@ -399,6 +399,7 @@ def run_gb300(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}", "sigma_per_solve": nsig,
                        "sigma_per_state": [int(r.n_sigma) for r in R],
                        "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R],
+                       "controller_us_per_step": sum(r.ctl_cycles for r in R) / max(nsig, 1) / (clocks.get("sm_mhz") or 2070.0),
                        "energies": [float(e) for e in E]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "single_solve": single,

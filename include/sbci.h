@@ -101,6 +101,8 @@ typedef struct {
   int n_sigma_fp64;   /* of which FP64 */
   int n_step;         /* SB steps */
   int n_restart[4];   /* restarts by cause: S62a, S62b, S62c, max_cycle */
+  long long ctl_cycles; /* SM clock cycles the device controller (convergence and
+                           restart tests, subspace solve) spent on this state */
 } sbci_report;
 
 typedef struct {
@@ -238,7 +240,7 @@ sbci_status sbci_batch_profile(int enable);
 
 /* Waits for the recorded events and copies up to cap entries (families
  * "batch_update", "batch_project", "batch_gather_contract_tc",
- * "batch_scatter", "batch_end"); *n = 5. */
+ * "batch_scatter", "batch_symfinish", "batch_end"); *n = 6. */
 sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n);
 
 /* Launch shapes of the batch engine on the current device, one record per
@@ -249,7 +251,7 @@ typedef struct {
   int smem_bytes;        /* dynamic shared memory of a tensor-core CTA */
   int tc_per_sm_max;     /* tensor-core CTAs that fit one SM */
   int tuned;             /* 1 once the autotuner has chosen */
-  int ctas[5];           /* update, projection, tensor core, scatter, end */
+  int ctas[6];           /* update, projection, tensor core, scatter, symmetric finish, end */
 } sbci_batch_class;
 
 /* Copies up to cap records; *n = classes. */

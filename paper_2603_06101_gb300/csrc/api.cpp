@@ -57,10 +57,10 @@ namespace {
 
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
-enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_COUNT };
+enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
-                                       "sigma_gather_contract_tc"};
+                                       "sigma_gather_contract_tc", "sigma_symfinish"};
 
 struct Prof {
   bool on = false;
@@ -149,9 +149,7 @@ sbci_status ensure_G(sbci_ctx *c, int prec) {
   if (c->d_G) CK(cudaFree(c->d_G));
   c->d_G = nullptr;
   c->G_bytes = 0;
-  // slack after the last pair: the staged scatter's bulk copies move 16-byte
-  // aligned covers of their segments
-  CK(cudaMalloc(&c->d_G, need + 256));
+  CK(cudaMalloc(&c->d_G, need));
   c->G_bytes = need;
   return SBCI_OK;
 }
@@ -235,9 +233,7 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.dot_slot[1] = S_HYZ;
   a.dot_slot[2] = S_HZZ;
   a.partials = c->d_partials;
-  a.sc_rows = scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, prec == SBCI_FP64 ? 0 : 1);
-  a.status = c->d_status;
-  a.grid = scatter_grid(c->ndet, c->Na, a.sc_rows, c->nsm);
+  a.grid = scatter_grid(c->ndet, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   if (prec == SBCI_TF32X3)
     RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
@@ -254,7 +250,7 @@ sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
     return SBCI_ERR_TIMEOUT;
   }
   for (int i = s0; i < s1; ++i)
@@ -288,12 +284,12 @@ double shift_for(const sbci_ctx *c, int alpha, double E) {
 // Copies the controller header (and any committed trace records) to the host.
 sbci_status ctl_read(sbci_ctx *c) {
   Solver &s = c->s;
-  const size_t hdr = offsetof(CtlState, trace);
+  const size_t hdr = sizeof(CtlHead);
   CK(cudaMemcpyAsync(s.h_ctl, s.d_ctl, hdr, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
     return SBCI_ERR_TIMEOUT;
   }
   const int n = std::min(s.h_ctl->ntrace, kTraceCap);
@@ -311,7 +307,7 @@ sbci_status ctl_read(sbci_ctx *c) {
 sbci_status ctl_write(sbci_ctx *c) {
   Solver &s = c->s;
   s.h_ctl->ntrace = 0;
-  CK(cudaMemcpyAsync(s.d_ctl, s.h_ctl, offsetof(CtlState, trace), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(s.d_ctl, s.h_ctl, sizeof(CtlHead), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return SBCI_OK;
 }
@@ -337,6 +333,10 @@ StepArgs step_args(sbci_ctx *c, unsigned long long cond) {
   return a;
 }
 
+// The singlet-sector split needs c = c^T exactly (the projection symmetrises
+// z in sector mode) and the same strings for both spins.
+bool use_symfin(const sbci_ctx *c) { return c->s.p.sector != 0 && c->ne_a == c->ne_b; }
+
 SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
   Solver &s = c->s;
   SigmaArgs a{};
@@ -349,9 +349,11 @@ SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
   a.dot_slot[1] = S_HYZ;
   a.dot_slot[2] = S_HZZ;
   a.partials = c->d_partials;
-  a.sc_rows = scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, prec == SBCI_FP64 ? 0 : 1);
-  a.status = c->d_status;
-  a.grid = scatter_grid(c->ndet, c->Na, a.sc_rows, c->nsm);
+  a.grid = scatter_grid(c->ndet, c->nsm);
+  if (use_symfin(c)) {  // singlet sector: sigma = A + A^T, A kept in w (free after the projection)
+    a.symA = s.w;
+    a.sf_grid = symfin_grid(c->Na, c->nsm);
+  }
   a.ctl = s.d_ctl;
   a.counter = s.d_counters + 2;
   a.cond = cond;
@@ -377,6 +379,7 @@ sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool tim
   else
     RET(L(K_GC, [&] { return launch_gather_contract(sa, p32, c->stream); }));
   RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
+  if (sa.symA) RET(L(K_SF, [&] { return launch_symfin(sa, p32, c->stream); }));
   return SBCI_OK;
 }
 
@@ -427,6 +430,7 @@ sbci_status run_until_halt(sbci_ctx *c) {
     pf.launches[K_PROJ] += bodies;
     pf.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
     pf.launches[K_SC] += bodies;
+    if (use_symfin(c)) pf.launches[K_SF] += bodies;
     s.h_ctl->iters = 0;
     CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
     return SBCI_OK;
@@ -476,6 +480,7 @@ sbci_status start_state(sbci_ctx *c, int alpha, double E0) {
   h.alpha = alpha;
   h.Ec0 = alpha > 0 ? s.Ec[0] : 0.0;
   h.n_sigma = h.n_sigma_fp64 = h.n_step = h.n_stage1 = 0;
+  h.ctl_cycles = 0;
   for (int i = 0; i < 4; ++i) h.n_restart[i] = 0;
   s.verified = 0;
   return start_iteration(c, 1.0, E0, s.p.prec == SBCI_FP64 ? 1 : 0);
@@ -528,6 +533,7 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residua
   r.n_sigma_fp64 = h.n_sigma_fp64;
   r.n_step = h.n_step;
   for (int i = 0; i < 4; ++i) r.n_restart[i] = h.n_restart[i];
+  r.ctl_cycles = h.ctl_cycles;
   if (!converged) s.any_unconverged = 1;
   if (alpha + 1 >= s.k) {
     s.done = true;
@@ -652,6 +658,7 @@ sbci_status alloc_solver(sbci_ctx *c, int k) {
   CK(cudaMemsetAsync(s.d_ctl, 0, sizeof(CtlState), c->stream));
   CK(cudaMallocHost((void **)&s.h_ctl, sizeof(CtlState)));
   std::memset(s.h_ctl, 0, sizeof(CtlState));
+  s.h_ctl->trace_ptr = s.d_ctl->trace;  // device address of the ring (no dereference)
   CK(cudaMalloc((void **)&s.d_counters, 4 * sizeof(unsigned int)));
   CK(cudaMemsetAsync(s.d_counters, 0, 4 * sizeof(unsigned int), c->stream));
   return SBCI_OK;
@@ -809,6 +816,7 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
     c->prof.launches[K_PROJ] += bodies;
     c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
     c->prof.launches[K_SC] += bodies;
+    if (use_symfin(c)) c->prof.launches[K_SF] += bodies;
   }
   s.h_ctl->iters = 0;
   CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
@@ -833,10 +841,8 @@ bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
 }
 
 int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_grid(c->ndet, c->nsm); }
-int sbci::ctx_scatter_blocks(const sbci_ctx *c) {
-  // the batch engine serves TF32x3 solves only: FP32 G
-  return scatter_grid(c->ndet, c->Na, scatter_rows(c->npair, c->Na, c->Nb, c->sa.nlink, 1), c->nsm);
-}
+int sbci::ctx_scatter_blocks(const sbci_ctx *c) { return scatter_grid(c->ndet, c->nsm); }
+int sbci::ctx_symfin_blocks(const sbci_ctx *c) { return use_symfin(c) ? symfin_grid(c->Na, c->nsm) : 0; }
 long long sbci::ctx_ndet(const sbci_ctx *c) { return c->ndet; }
 
 long long sbci::ctx_launch_count(const sbci_ctx *c) {
@@ -865,7 +871,6 @@ bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream)
   a->link_a = c->d_link_a;
   a->link_b = c->d_link_b;
   a->link_bT = c->d_link_bT;
-  a->status = c->d_status;
   a->W = c->d_W;
   a->Wf = c->d_Wf;
   a->Wtc = c->d_Wtc;
@@ -1015,7 +1020,6 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   c->nsm = std::max(nsm, 1);
   c->grid = 8 * c->nsm;  // upper bound of every kernel's block count that writes partials
   TRY(cuda_ok(prepare_sigma_kernels(), "kernel attributes"));
-  TRY(cuda_ok(prepare_scatter_kernels(), "kernel attributes"));
   // packed operator W[P][Q], P = (i>=j), Q = (k>=l):
   //   W = 1/2 (ij|kl) + (k_ij d_kl + d_ij k_kl) / (2N),  k_ij = h_ij - 1/2 sum_m (im|mj)
   const int N = nalpha + nbeta;
@@ -1183,7 +1187,7 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
-    set_error("a bounded device wait ran out (tensor-core MMA completion or staged-scatter copy)");
+    set_error("a bounded device wait ran out (tensor-core MMA completion)");
     return SBCI_ERR_TIMEOUT;
   }
   return SBCI_OK;

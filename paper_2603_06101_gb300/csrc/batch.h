@@ -25,8 +25,9 @@ struct BatchTable {
   int off_step[kMaxBatch + 1];  // prefix sums of the update / projection virtual blocks
   int off_sc[kMaxBatch + 1];    // prefix sums of the scatter virtual blocks
   int off_tc[kMaxBatch + 1];    // prefix sums of the 128-determinant tensor-core tiles
+  int off_sf[kMaxBatch + 1];    // prefix sums of the symmetric-finish virtual blocks (0 if none)
   unsigned int tc_next;         // work-queue head of the tensor-core kernel
-  unsigned long long bodies;    // loop bodies run (five kernels each)
+  unsigned long long bodies;    // loop bodies run (BK_COUNT kernels each)
   int stop;                     // the last body ended with a halted solve
   int halted[kMaxBatch];        // set by a job's last block when its controller halts
   BatchJob job[kMaxBatch];
@@ -37,8 +38,9 @@ struct BatchTable {
 constexpr int kBatchMaxPair = 105;
 
 
-// The five kernels of one batched loop body, in launch order.
-enum BatchKernel { BK_UPDATE = 0, BK_PROJECT, BK_TC, BK_SCATTER, BK_END, BK_COUNT };
+// The kernels of one batched loop body, in launch order (the symmetric finish
+// serves the singlet-sector solves; the others finish in the scatter).
+enum BatchKernel { BK_UPDATE = 0, BK_PROJECT, BK_TC, BK_SCATTER, BK_SYMFIN, BK_END, BK_COUNT };
 
 // Launch shapes of the batched kernels on a device with num_sms SMs for one
 // operand class: the tensor-core buffers are sized for the largest Kp x Np of

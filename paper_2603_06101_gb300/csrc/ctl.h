@@ -36,7 +36,11 @@ struct UpdParams {
   double sx, sy, b, c, E, kinv, Epre;
 };
 
-struct CtlState {
+// The controller's scalar state.  The device runs its decisions on a copy of
+// this header in shared memory (one L2 round trip in, one out) instead of
+// chasing global-memory loads on a single thread; trace records go straight to
+// the ring behind trace_ptr.
+struct CtlHead {
   CtlParams p;
   // ping-pong z / Z: the update reads (zc, Zc), projection/sigma write (zn, Zn)
   double *zc, *Zc, *zn, *Zn;
@@ -54,10 +58,15 @@ struct CtlState {
   UpdParams up;
   double second[3], E2;  // second Ritz vector on (x_new, y_new, z_t) and its value
   int n_sigma, n_sigma_fp64, n_step, n_restart[4];
+  long long ctl_cycles;  // device cycles spent in ctl_check + ctl_solve (this state)
   int iters, iter_cap;  // bodies run since the host last wrote the state; hard bound
   sbci_trace_record pending;
   int ntrace;  // records committed since the host last drained them
   double dots[S_COUNT];
+  sbci_trace_record *trace_ptr;  // the ring of the device state (CtlState::trace)
+};
+
+struct CtlState : CtlHead {
   sbci_trace_record trace[kTraceCap];
 };
 
@@ -86,8 +95,12 @@ __host__ __device__ inline double f_rsqrt(double x) {
   return r;
 }
 
-// Symmetric eigen-solver in FP32 (cyclic Jacobi), ascending.
-__host__ __device__ inline void eigh_f32(int n, const double *Ain, float *w, float *V) {
+// Symmetric eigen-solver in FP32 (cyclic Jacobi), ascending.  n is a
+// template parameter so that every loop unrolls and the arrays stay in
+// registers (the controller runs on one thread; local memory would put an
+// L1 round trip on its serial path).
+template <int n>
+__host__ __device__ inline void eigh_f32(const double *Ain, float *w, float *V) {
   float A[9];
   for (int i = 0; i < n * n; ++i) A[i] = (float)Ain[i];
   for (int i = 0; i < n; ++i)
@@ -146,7 +159,8 @@ __host__ __device__ inline void eigh_f32(int n, const double *Ain, float *w, flo
 // lam <- v^T V v.  Cubically convergent, so FP32 accuracy becomes FP64
 // accuracy in one step for separated eigenvalues.  Returns the residual
 // |V v - lam v| for the caller's acceptance test.
-__host__ __device__ inline double rqi_refine(int n, const double *V, double &lam, double *v) {
+template <int n>
+__host__ __device__ inline double rqi_refine(const double *V, double &lam, double *v) {
   double w[3];
   if (n == 2) {
     const double a = V[0] - lam, b = V[1], d = V[3] - lam;
@@ -183,29 +197,32 @@ __host__ __device__ inline double rqi_refine(int n, const double *V, double &lam
   return r;
 }
 
-__host__ __device__ inline void ctl_eigh(int n, const double *Ain, double *w, double *V);
+template <int n>
+__host__ __device__ inline void ctl_eigh(const double *Ain, double *w, double *V);
 
 // Lowest two eigenpairs of a 2x2 / 3x3 symmetric V to FP64 accuracy: FP32
 // Jacobi, then one FP64 Rayleigh-quotient step each; falls back to the FP64
 // Jacobi solver when a refined residual is not at rounding level.
-__host__ __device__ inline void ctl_eigh_fast(int n, const double *V, double *w, double *U) {
+template <int n>
+__host__ __device__ inline void ctl_eigh_fast(const double *V, double *w, double *U) {
   float wf[3], Uf[9];
-  eigh_f32(n, V, wf, Uf);
+  eigh_f32<n>(V, wf, Uf);
   double scale = 0.0;
   for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(V[i]));
   bool ok = true;
   for (int j = 0; j < 2 && j < n; ++j) {
     double v[3], lam = (double)wf[j];
     for (int i = 0; i < n; ++i) v[i] = (double)Uf[i * n + j];
-    const double r = rqi_refine(n, V, lam, v);
+    const double r = rqi_refine<n>(V, lam, v);
     if (!(r <= 1e-26 * scale * scale)) ok = false;
     w[j] = lam;
     for (int i = 0; i < n; ++i) U[i * n + j] = v[i];
   }
-  if (!ok || (n > 1 && !(w[0] <= w[1]))) ctl_eigh(n, V, w, U);
+  if (!ok || (n > 1 && !(w[0] <= w[1]))) ctl_eigh<n>(V, w, U);
 }
 
-__host__ __device__ inline void ctl_eigh(int n, const double *Ain, double *w, double *V) {
+template <int n>
+__host__ __device__ inline void ctl_eigh(const double *Ain, double *w, double *V) {
   double A[9];
   for (int i = 0; i < n * n; ++i) A[i] = Ain[i];
   for (int i = 0; i < n; ++i)
@@ -266,7 +283,7 @@ struct StepOut {
 };
 
 // First-step path (Eqs. S10-S24) on x_0 = sx * x (|x_0| = 1).
-__host__ __device__ inline void ctl_first_step(const CtlState &s, StepOut &o) {
+__host__ __device__ inline void ctl_first_step(const CtlHead &s, StepOut &o) {
   const double *d = s.dots;
   const double sx = s.sx_pending;
   const double Hxx = sx * sx * d[S_HXX];
@@ -290,7 +307,7 @@ __host__ __device__ inline void ctl_first_step(const CtlState &s, StepOut &o) {
   V[0] = Hxx;
   V[1] = V[2] = Bx * Hxx + Bz * Hxz;
   V[3] = Bx * Bx * Hxx + Bz * Bz * Hzz + 2.0 * Bx * Bz * Hxz;
-  ctl_eigh_fast(2, V, w, U);
+  ctl_eigh_fast<2>(V, w, U);
   const double vx = U[0], vz = U[2];
   o.E = w[0];
   const double den = f_recip(vx + vz * Bx);
@@ -304,7 +321,7 @@ __host__ __device__ inline void ctl_first_step(const CtlState &s, StepOut &o) {
 }
 
 // Later-step path (Eqs. S33-S55).
-__host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
+__host__ __device__ inline void ctl_later_step(const CtlHead &s, StepOut &o) {
   const double *d = s.dots;
   const double Nxx = d[S_NXX], Nxy = d[S_NXY], Nxz = d[S_NXZ];
   const double Nyy = d[S_NYY], Nyz = d[S_NYZ], Nzz = d[S_NZZ];
@@ -323,7 +340,7 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
     V[0] = Ax * Ax * Hxx;
     V[1] = V[2] = Ax * (Bx * Hxx + By * Hxy);
     V[3] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;
-    ctl_eigh_fast(2, V, w, U);
+    ctl_eigh_fast<2>(V, w, U);
     const double vx = U[0], vy = U[2];
     o.k = f_recip(vx * Ax + vy * Bx);
     o.b = vy * By * o.k;
@@ -349,7 +366,7 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
   V[5] = V[7] = Bx * hx + By * hy;                             // S44e
   V[8] = Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz + 2.0 * Cx * Cy * Hxy +
          2.0 * Cx * Cz * Hxz + 2.0 * Cy * Cz * Hyz;            // S44f
-  ctl_eigh_fast(3, V, w, U);
+  ctl_eigh_fast<3>(V, w, U);
   const double vx = U[0], vy = U[3], vz = U[6];
   const double iden = f_recip(vx * Ax + vy * Bx + vz * Cx);
   o.E = w[0];
@@ -363,13 +380,13 @@ __host__ __device__ inline void ctl_later_step(const CtlState &s, StepOut &o) {
   o.E2 = w[1];
 }
 
-__host__ __device__ inline void ctl_commit(CtlState &s, const sbci_trace_record &r) {
-  if (s.ntrace < kTraceCap) s.trace[s.ntrace] = r;
+__host__ __device__ inline void ctl_commit(CtlHead &s, const sbci_trace_record &r) {
+  if (s.ntrace < kTraceCap) s.trace_ptr[s.ntrace] = r;
   s.ntrace += 1;
 }
 
 // After the update sweep: finish the pending record and decide.
-__host__ __device__ inline void ctl_check(CtlState &s) {
+__host__ __device__ inline void ctl_check(CtlHead &s) {
   if (s.halt || !s.pending_check) return;
   s.pending_check = 0;
   const double *d = s.dots;
@@ -424,7 +441,7 @@ __host__ __device__ inline void ctl_check(CtlState &s) {
 }
 
 // After sigma of the next z: subspace solve, parameters of the next update.
-__host__ __device__ inline void ctl_solve(CtlState &s) {
+__host__ __device__ inline void ctl_solve(CtlHead &s) {
   if (s.halt) return;
   StepOut o;
   if (s.first) ctl_first_step(s, o);
@@ -470,5 +487,32 @@ __host__ __device__ inline void ctl_solve(CtlState &s) {
   s.zn = tz;
   s.Zn = tZ;
 }
+
+#ifdef __CUDACC__
+// Runs f on a shared-memory copy of the controller header (thread 0 of the
+// calling block; all threads copy the header in and out) and returns the
+// halt code.  Called by the one block that finishes a step's reductions.
+template <typename F>
+__device__ __forceinline__ int ctl_run_shadowed(CtlState *g, F f) {
+  __shared__ __align__(16) CtlHead sh;
+  static_assert(sizeof(CtlHead) % 4 == 0, "word copy");
+  constexpr int nw = (int)(sizeof(CtlHead) / 4);
+  uint32_t *d = reinterpret_cast<uint32_t *>(&sh);
+  uint32_t *gw = reinterpret_cast<uint32_t *>(static_cast<CtlHead *>(g));
+  __syncthreads();
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = __ldcg(gw + i);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    f(sh);
+    sh.ctl_cycles += clock64() - t0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) gw[i] = d[i];
+  const int h = sh.halt;
+  __syncthreads();
+  return h;
+}
+#endif
 
 }  // namespace sbci

@@ -141,16 +141,8 @@ __global__ void __launch_bounds__(kScTile, 3) k_scatter(SigmaArgs a) {
     cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
 }
 
-int scatter_rows(int npair, int na, int nb, int nlink_a, int prec) {
-  if (prec == 0 || nb > kScTile) return 0;  // staging is for FP32 G and rows of <= 256 strings
-  int rows = kScTile / nb;
-  if (rows > na) rows = na;
-  while (rows > 0 && scatter_stage_bytes(npair, nlink_a, rows, nb) + 8 > (size_t)kScStageBytes) --rows;
-  return rows;
-}
-
-int scatter_grid(long long ndet, int na, int rows, int nsm) {
-  long long g = rows > 0 ? (na + rows - 1) / rows : (ndet + kScTile - 1) / kScTile;
+int scatter_grid(long long ndet, int nsm) {
+  long long g = (ndet + kScTile - 1) / kScTile;
   if (g > 8LL * nsm) g = 8LL * nsm;
   if (g < 1) g = 1;
   return (int)g;
@@ -158,9 +150,33 @@ int scatter_grid(long long ndet, int na, int rows, int nsm) {
 
 template <typename AccT>
 static cudaError_t launch_sc_t(const SigmaArgs &a, cudaStream_t s) {
-  const size_t smem =
-      (sizeof(AccT) == 4 && a.sc_rows > 0) ? scatter_stage_bytes(a.npair, a.nlink_a, a.sc_rows, a.nb) + 8 : 0;
-  k_scatter<AccT><<<a.grid, kScTile, smem, s>>>(a);
+  k_scatter<AccT><<<a.grid, kScTile, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(kScTile) k_symfin(SigmaArgs a) {
+  if (a.ctl->halt) {
+    if (a.cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+    return;
+  }
+  const bool halted = symfin_body<AccT>(a, blockIdx.x, gridDim.x);
+  if (halted && a.cond && threadIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+}
+
+int symfin_grid(int na, int nsm) {
+  const long long T = (na + kSfT - 1) / kSfT;
+  long long g = T * (T + 1) / 2;
+  if (g > 8LL * nsm) g = 8LL * nsm;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_symfin(const SigmaArgs &a, int prec, cudaStream_t s) {
+  if (prec == 0) k_symfin<double><<<a.sf_grid, kScTile, 0, s>>>(a);
+  else k_symfin<float><<<a.sf_grid, kScTile, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -332,6 +348,16 @@ __global__ void __launch_bounds__(kScTile, 2) k_scatter_batch(BatchTable *bt) {
   }
 }
 
+__global__ void __launch_bounds__(kScTile) k_symfin_batch(BatchTable *bt) {
+  const int nj = bt->njobs;
+  const int total = bt->off_sf[nj];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = find_job(bt->off_sf, nj, item);
+    const int vb = item - bt->off_sf[j], nvb = bt->off_sf[j + 1] - bt->off_sf[j];
+    if (symfin_body<float>(bt->job[j].sig, vb, nvb) && threadIdx.x == 0) bt->halted[j] = 1;
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_tc_batch(BatchTable *bt, int Kpmax, int Npmax, uint32_t tmem_cols, int *status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -342,7 +368,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   sm.Blo = sm.Bhi + Npmax * Kpmax;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sm.Blo + Npmax * Kpmax);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-  __shared__ int s_item;
+  // per-job data of the table, read once: tile offsets, halted flags, inputs
+  __shared__ int s_off[kMaxBatch + 1];
+  __shared__ int s_halt[kMaxBatch];
+  __shared__ const float *s_zf[kMaxBatch];
+  __shared__ const double *s_zn[kMaxBatch];
+  __shared__ __align__(16) SigmaArgs s_args;  // the current job's arguments
   sm.sA = smem_u32(sm.A);
   sm.sAlo = smem_u32(sm.Alo);
   sm.sBhi = smem_u32(sm.Bhi);
@@ -351,7 +382,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nj = bt->njobs;
   const int total = bt->off_tc[nj];
-  if (total == 0) return;
+  // contiguous chunks of tiles: a CTA meets one or two jobs, so it loads
+  // operand B once or twice
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int first = blockIdx.x * chunk, last = min(total, first + chunk);
+  if (first >= last) return;  // uniform: before any TMEM allocation or barrier
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(tmem_slot)),
@@ -363,31 +398,36 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm.sbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  for (int i = tid; i <= nj; i += blockDim.x) s_off[i] = bt->off_tc[i];
+  for (int i = tid; i < nj; i += blockDim.x) {
+    const CtlState *c = bt->job[i].step.ctl;
+    s_halt[i] = c->halt;
+    s_zf[i] = c->zf;
+    s_zn[i] = c->zn;
+  }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
   uint32_t phase = 0;
   bool ok = true;
-  int cur = -1;
-  for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(&bt->tc_next, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= total) break;
-    const int j = find_job(bt->off_tc, nj, item);
-    const BatchJob &J = bt->job[j];
-    if (J.step.ctl->halt) continue;  // block-uniform
+  int cur = -1, Kp = 0, Np = 0;
+  for (int item = first; item < last && ok; ++item) {
+    const int j = find_job(s_off, nj, item);
+    if (s_halt[j]) continue;  // block-uniform
     if (j != cur) {
-      tc_load_B(J.sig, J.Kp, J.Np, sm);
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(&bt->job[j].sig);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+      for (int i = tid; i < (int)(sizeof(SigmaArgs) / 4); i += blockDim.x) dst[i] = src[i];
+      Kp = bt->job[j].Kp;
+      Np = bt->job[j].Np;
+      __syncthreads();
+      tc_load_B(s_args, Kp, Np, sm);  // (ends with a barrier)
       cur = j;
     }
-    const float *zf = J.step.ctl->zf;
-    const long long tile = item - bt->off_tc[j];
-    ok = zf ? tc_tile(J.sig, zf, tile, J.Kp, J.Np, sm, tmem, phase)
-            : tc_tile(J.sig, J.step.ctl->zn, tile, J.Kp, J.Np, sm, tmem, phase);
-    if (!ok) break;
+    const long long tile = item - s_off[j];
+    ok = s_zf[j] ? tc_tile(s_args, s_zf[j], tile, Kp, Np, sm, tmem, phase)
+                 : tc_tile(s_args, s_zn[j], tile, Kp, Np, sm, tmem, phase);
   }
   if (!ok) {
     if (tid == 0) atomicOr(status, 1);
@@ -448,6 +488,7 @@ cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
   cfg->ctas[BK_PROJECT] = 4 * num_sms;
   cfg->ctas[BK_TC] = num_sms * per_sm;
   cfg->ctas[BK_SCATTER] = 3 * num_sms;
+  cfg->ctas[BK_SYMFIN] = 2 * num_sms;
   cfg->ctas[BK_END] = 1;
   return cudaSuccess;
 }
@@ -460,7 +501,8 @@ cudaError_t launch_batch_kernel(int which, const BatchConfig &cfg, BatchTable *d
     case BK_TC:
       k_tc_batch<<<cfg.ctas[BK_TC], kTcThreads, cfg.smem, s>>>(d_table, cfg.Kp, cfg.Np, cfg.cols, status);
       break;
-    case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, kScStageBytes, s>>>(d_table); break;
+    case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, 0, s>>>(d_table); break;
+    case BK_SYMFIN: k_symfin_batch<<<cfg.ctas[BK_SYMFIN], kScTile, 0, s>>>(d_table); break;
     case BK_END: k_batch_end<<<1, kMaxBatch, 0, s>>>(d_table, cond); break;
     default: return cudaErrorInvalidValue;
   }
@@ -494,12 +536,5 @@ cudaError_t build_batch_graph(const BatchConfig &cfg, BatchTable *d_table, int *
   return cudaSuccess;
 }
 
-// Opts the staged-row scatter kernels into their dynamic shared memory (once
-// per process, outside any stream capture).
-cudaError_t prepare_scatter_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScStageBytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_scatter_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kScStageBytes);
-}
 
 }  // namespace sbci

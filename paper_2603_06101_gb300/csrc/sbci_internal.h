@@ -105,8 +105,11 @@ struct SigmaArgs {
   int dot_slot[3];
   double *partials;      // [S_COUNT][grid]
   int grid;
-  int sc_rows;           // scatter work unit: whole alpha rows staged in shared memory (0: none)
-  int *status;           // device error word: bit 1 = a bulk-copy wait of the scatter ran out
+  // singlet-sector split (c = c^T exactly, n_alpha = n_beta): the scatter
+  // writes only the alpha part A (AccT, [Na][Nb]) here, and sigma = A + A^T is
+  // formed by the symmetric finish, which also takes the dots (nullptr: off)
+  void *symA;
+  int sf_grid;           // virtual blocks of the symmetric finish
   // device-controlled mode (ctl != nullptr): input z and output Z come from the
   // controller, the scatter's dots are against (dot_u[0], dot_u[1], ctl->zn),
   // and its last block runs the subspace solve
@@ -119,11 +122,11 @@ struct SigmaArgs {
 // prec: 0 = FP64 scratch and contraction, 1 = FP32 (SIMT) contraction
 cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_scatter(const SigmaArgs &a, int prec, cudaStream_t s);
-// Rows per work unit of the staged-row scatter for FP32 G (0: global gathers).
-int scatter_rows(int npair, int na, int nb, int nlink_a, int prec);
-// Virtual blocks of the scatter: min(work units, 8 x SMs).
-int scatter_grid(long long ndet, int na, int rows, int nsm);
-cudaError_t prepare_scatter_kernels();
+// Virtual blocks of the scatter: min(256-determinant tiles, 8 x SMs).
+int scatter_grid(long long ndet, int nsm);
+// Virtual blocks of the symmetric finish: min(32 x 32 tile pairs, 8 x SMs).
+int symfin_grid(int na, int nsm);
+cudaError_t launch_symfin(const SigmaArgs &a, int prec, cudaStream_t s);
 cudaError_t prepare_sigma_kernels();
 // tcgen05 TF32x3 gather + contract (kernels_loop.cu); writes FP32 G like prec 1.
 bool tc_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
@@ -174,6 +177,7 @@ struct BatchJob;
 bool ctx_batch_job(sbci_ctx *c, BatchJob *j);
 int ctx_step_blocks(const sbci_ctx *c);
 int ctx_scatter_blocks(const sbci_ctx *c);
+int ctx_symfin_blocks(const sbci_ctx *c);  // 0 unless the solve uses the singlet-sector split
 long long ctx_ndet(const sbci_ctx *c);
 long long ctx_launch_count(const sbci_ctx *c);
 size_t ctx_device_bytes(int norb, int nalpha, int nbeta, int k);

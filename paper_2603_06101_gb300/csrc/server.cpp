@@ -87,6 +87,7 @@ void tune_init(ClassGraph &g, int nsm) {
   g.cand[BK_PROJECT] = {nsm, 2 * nsm, 4 * nsm, 8 * nsm};
   for (int k = 1; k <= g.cfg.tc_per_sm_max; ++k) g.cand[BK_TC].push_back(k * nsm);
   g.cand[BK_SCATTER] = {nsm, 2 * nsm, 3 * nsm, 6 * nsm};
+  g.cand[BK_SYMFIN] = {nsm, 2 * nsm, 4 * nsm};
   g.cand[BK_END] = {1};
   for (int k = 0; k < BK_COUNT; ++k) g.ms[k].assign(g.cand[k].size(), std::vector<float>());
 }
@@ -323,7 +324,7 @@ sbci_status launch_batch_round(sbci_server *sv) {
   BatchTable &t = *sv->h_table;
   sv->batch_slots.clear();
   int nj = 0;
-  t.off_step[0] = t.off_sc[0] = t.off_tc[0] = 0;
+  t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
   for (int i = 0; i < (int)sv->slots.size(); ++i) {
     SolveSlot &sl = sv->slots[i];
     if (!sl.used || !sl.batched || nj >= kMaxBatch) continue;
@@ -337,6 +338,7 @@ sbci_status launch_batch_round(sbci_server *sv) {
     t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(sl.ctx);
     t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(sl.ctx);
     t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(sl.ctx) + 127) / 128);
+    t.off_sf[nj + 1] = t.off_sf[nj] + ctx_symfin_blocks(sl.ctx);
     t.halted[nj] = 0;
     sv->batch_slots.push_back(i);
     ++nj;
@@ -416,7 +418,7 @@ struct Engine {
 constexpr int kMaxDevices = 64;
 Engine g_engines[kMaxDevices];
 const char *const kBatchKernelName[BK_COUNT] = {"batch_update", "batch_project", "batch_gather_contract_tc",
-                                                "batch_scatter", "batch_end"};
+                                                "batch_scatter", "batch_symfinish", "batch_end"};
 
 cudaError_t engine_setup(Engine &eng, int dev) {
   if (eng.ready) return cudaSuccess;
@@ -488,7 +490,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     BatchTable &t = *eng.h_table;
     std::vector<int> row;
     int nj = 0;
-    t.off_step[0] = t.off_sc[0] = t.off_tc[0] = 0;
+    t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
     for (int i = 0; i < n; ++i) {
       if (done[i]) continue;
       if (!ctx_batch_job(ctx[i], &t.job[nj])) {  // not batchable: solve it on its own
@@ -507,6 +509,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(ctx[i]);
       t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(ctx[i]);
       t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(ctx[i]) + 127) / 128);
+      t.off_sf[nj + 1] = t.off_sf[nj] + ctx_symfin_blocks(ctx[i]);
       t.halted[nj] = 0;
       row.push_back(i);
       ++nj;
@@ -548,7 +551,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
   if (launches) {
     long long host_launches1 = 0;
     for (int i = 0; i < n; ++i) host_launches1 += ctx_launch_count(ctx[i]);
-    *launches = (long long)(5 * bodies) + (host_launches1 - host_launches0);
+    *launches = (long long)(BK_COUNT * bodies) + (host_launches1 - host_launches0);
   }
   return worst;
 }

@@ -97,15 +97,11 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
   for (int j = 0; j < NV; ++j)
     if (slots[j] >= 0) act[na++] = slots[j];
   finish_slots(a.partials, nvb, act, na, s->dots, a.counter + 0);
-  __shared__ int s_halt;
-  if (threadIdx.x == 0) {
-    s->iters += 1;
-    if (s->iters > s->iter_cap) s->halt = H_CAP;
-    ctl_check(*s);
-    s_halt = s->halt;
-  }
-  __syncthreads();
-  return s_halt != 0;
+  return ctl_run_shadowed(s, [](CtlHead &h) {
+           h.iters += 1;
+           if (h.iters > h.iter_cap) h.halt = H_CAP;
+           ctl_check(h);
+         }) != 0;
 }
 
 // Projection against the stored states (Eq. S31) with the c = c^T

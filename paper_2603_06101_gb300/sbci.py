@@ -52,7 +52,7 @@ class sbci_params(C.Structure):
 class sbci_report(C.Structure):
     _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("converged", C.c_int),
                 ("n_sigma", C.c_int), ("n_sigma_fp64", C.c_int), ("n_step", C.c_int),
-                ("n_restart", C.c_int * 4)]
+                ("n_restart", C.c_int * 4), ("ctl_cycles", C.c_longlong)]
 
 
 class sbci_trace_record(C.Structure):
@@ -67,7 +67,7 @@ class sbci_kernel_stat(C.Structure):
 
 class sbci_batch_class(C.Structure):
     _fields_ = [("Kp", C.c_int), ("Np", C.c_int), ("smem_bytes", C.c_int), ("tc_per_sm_max", C.c_int),
-                ("tuned", C.c_int), ("ctas", C.c_int * 5)]
+                ("tuned", C.c_int), ("ctas", C.c_int * 6)]
 
 
 _lib = None
@@ -330,7 +330,7 @@ def batch_classes() -> list:
     _check(load().sbci_batch_classes(buf, 16, C.byref(n)))
     return [{"Kp": b.Kp, "Np": b.Np, "smem_bytes": b.smem_bytes, "tc_per_sm_max": b.tc_per_sm_max,
              "tuned": bool(b.tuned), "ctas": {"update": b.ctas[0], "project": b.ctas[1], "tensor_core": b.ctas[2],
-                                              "scatter": b.ctas[3], "end": b.ctas[4]}}
+                                              "scatter": b.ctas[3], "symfinish": b.ctas[4], "end": b.ctas[5]}}
             for b in list(buf)[: min(n.value, 16)]]
 
 

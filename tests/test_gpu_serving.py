@@ -128,7 +128,7 @@ def test_batch_profile_same_result():
     sbci.batch_profile(False)
     assert np.array_equal(E1, E0)
     assert set(stats) == {"batch_update", "batch_project", "batch_gather_contract_tc", "batch_scatter",
-                          "batch_end"}
+                          "batch_symfinish", "batch_end"}
     bodies = stats["batch_end"][0]
     assert bodies > 0 and all(v[0] == bodies and v[1] > 0.0 for v in stats.values())
     assert n_graph >= 5 * bodies  # the graph loop ran the same bodies (plus host-driven kernels)
