@@ -80,6 +80,7 @@ struct Solver {
   double *z[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr};
   double *xc = nullptr;  // [k][ndet]
   float *zf = nullptr;   // FP32 copy of the next z (split and FP32 sigma modes)
+  double *pinv = nullptr;  // excited-state preconditioner 1 / guarded(D - Ec0)
   CtlState *d_ctl = nullptr;  // device controller state
   CtlState *h_ctl = nullptr;  // pinned host mirror
   unsigned int *d_counters = nullptr;
@@ -323,6 +324,7 @@ StepArgs step_args(sbci_ctx *c, unsigned long long cond) {
   a.w = s.w;
   a.diag = c->d_diag;
   a.xc = s.xc;
+  a.pinv = s.pinv;
   a.n = c->ndet;
   a.sector = s.p.sector;
   a.na = c->Na;
@@ -479,6 +481,11 @@ sbci_status start_state(sbci_ctx *c, int alpha, double E0) {
   CtlState &h = *s.h_ctl;
   h.alpha = alpha;
   h.Ec0 = alpha > 0 ? s.Ec[0] : 0.0;
+  h.pinv_ready = 0;
+  if (alpha > 0 && s.pinv) {  // the shift is fixed for the state: precompute its preconditioner
+    CK(launch_pinv(c->d_diag, h.Ec0, s.p.guard, c->ndet, s.pinv, c->stream));
+    h.pinv_ready = 1;
+  }
   h.n_sigma = h.n_sigma_fp64 = h.n_step = h.n_stage1 = 0;
   h.ctl_cycles = 0;
   for (int i = 0; i < 4; ++i) h.n_restart[i] = 0;
@@ -634,6 +641,8 @@ void free_solver(sbci_ctx *c) {
   }
   if (s.zf) cudaFree(s.zf);
   s.zf = nullptr;
+  if (s.pinv) cudaFree(s.pinv);
+  s.pinv = nullptr;
   if (s.d_ctl) cudaFree(s.d_ctl);
   if (s.h_ctl) cudaFreeHost(s.h_ctl);
   if (s.d_counters) cudaFree(s.d_counters);
@@ -653,6 +662,7 @@ sbci_status alloc_solver(sbci_ctx *c, int k) {
   }
   RET(dmalloc(&s.xc, (size_t)k * c->ndet));
   if (s.p.prec != SBCI_FP64) RET(dmalloc(&s.zf, (size_t)c->ndet));
+  if (k > 1) RET(dmalloc(&s.pinv, (size_t)c->ndet));
   CK(cudaMemsetAsync(s.xc, 0, sizeof(double) * (size_t)k * c->ndet, c->stream));
   CK(cudaMalloc((void **)&s.d_ctl, sizeof(CtlState)));
   CK(cudaMemsetAsync(s.d_ctl, 0, sizeof(CtlState), c->stream));
@@ -859,7 +869,7 @@ size_t sbci::ctx_device_bytes(int norb, int nalpha, int nbeta, int k) {
   };
   const long long na = binom(norb, nalpha), nb = binom(norb, nbeta), nd = na * nb;
   const long long npair = norb * (norb + 1) / 2;
-  const long long vec = (9LL + k) * nd * 8 + nd * 4;  // x X y Y w z0 z1 Z0 Z1 + stored states + FP32 z
+  const long long vec = (10LL + k) * nd * 8 + nd * 4;  // x X y Y w z0 z1 Z0 Z1 pinv + stored states + FP32 z
   const long long G = npair * nd * 8;            // sigma scratch (FP64 size, shared by FP32 modes)
   const long long tab = (na * nalpha * (norb - nalpha + 1) + nb * nbeta * (norb - nbeta + 1)) * 4;
   return (size_t)(vec + G + tab + nd * 8 + (1 << 20));

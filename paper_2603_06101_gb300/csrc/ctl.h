@@ -50,6 +50,7 @@ struct CtlHead {
   float *zf;
   int alpha, t, first, pending_check, prec, halt;
   int stage;       // 0: low-precision stage (ends with H_SWITCH); 1: to Eq. S61
+  int pinv_ready;  // the step arguments' pinv holds 1 / guarded(D - Ec0) for this state
   int n_stage1;    // H-products spent in stage 1 of this state
   double sx_pending;
   double E;        // E_t

@@ -124,6 +124,18 @@ cudaError_t launch_update_ctl(const StepArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void k_pinv(const double *diag, double E, double guard, long long n, double *out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = recip(guarded(diag[i] - E, guard));
+}
+
+cudaError_t launch_pinv(const double *diag, double E, double guard, long long n, double *out, cudaStream_t s) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  k_pinv<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(diag, E, guard, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_project_ctl(const StepArgs &a, int grid, cudaStream_t s) {
   k_project_ctl<<<grid, kStepThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -12,6 +12,7 @@ struct StepArgs {
   double *x, *X, *y, *Y, *w;
   const double *diag;
   const double *xc;          // [k][n] stored states x_c^i
+  const double *pinv;        // [n] 1 / guarded(D - E_c^0), valid while ctl->pinv_ready
   long long n;
   int sector, na, nb;
   double *partials;          // [S_COUNT][grid] block partials
@@ -22,5 +23,9 @@ struct StepArgs {
 int step_grid(long long n, int nsm);
 cudaError_t launch_update_ctl(const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_project_ctl(const StepArgs &a, int grid, cudaStream_t s);
+// out[i] = 1 / guarded(diag[i] - E): the preconditioner of the excited states,
+// whose shift E_c^0 is fixed for the whole state (the same arithmetic as the
+// update sweep's, so the sweep may read it instead).
+cudaError_t launch_pinv(const double *diag, double E, double guard, long long n, double *out, cudaStream_t s);
 
 }  // namespace sbci

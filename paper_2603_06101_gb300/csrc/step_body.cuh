@@ -49,6 +49,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
   double *wout = proj ? a.w : s->zn;
   float *zf = proj ? nullptr : s->zf;
   const double guard = s->p.guard;
+  const double *pinv = s->pinv_ready ? a.pinv : nullptr;
   constexpr int NV = 10 + kMaxStates;
   double acc[NV];
 #pragma unroll
@@ -64,7 +65,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
     a.x[i] = x;
     a.X[i] = X;
     const double zp = fma(-u.E, x, X) * u.kinv;
-    const double w = zp * recip(guarded(a.diag[i] - u.Epre, guard));
+    const double w = zp * (pinv ? pinv[i] : recip(guarded(a.diag[i] - u.Epre, guard)));
     wout[i] = w;
     if (zf) zf[i] = (float)w;
     acc[0] = fma(x, x, acc[0]);
