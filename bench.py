@@ -328,11 +328,24 @@ def run_gb300(args, rank, world, local_rank):
     base = name[len("batch_"):] if name.startswith("batch_") else name
     base = {"update": "sb_update", "project": "sb_project", "scatter": "sigma_scatter"}.get(base, base)
     if base == "gather_contract_tc" or base == "sigma_gather_contract_tc":
-        peak = pk.get("bf16_tflops", 1900.0) * 0.5  # TF32 dense = half the BF16 rate (1.1 vs 2.25 PF)
-        roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_kind": f"{pk_kind} bf16 x nominal TF32/BF16 ratio 0.5; achieved counts the "
-                             "algorithmic 2 npair^2 flops per determinant once (the 3-term split executes 3x)",
-                "algorithmic_per_launch": flops}
+        # two ceilings: the contraction on the tensor pipe and the HBM traffic the
+        # kernel must move (G written, 4 B per pair, and the FP32 z read, 4 B, per
+        # determinant); the larger ideal time is the binding one
+        tpeak = pk.get("bf16_tflops", 1900.0) * 0.5  # TF32 dense = half the BF16 rate (1.1 vs 2.25 PF)
+        bytes_alg = float(4 * npair + 4) * ndet * units
+        t_tensor = flops / (tpeak * 1e12)
+        t_hbm = bytes_alg / (pk["hbm_gbs"] * 1e9)
+        tensor = {"achieved": flops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                  "frac": flops / avg_s / 1e12 / tpeak, "algorithmic_per_launch": flops,
+                  "peak_kind": f"{pk_kind} bf16 x nominal TF32/BF16 ratio 0.5; algorithmic 2 npair^2 flops "
+                               "per determinant (the 3-term split executes 3x)"}
+        hbm = {"achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": bytes_alg / avg_s / 1e9 / pk["hbm_gbs"], "algorithmic_per_launch": bytes_alg,
+               "peak_kind": pk_kind, "algorithmic_note": f"{4 * npair + 4} B per determinant (G write + z read)"}
+        if t_hbm >= t_tensor:
+            roof = {"bound": "hbm", **hbm, "other_ceiling": {"bound": "tensor", **tensor}}
+        else:
+            roof = {"bound": "tensor", **tensor, "other_ceiling": {"bound": "hbm", **hbm}}
     elif base == "sigma_gather_contract" and args.prec == "fp64":
         peak = 4.0 * 152 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA per clock per SM (1.25 TF/s at 2.07 GHz)
         roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -480,6 +493,7 @@ def run_serving(args):
         server = sbci.Server(budget, slots)
         t0 = time.perf_counter()
         tickets, done, lat = {}, {}, {}
+        serve.errors = {}
         order = np.argsort(arrivals, kind="stable")
         nxt = 0
         while len(done) < n:
@@ -495,6 +509,8 @@ def run_serving(args):
                 r = server.poll(t)
                 if r is not None:
                     done[i] = r
+                    if r[3] != 0:
+                        serve.errors[i] = sbci.last_error()
                     lat[i] = (time.perf_counter() - t0) - arrivals[i]
         makespan = time.perf_counter() - t0
         server.close()
@@ -514,6 +530,7 @@ def run_serving(args):
     gaps = np.random.default_rng(4).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
     span_m, lat_m, done_m = serve(arrivals, p_mixed, args.slots)
+    errors_m = dict(serve.errors)
     # plain FP64, one solve per launch, in arrival order
     t0 = time.perf_counter()
     lat_f = np.zeros(n)
@@ -536,7 +553,8 @@ def run_serving(args):
                 "E_mixed": [float(e) for e in done_m[i][0]], "status_mixed": int(done_m[i][3]),
                 "converged_mixed": [int(r.converged) for r in done_m[i][1]],
                 "n_sigma_mixed": [int(r.n_sigma) for r in done_m[i][1]],
-                "E_fp64": [float(e) for e in E_f[i]], "status_fp64": st_f[i]} for i in bad]
+                "E_fp64": [float(e) for e in E_f[i]], "status_fp64": st_f[i],
+                "error_mixed": errors_m.get(i)} for i in bad]
     line = {
         "serving": f"{n} requests, H6/H8/H10/H12 STO-3G, spacing U(0.7, 3.0) A, 1-4 states (seed 4)",
         "saturation_solves_per_s": capacity, "poisson_rate_per_s": rate,

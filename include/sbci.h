@@ -286,7 +286,8 @@ sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued);
 
 /* *done = 1 once the request has finished; then energies [k] (total),
  * rep [k] and times [2] = {queueing seconds, latency seconds from submit to
- * completion} are written (each nullable) and the solve's status returned. */
+ * completion} are written (each nullable) and the solve's status returned;
+ * for an error status, sbci_last_error() then gives that solve's message. */
 sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, double *energies,
                              sbci_report *rep, double *times);
 

@@ -206,8 +206,7 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
   return SBCI_ERR_INVALID;
 }
 
-sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, const double *u0,
-                      const double *u1, const double *u2) {
+sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   RET(check_prec(c, prec));
   RET(ensure_G(c, prec));
   SigmaArgs a{};
@@ -227,13 +226,7 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   a.npair = c->npair;
   a.npair_pad = c->npair_pad;
   a.ndet = c->ndet;
-  a.dot_u[0] = u0;
-  a.dot_u[1] = u1;
-  a.dot_u[2] = u2;
-  a.dot_slot[0] = S_HXZ;
-  a.dot_slot[1] = S_HYZ;
-  a.dot_slot[2] = S_HZZ;
-  a.partials = c->d_partials;
+  a.partials = c->d_partials;  // (no dots: dot_u all null)
   a.grid = scatter_grid(c->ndet, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   if (prec == SBCI_TF32X3)
@@ -244,8 +237,8 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec, cons
   return SBCI_OK;
 }
 
-sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
-  RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, c->grid, s0, s1, c->d_result, c->stream); }));
+sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1, int grid) {
+  RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, grid, s0, s1, c->d_result, c->stream); }));
   CK(cudaMemcpyAsync(c->h_result + s0, c->d_result + s0, sizeof(double) * (s1 - s0),
                      cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -264,10 +257,15 @@ sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1) {
 
 // dots over up to 16 pairs, results in h_result[S_GEN0 + i]
 sbci_status gen_dots(sbci_ctx *c, std::vector<const double *> u, std::vector<const double *> v) {
+  // about four elements per thread, at most the partials' capacity of blocks
+  long long g = (c->ndet + 1023) / 1024;
+  if (g > c->grid) g = c->grid;
+  if (g < 1) g = 1;
+  const int grid = (int)g;
   RET(timed(c, K_DOTS, [&] {
-    return launch_dots(u.data(), v.data(), (int)u.size(), c->ndet, c->d_partials, c->grid, c->stream);
+    return launch_dots(u.data(), v.data(), (int)u.size(), c->ndet, c->d_partials, grid, c->stream);
   }));
-  return reduce_and_fetch(c, S_GEN0, S_GEN0 + (int)u.size());
+  return reduce_and_fetch(c, S_GEN0, S_GEN0 + (int)u.size(), grid);
 }
 
 sbci_status lincomb(sbci_ctx *c, double *out, std::vector<const double *> in, std::vector<double> co) {
@@ -496,7 +494,7 @@ sbci_status start_state(sbci_ctx *c, int alpha, double E0) {
 // X <- H x in FP64; returns x.x, x.X and X.X.
 sbci_status resync(sbci_ctx *c, double *xx, double *xX, double *XX) {
   Solver &s = c->s;
-  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64));
   RET(gen_dots(c, {s.x, s.x, s.X}, {s.x, s.X, s.X}));
   *xx = c->h_result[S_GEN0];
   *xX = c->h_result[S_GEN0 + 1];
@@ -513,7 +511,7 @@ sbci_status mix_noise(sbci_ctx *c, int alpha, double *E0) {
   Solver &s = c->s;
   CK(launch_splitmix(s.y, c->ndet, (unsigned long long)s.p.noise_seed, alpha, c->stream));
   if (s.p.sector) CK(launch_symmetrize(s.y, c->Na, c->stream));
-  RET(run_sigma(c, s.y, s.Y, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(run_sigma(c, s.y, s.Y, SBCI_FP64));
   RET(gen_dots(c, {s.y, s.x}, {s.y, s.x}));
   const double nr = std::sqrt(c->h_result[S_GEN0]), nx = std::sqrt(c->h_result[S_GEN0 + 1]);
   const double eta = s.p.start_noise;
@@ -739,7 +737,7 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
     CK(cudaMemsetAsync(s.w, 0, sizeof(double) * c->ndet, c->stream));
     for (auto &kv : basis[i])
       CK(cudaMemcpyAsync(s.w + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, SBCI_FP64, nullptr, nullptr, nullptr));
+    RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, SBCI_FP64));
   }
   CK(cudaStreamSynchronize(c->stream));
   for (int i = 0; i < m; ++i)
@@ -796,7 +794,7 @@ sbci_status init_from_vector(sbci_ctx *c, const double *c0, double *E0) {
     return SBCI_ERR_INVALID;
   }
   RET(lincomb(c, s.x, {s.x}, {1.0 / nrm}));
-  RET(run_sigma(c, s.x, s.X, SBCI_FP64, nullptr, nullptr, nullptr));
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64));
   RET(gen_dots(c, {s.x}, {s.X}));
   *E0 = c->h_result[S_GEN0];
   return SBCI_OK;
@@ -1188,10 +1186,10 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
     double *dst = out + v * n;
     if (!on_device) {
       CK(cudaMemcpyAsync(c->d_tmp_in, src, n * 8, cudaMemcpyHostToDevice, c->stream));
-      RET(run_sigma(c, c->d_tmp_in, c->d_tmp_out, prec, nullptr, nullptr, nullptr));
+      RET(run_sigma(c, c->d_tmp_in, c->d_tmp_out, prec));
       CK(cudaMemcpyAsync(dst, c->d_tmp_out, n * 8, cudaMemcpyDeviceToHost, c->stream));
     } else {
-      RET(run_sigma(c, src, dst, prec, nullptr, nullptr, nullptr));
+      RET(run_sigma(c, src, dst, prec));
     }
   }
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -92,7 +92,8 @@ __host__ __device__ inline double f_rsqrt(double x) {
 #else
   double r = (double)(1.0f / sqrtf((float)x));
 #endif
-  for (int i = 0; i < 3; ++i) r = r * fma(-0.5 * x * r, r, 1.5);  // r <- r (3 - x r^2) / 2
+  // two Newton steps from the ~23-bit estimate: ~46, then FP64 rounding level
+  for (int i = 0; i < 2; ++i) r = r * fma(-0.5 * x * r, r, 1.5);  // r <- r (3 - x r^2) / 2
   return r;
 }
 
@@ -201,25 +202,31 @@ __host__ __device__ inline double rqi_refine(const double *V, double &lam, doubl
 template <int n>
 __host__ __device__ inline void ctl_eigh(const double *Ain, double *w, double *V);
 
-// Lowest two eigenpairs of a 2x2 / 3x3 symmetric V to FP64 accuracy: FP32
-// Jacobi, then one FP64 Rayleigh-quotient step each; falls back to the FP64
-// Jacobi solver when a refined residual is not at rounding level.
+// Lowest two eigenpairs of a 2x2 / 3x3 symmetric V: FP32 Jacobi, then one
+// FP64 Rayleigh-quotient step for the lowest pair (E_{t+1} and the step
+// coefficients need FP64 accuracy); the second pair only seeds the next
+// state's start vector (S1.4), whose H-image is formed consistently from the
+// same coefficients, so its FP32 accuracy is kept.  Falls back to the FP64
+// Jacobi solver when the refined residual is not at rounding level or the
+// order is lost.
 template <int n>
 __host__ __device__ inline void ctl_eigh_fast(const double *V, double *w, double *U) {
   float wf[3], Uf[9];
   eigh_f32<n>(V, wf, Uf);
   double scale = 0.0;
   for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(V[i]));
-  bool ok = true;
-  for (int j = 0; j < 2 && j < n; ++j) {
-    double v[3], lam = (double)wf[j];
-    for (int i = 0; i < n; ++i) v[i] = (double)Uf[i * n + j];
-    const double r = rqi_refine<n>(V, lam, v);
-    if (!(r <= 1e-26 * scale * scale)) ok = false;
-    w[j] = lam;
-    for (int i = 0; i < n; ++i) U[i * n + j] = v[i];
+  double v[3], lam = (double)wf[0];
+  for (int i = 0; i < n; ++i) v[i] = (double)Uf[i * n];
+  const double r = rqi_refine<n>(V, lam, v);
+  w[0] = lam;
+  for (int i = 0; i < n; ++i) U[i * n] = v[i];
+  w[1] = (double)wf[1];
+  for (int i = 0; i < n; ++i) U[i * n + 1] = (double)Uf[i * n + 1];
+  if (n == 3) {
+    w[2] = (double)wf[2];
+    for (int i = 0; i < n; ++i) U[i * n + 2] = (double)Uf[i * n + 2];
   }
-  if (!ok || (n > 1 && !(w[0] <= w[1]))) ctl_eigh<n>(V, w, U);
+  if (!(r <= 1e-26 * scale * scale) || !(w[0] <= w[1])) ctl_eigh<n>(V, w, U);
 }
 
 template <int n>
@@ -429,7 +436,7 @@ __host__ __device__ inline void ctl_check(CtlHead &s) {
     s.t = 0;
   } else {
     s.t += 1;
-    const double gy = d[S_NYY] - d[S_NXY] * d[S_NXY] / d[S_NXX];
+    const double gy = d[S_NYY] - d[S_NXY] * d[S_NXY] * f_recip(d[S_NXX]);
     if (gy < s.p.gs_tol * d[S_NYY]) {  // y inside span{x}: first-step path
       s.first = 1;
       s.sx_pending = f_rsqrt(d[S_NXX]);

@@ -29,7 +29,8 @@ constexpr int kRows = 8;    // W rows per register block of the contraction
 template <typename AccT, typename T>
 __device__ __forceinline__ void simt_gather(const SigmaArgs &a, const T *cin, long long I, int tid, AccT *sD) {
   for (int q = 0; q < a.npair; ++q) sD[q * kTile + tid] = (AccT)0;
-  const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
+  int ia, ib;
+    split_det(I, a.nb, ia, ib);
   const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
   const T *ccol = cin + ib;
   for_links<8, T>(

@@ -28,6 +28,15 @@ __host__ __device__ inline int link_pair(uint32_t v) { return (int)((v >> kPairS
 __host__ __device__ inline bool link_neg(uint32_t v) { return (v & kSignBit) != 0u; }
 
 #ifdef __CUDACC__
+// (Ia, Ib) of flat determinant index I = Ia * nb + Ib.  Determinant counts
+// stay below 2^31 (the largest space, n = 16, has 165.6 M), so 32-bit
+// unsigned division suffices; 64-bit division is a long instruction sequence.
+__device__ __forceinline__ void split_det(long long I, int nb, int &ia, int &ib) {
+  const unsigned u = (unsigned)I, q = u / (unsigned)nb;
+  ia = (int)q;
+  ib = (int)(u - q * (unsigned)nb);
+}
+
 // Visits the links of one string U at a time: the U list entries, then the U
 // gathered values (independent loads, all in flight), then the U updates.
 // Entry e of the list is lst[e * stride] (stride 1: a row of a [N][nlink]

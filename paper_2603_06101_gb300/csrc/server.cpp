@@ -214,6 +214,7 @@ struct Result {
   std::vector<double> energies;
   std::vector<sbci_report> rep;
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  std::string error;  // the library's message when status is an error
 };
 
 }  // namespace
@@ -243,6 +244,7 @@ namespace {
 sbci_status retire(sbci_server *sv, SolveSlot &sl, sbci_status st) {
   Result &r = sv->results[sl.req.ticket];
   r.status = st;
+  if (st != SBCI_OK) r.error = sbci_last_error();
   r.energies.assign(sl.req.k, 0.0);
   r.rep.assign(sl.req.k, sbci_report{});
   if (st == SBCI_OK || st == SBCI_ERR_NOT_CONVERGED) {
@@ -759,6 +761,7 @@ sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, doubl
     times[0] = r.t_admit - r.t_submit;  // queueing
     times[1] = r.t_done - r.t_submit;   // latency
   }
+  if (r.status != SBCI_OK) set_error(r.error);
   return r.status;
 }
 

@@ -36,7 +36,8 @@ __device__ __forceinline__ bool scatter_body(const SigmaArgs &a, int vb, int nvb
   for (long long tile = vb; tile < ntiles; tile += nvb) {
     const long long I = tile * kScTile + tid;
     if (I >= a.ndet) continue;
-    const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
+    int ia, ib;
+    split_det(I, a.nb, ia, ib);
     AccT acc = (AccT)0;
     const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
     const AccT *gcol = G + ib;

@@ -122,7 +122,8 @@ __device__ __forceinline__ void project_body(const StepArgs &a, int vb, int nvb)
   for (long long i = (long long)vb * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     double v = a.w[i];
     if (a.sector) {
-      const int ia = (int)(i / a.nb), ib = (int)(i - (long long)ia * a.nb);
+      int ia, ib;
+      split_det(i, a.nb, ia, ib);
       v = 0.5 * (v + a.w[(size_t)ib * a.nb + ia]);
     }
 #pragma unroll

@@ -26,6 +26,14 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
   return r;
 }
 
+// The same rounding (to nearest, ties away from zero) with two integer
+// operations on the bit pattern: add half a TF32 unit to the magnitude bits
+// and clear the 13 dropped bits (a carry into the exponent is the correct
+// result).  For the finite values of the tile split.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 // Shared-memory matrix descriptor: no swizzle, start/LBO/SBO in 16-byte units,
 // descriptor version 1 (bit 46).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -161,7 +169,8 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const T *cin, long l
     for (int q = 0; q < Kp; q += 4)
       *reinterpret_cast<float4 *>(mine + opnd_off(row, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
-      const int ia = (int)(I / a.nb), ib = (int)(I - (long long)ia * a.nb);
+      int ia, ib;
+    split_det(I, a.nb, ia, ib);
       if (half == 0) {
         const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
         const T *ccol = cin + ib;
@@ -191,14 +200,14 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const T *cin, long l
       const float4 va = *p, vb = *pl;
       const float4 v = make_float4(va.x + vb.x, va.y + vb.y, va.z + vb.z, va.w + vb.w);
       float4 h, l;
-      h.x = __uint_as_float(tf32_bits(v.x));
-      h.y = __uint_as_float(tf32_bits(v.y));
-      h.z = __uint_as_float(tf32_bits(v.z));
-      h.w = __uint_as_float(tf32_bits(v.w));
-      l.x = __uint_as_float(tf32_bits(v.x - h.x));
-      l.y = __uint_as_float(tf32_bits(v.y - h.y));
-      l.z = __uint_as_float(tf32_bits(v.z - h.z));
-      l.w = __uint_as_float(tf32_bits(v.w - h.w));
+      h.x = tf32_round(v.x);
+      h.y = tf32_round(v.y);
+      h.z = tf32_round(v.z);
+      h.w = tf32_round(v.w);
+      l.x = tf32_round(v.x - h.x);
+      l.y = tf32_round(v.y - h.y);
+      l.z = tf32_round(v.z - h.z);
+      l.w = tf32_round(v.w - h.w);
       *p = h;
       *pl = l;
     }

@@ -309,6 +309,11 @@ def solve_batch(contexts, k: int, p: sbci_params | None = None):
     return E, list(R), st
 
 
+def last_error() -> str:
+    """sbci_last_error: the calling thread's last error message."""
+    return load().sbci_last_error().decode()
+
+
 def batch_profile(enable: bool):
     """sbci_batch_profile: reset the batch engine's kernel statistics; enable
     event timing of every batched kernel launch."""
