@@ -114,7 +114,10 @@ typedef struct {
   int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle,
                          6 low-precision stage ended: switch to FP64 refinement,
                          7 refinement budget spent: the state continues with
-                           FP64 sigma from an exact X (host record) */
+                           FP64 sigma from an exact X (host record),
+                         8 later-step coefficients undefined (zero denominator
+                           in Eqs. S53-S55): the step was taken on the
+                           first-step path from x */
   int prec;           /* sbci_precision of the sigma used in the step */
 } sbci_trace_record;
 

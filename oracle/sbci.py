@@ -43,6 +43,11 @@ R11 start_noise = eta > 0 adds eta * r_alpha / |r_alpha| to the (unit) start
     of its start vector; the small full-symmetry component lets it reach the
     lowest state of the orthogonal complement in symmetric molecules.  The
     default eta = 0 is the paper's choice (S1.1 / S1.4 starts as stated).
+R15 If a later step's coefficients are undefined (a zero denominator in
+    Eqs. S53-S55: the lowest Ritz vector of span{x, y, z} gives no finite k,
+    b or c), that step is taken on the first-step path (Eqs. S10-S24) from
+    x/|x| with y dropped, as a restart just before it would (trace event
+    "undef").
 """
 from __future__ import annotations
 
@@ -204,6 +209,19 @@ class SBCI1:
                     y = np.zeros_like(x)
                     Y = np.zeros_like(x)
                     t = 0
+            undefined = False
+            if t > 0:
+                E_new, b, c, k, sec = self._later_step(x, X, y, Y, z, Z)
+                if not np.all(np.isfinite([E_new, b, c, k])):
+                    # R15: a zero denominator in S53-S55 leaves the later step
+                    # undefined; this step is taken on the first-step path
+                    # from x/|x| with y dropped, as after a restart
+                    nx = np.sqrt(x @ x)
+                    x, X = x / nx, X / nx
+                    y = np.zeros_like(x)
+                    Y = np.zeros_like(x)
+                    t = 0
+                    undefined = True
             if t == 0:
                 E_new, b, c, k, sec = self._first_step(x, X, z, Z)
                 y_new = -c * z  # S25
@@ -211,7 +229,6 @@ class SBCI1:
                 x_new = x + y_new  # S27 (b_0 = 1)
                 X_new = X + Y_new  # S28
             else:
-                E_new, b, c, k, sec = self._later_step(x, X, y, Y, z, Z)
                 y_new = y - c * z  # S56
                 Y_new = Y - c * Z  # S57
                 x_new = x + b * y_new  # S58
@@ -238,7 +255,7 @@ class SBCI1:
             elif t + 1 >= p.max_cycle:
                 cause = "max"
             self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz,
-                                         f"restart:{cause}" if cause else ""))
+                                         f"restart:{cause}" if cause else ("undef" if undefined else "")))
             E = E_new
             if cause:  # restart of Algorithm 1 with R4
                 restarts[cause] += 1

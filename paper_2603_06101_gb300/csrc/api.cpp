@@ -109,6 +109,7 @@ struct sbci_ctx {
   uint32_t *d_link_bT = nullptr;  // beta lists transposed, [nlink_b][Nb]
   double *d_W = nullptr;
   float *d_Wf = nullptr;
+  float *d_cf = nullptr;      // FP32 copy of a plain sigma's input (tensor-core mode)
   uint32_t *d_Wtc = nullptr;  // TF32 hi/lo operand B of the tensor-core sigma (nullptr: unsupported)
   double *d_diag = nullptr;
   double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
@@ -229,10 +230,14 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   a.partials = c->d_partials;  // (no dots: dot_u all null)
   a.grid = scatter_grid(c->ndet, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
-  if (prec == SBCI_TF32X3)
+  if (prec == SBCI_TF32X3) {
+    if (!c->d_cf) RET(dmalloc(&c->d_cf, (size_t)c->ndet));
+    CK(launch_to_float(in, c->d_cf, c->ndet, c->stream));
+    a.cf = c->d_cf;
     RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
-  else
+  } else {
     RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
+  }
   RET(timed(c, K_SC, [&] { return launch_scatter(a, p32, c->stream); }));
   return SBCI_OK;
 }
@@ -931,7 +936,7 @@ void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_diag, c->d_ea, c->d_eb,
+  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_cf, c->d_diag, c->d_ea, c->d_eb,
                   c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in, c->d_tmp_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);

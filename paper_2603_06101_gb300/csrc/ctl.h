@@ -427,7 +427,7 @@ __host__ __device__ inline void ctl_check(CtlHead &s) {
   else if (fabs(r.k) < s.p.x_th1 || fabs(r.k) > s.p.x_th2) cause = 2;
   else if (dz > s.p.r1 && r.t > 0) cause = 3;
   else if (r.t + 1 >= s.p.max_cycle) cause = 4;
-  r.event = cause ? cause + 1 : 0;
+  r.event = cause ? cause + 1 : r.event;  // (8 stays when no restart follows)
   ctl_commit(s, r);
   if (cause) {
     s.n_restart[cause - 1] += 1;
@@ -452,8 +452,22 @@ __host__ __device__ inline void ctl_check(CtlHead &s) {
 __host__ __device__ inline void ctl_solve(CtlHead &s) {
   if (s.halt) return;
   StepOut o;
-  if (s.first) ctl_first_step(s, o);
-  else ctl_later_step(s, o);
+  int event = 0;
+  if (s.first) {
+    ctl_first_step(s, o);
+  } else {
+    ctl_later_step(s, o);
+    if (!isfinite(o.E) || !isfinite(o.k) || !isfinite(o.b) || !isfinite(o.c)) {
+      // reading R15: a zero denominator in Eqs. S53-S55 leaves the later step
+      // undefined; the step is taken on the first-step path from x/|x| (y
+      // dropped), as a restart just before it would
+      s.first = 1;
+      s.sx_pending = f_rsqrt(s.dots[S_NXX]);
+      s.t = 0;
+      event = 8;
+      ctl_first_step(s, o);
+    }
+  }
   if (!isfinite(o.E) || !isfinite(o.k) || !isfinite(o.b) || !isfinite(o.c)) {
     s.halt = H_NUMERIC;
     return;
@@ -471,7 +485,7 @@ __host__ __device__ inline void ctl_solve(CtlHead &s) {
   r.k = o.k;
   r.dE = 0.0;
   r.dz = 0.0;
-  r.event = 0;
+  r.event = event;
   r.prec = s.prec;
   s.pending = r;
   s.E_solve = o.E;

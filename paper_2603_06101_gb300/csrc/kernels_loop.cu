@@ -213,12 +213,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   sm.sBlo = smem_u32(sm.Blo);
   sm.sbar = smem_u32(mbar);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const double *cin = a.c;
-  const float *cinf = nullptr;
+  const float *cin = a.cf;
   if (a.ctl) {
     if (a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
-    cin = a.ctl->zn;
-    cinf = a.ctl->zf;
+    cin = a.ctl->zf;
+  }
+  if (!cin) {  // no FP32 input: refuse (uniform, before any allocation)
+    if (threadIdx.x == 0) atomicOr(status, 4);
+    return;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   uint32_t phase = 0;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
-    ok = cinf ? tc_tile(a, cinf, tile, Kp, Np, sm, tmem, phase) : tc_tile(a, cin, tile, Kp, Np, sm, tmem, phase);
+    ok = tc_tile(a, cin, tile, Kp, Np, sm, tmem, phase);
   if (!ok) {
     if (tid == 0) atomicOr(status, 1);
     mbar_wait(sm.sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
@@ -384,7 +386,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   __shared__ int s_off[kMaxBatch + 1];
   __shared__ int s_halt[kMaxBatch];
   __shared__ const float *s_zf[kMaxBatch];
-  __shared__ const double *s_zn[kMaxBatch];
   __shared__ __align__(16) SigmaArgs s_args;  // the current job's arguments
   sm.sA = smem_u32(sm.A);
   sm.sAlo = smem_u32(sm.Alo);
@@ -415,7 +416,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const CtlState *c = bt->job[i].step.ctl;
     s_halt[i] = c->halt;
     s_zf[i] = c->zf;
-    s_zn[i] = c->zn;
   }
   fence_before();
   __syncthreads();
@@ -438,8 +438,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       cur = j;
     }
     const long long tile = item - s_off[j];
-    ok = s_zf[j] ? tc_tile(s_args, s_zf[j], tile, Kp, Np, sm, tmem, phase)
-                 : tc_tile(s_args, s_zn[j], tile, Kp, Np, sm, tmem, phase);
+    if (!s_zf[j]) {  // a batched solve always has its FP32 copy of z; refuse otherwise
+      if (tid == 0) atomicOr(status, 4);
+      continue;
+    }
+    ok = tc_tile(s_args, s_zf[j], tile, Kp, Np, sm, tmem, phase);
   }
   if (!ok) {
     if (tid == 0) atomicOr(status, 1);
@@ -480,6 +483,7 @@ cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
   while (cfg->cols < (uint32_t)Np) cfg->cols <<= 1;
   cfg->smem = (size_t)(2 * kTcM * Kp + 2 * Np * Kp) * 4 + 16;
   if (cfg->smem > 227 * 1024) return cudaErrorInvalidValue;
+
   // the opt-in limit is a property of the function, shared by every class and
   // context: always the largest the device allows (minus the kernel's static
   // shared memory), so no later setting can fail a launch

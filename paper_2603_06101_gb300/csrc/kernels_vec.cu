@@ -180,6 +180,16 @@ cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, co
   return cudaGetLastError();
 }
 
+__global__ void k_to_float(const double *in, float *out, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)in[i];
+}
+
+cudaError_t launch_to_float(const double *in, float *out, long long n, cudaStream_t s) {
+  k_to_float<<<grid_for(n, 8192), kVecThreads, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s) {
   k_splitmix<<<grid_for(n, 8192), kVecThreads, 0, s>>>(r, n, seed, alpha);
   return cudaGetLastError();

@@ -71,6 +71,7 @@ __device__ __forceinline__ void for_links(const uint32_t *lst, int n, long long 
       if (j < m) use(v[j], x[j]);
   }
 }
+
 #endif
 
 constexpr int kMaxOrb = 16;
@@ -99,6 +100,7 @@ enum Slot : int {
 // Arguments of the sigma kernels for one vector.
 struct SigmaArgs {
   const double *c;       // [Na*Nb]
+  const float *cf;       // FP32 copy of c for the tensor-core gather (plain calls)
   double *sigma;         // [Na*Nb]
   void *G;               // [npair][ndet] FP64 or FP32 scratch
   const uint32_t *link_a, *link_b;
@@ -146,6 +148,8 @@ cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid,
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
 // Helper kernels (kernels_vec.cu)
+// out = (float) in, elementwise.
+cudaError_t launch_to_float(const double *in, float *out, long long n, cudaStream_t s);
 // out = sum_i coef_i in_i (out may alias in[0]); up to 8 inputs.
 cudaError_t launch_lincomb(double *out, const double *const *in, const double *coef, int nin,
                            long long n, cudaStream_t s);

@@ -144,10 +144,9 @@ __device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, co
 // One tile of 128 determinants: gather, split, three MMAs per K step, bounded
 // wait, epilogue into G.  256 threads.  Returns false (block-uniformly) if
 // the MMA-completion wait ran out.
-// cin: the input vector, FP64 or its FP32 copy (the gather rounds to FP32
-// either way, so both give the same D).
-template <typename T>
-__device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const T *cin, long long tile, int Kp, int Np,
+// cin: the FP32 copy of the input vector (written by its producer, or by a
+// conversion before a plain sigma call).
+__device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const float *cin, long long tile, int Kp, int Np,
                                         const TcSmem &sm, uint32_t tmem, uint32_t &phase) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int npair = a.npair;
@@ -170,23 +169,21 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const T *cin, long l
       *reinterpret_cast<float4 *>(mine + opnd_off(row, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
       int ia, ib;
-    split_det(I, a.nb, ia, ib);
+      split_det(I, a.nb, ia, ib);
       if (half == 0) {
         const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-        const T *ccol = cin + ib;
-        for_links<8, T>(
+        const float *ccol = cin + ib;
+        for_links<8, float>(
             la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
-            [&](uint32_t v, T cv) {
-              const float f = (float)cv;
+            [&](uint32_t v, float f) {
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
             });
       } else {
         const uint32_t *lb = a.link_bT + ib;
-        const T *crow = cin + (size_t)ia * a.nb;
-        for_links<8, T>(
+        const float *crow = cin + (size_t)ia * a.nb;
+        for_links<8, float>(
             lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-            [&](uint32_t v, T cv) {
-              const float f = (float)cv;
+            [&](uint32_t v, float f) {
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
             });
       }

@@ -212,3 +212,30 @@ def test_energy_conservation_diagnostic_is_close_to_one():
             ratios.append(abs(dE / ((2.0 / c2) * dT)))
     assert len(ratios) >= 5
     assert 0.3 < float(np.median(ratios)) < 3.0
+
+
+def test_r15_later_step_undefined_and_first_step_fallback():
+    """A later step can be undefined (reading R15): with H = diag(1, 2, 0) and
+    x = (1, 1, 1), y = (1, -1, 0), z = (-1, -1, 2), the lowest Ritz vector of
+    span{x, y, z} is e3 = (x + z) / 3, which has no y component, so no finite
+    c reaches it through x + b (y - c z) (Eq. S55 divides by zero).  The
+    first-step path from x / |x| on the same z is defined and is the lowest
+    Ritz vector of span{x, z}."""
+    Hm = np.diag([1.0, 2.0, 0.0])
+    H = lambda v: Hm @ v
+    run = sbci.SBCI1(H, np.diag(Hm).copy(), (1, 3))
+    x = np.array([1.0, 1.0, 1.0])
+    y = np.array([1.0, -1.0, 0.0])
+    z = np.array([-1.0, -1.0, 2.0])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        E, b, c, k, _ = run._later_step(x, H(x), y, H(y), z, H(z))
+    assert abs(E) < 1e-12  # the Ritz value itself is fine: e3's eigenvalue 0
+    # in floating point the zero denominator comes out as 0 (non-finite c: R15)
+    # or as a rounding residue (an astronomically large c, and |k| = 3 outside
+    # [x_th1, x_th2], so S62b restarts right after the step)
+    assert (not np.all(np.isfinite([E, b, c, k]))) or (abs(c) > 1e12 and abs(k) > run.p.x_th2)
+    xn = x / np.linalg.norm(x)
+    E1, b1, c1, k1, _ = run._first_step(xn, H(xn), z, H(z))
+    assert np.all(np.isfinite([E1, b1, c1, k1]))
+    B = np.linalg.qr(np.stack([xn, z], axis=1))[0]
+    assert abs(E1 - np.linalg.eigvalsh(B.T @ Hm @ B)[0]) < 1e-12
