@@ -72,6 +72,35 @@ __device__ __forceinline__ void for_links(const uint32_t *lst, int n, long long 
   }
 }
 
+
+// The same visit with the list loads of batch k + 1 issued before the
+// gathered values of batch k are used, so each batch waits for one memory
+// round trip (its values) instead of two (entries, then values).  Same order
+// of use as for_links.
+template <int U, typename T, typename Load, typename Use>
+__device__ __forceinline__ void for_links_pipelined(const uint32_t *lst, int n, long long stride, Load load,
+                                                    Use use) {
+  uint32_t v[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+    if (j < n) v[j] = __ldg(lst + j * stride);
+  for (int e = 0; e < n; e += U) {
+    const int m = n - e;
+    T x[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (j < m) x[j] = load(v[j]);
+    uint32_t vn[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (e + U + j < n) vn[j] = __ldg(lst + (e + U + j) * stride);
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (j < m) use(v[j], x[j]);
+#pragma unroll
+    for (int j = 0; j < U; ++j) v[j] = vn[j];
+  }
+}
 #endif
 
 constexpr int kMaxOrb = 16;

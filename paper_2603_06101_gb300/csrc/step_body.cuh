@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ctl.h"
 #include "devreduce.cuh"
 #include "sbci_internal.h"
@@ -55,35 +57,43 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
 #pragma unroll
   for (int j = 0; j < NV; ++j) acc[j] = 0.0;
   const long long stride = (long long)nvb * blockDim.x;
-  for (long long i = (long long)vb * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const double y = fma(-u.c, z[i], u.sy * a.y[i]);
-    const double Y = fma(-u.c, Z[i], u.sy * a.Y[i]);
-    const double x = fma(u.b, y, u.sx * a.x[i]);
-    const double X = fma(u.b, Y, u.sx * a.X[i]);
-    a.y[i] = y;
-    a.Y[i] = Y;
-    a.x[i] = x;
-    a.X[i] = X;
-    const double zp = fma(-u.E, x, X) * u.kinv;
-    const double w = zp * (pinv ? pinv[i] : recip(guarded(a.diag[i] - u.Epre, guard)));
-    wout[i] = w;
-    if (zf) zf[i] = (float)w;
-    acc[0] = fma(x, x, acc[0]);
-    acc[1] = fma(x, y, acc[1]);
-    acc[2] = fma(y, y, acc[2]);
-    acc[3] = fma(x, X, acc[3]);
-    acc[4] = fma(x, Y, acc[4]);
-    acc[5] = fma(y, Y, acc[5]);
-    acc[6] = fma(zp, zp, acc[6]);
-    if (!proj) {
-      acc[7] = fma(x, w, acc[7]);
-      acc[8] = fma(y, w, acc[8]);
-      acc[9] = fma(w, w, acc[9]);
-    }
+  // Unit: sx = sy = 1 (every step but the first of a cycle and the lazily
+  // scaled restart); then sx * x and sy * y are x and y exactly and their
+  // products are skipped (two fewer FP64 operations per recurrence).
+  auto sweep = [&](auto unit_tag) {
+    constexpr bool Unit = decltype(unit_tag)::value;
+    for (long long i = (long long)vb * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+      const double y = fma(-u.c, z[i], Unit ? a.y[i] : u.sy * a.y[i]);
+      const double Y = fma(-u.c, Z[i], Unit ? a.Y[i] : u.sy * a.Y[i]);
+      const double x = fma(u.b, y, Unit ? a.x[i] : u.sx * a.x[i]);
+      const double X = fma(u.b, Y, Unit ? a.X[i] : u.sx * a.X[i]);
+      a.y[i] = y;
+      a.Y[i] = Y;
+      a.x[i] = x;
+      a.X[i] = X;
+      const double zp = fma(-u.E, x, X) * u.kinv;
+      const double w = zp * (pinv ? pinv[i] : recip(guarded(a.diag[i] - u.Epre, guard)));
+      wout[i] = w;
+      if (zf) zf[i] = (float)w;
+      acc[0] = fma(x, x, acc[0]);
+      acc[1] = fma(x, y, acc[1]);
+      acc[2] = fma(y, y, acc[2]);
+      acc[3] = fma(x, X, acc[3]);
+      acc[4] = fma(x, Y, acc[4]);
+      acc[5] = fma(y, Y, acc[5]);
+      acc[6] = fma(zp, zp, acc[6]);
+      if (!proj) {
+        acc[7] = fma(x, w, acc[7]);
+        acc[8] = fma(y, w, acc[8]);
+        acc[9] = fma(w, w, acc[9]);
+      }
 #pragma unroll
-    for (int j = 0; j < kMaxStates; ++j)
-      if (j < nxc) acc[10 + j] = fma(a.xc[(size_t)j * a.n + i], w, acc[10 + j]);
-  }
+      for (int j = 0; j < kMaxStates; ++j)
+        if (j < nxc) acc[10 + j] = fma(a.xc[(size_t)j * a.n + i], w, acc[10 + j]);
+    }
+  };
+  if (u.sx == 1.0 && u.sy == 1.0) sweep(std::true_type{});
+  else sweep(std::false_type{});
   int slots[NV];
 #pragma unroll
   for (int j = 0; j < 7; ++j) slots[j] = S_NXX + j;

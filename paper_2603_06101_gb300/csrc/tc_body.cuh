@@ -88,6 +88,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// tcgen05.ld of 16 columns into r[0..15] without waiting (the caller waits).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -173,7 +184,7 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const float *cin, lo
       if (half == 0) {
         const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
         const float *ccol = cin + ib;
-        for_links<8, float>(
+        for_links_pipelined<8, float>(
             la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
             [&](uint32_t v, float f) {
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
@@ -181,7 +192,7 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const float *cin, lo
       } else {
         const uint32_t *lb = a.link_bT + ib;
         const float *crow = cin + (size_t)ia * a.nb;
-        for_links<8, float>(
+        for_links_pipelined<8, float>(
             lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
             [&](uint32_t v, float f) {
               mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
@@ -236,13 +247,16 @@ __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const float *cin, lo
     const int ncol16 = Np / 16;
     const int c_begin = (warp >> 2) * ((ncol16 + 1) / 2) * 16;
     const int c_end = (warp >> 2) ? Np : ((ncol16 + 1) / 2) * 16;
-    for (int c0 = c_begin; c0 < c_end; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(lane_addr + (uint32_t)c0, r);
+    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+      // up to two 16-column loads in flight before one wait
+      uint32_t r[32];
+      tmem_ld16_nowait(lane_addr + (uint32_t)c0, r);
+      if (c0 + 16 < c_end) tmem_ld16_nowait(lane_addr + (uint32_t)(c0 + 16), r + 16);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
       if (valid) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < npair) G[(size_t)(c0 + j) * a.ndet + I] = __uint_as_float(r[j]);
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < c_end && c0 + j < npair) G[(size_t)(c0 + j) * a.ndet + I] = __uint_as_float(r[j]);
       }
     }
     fence_before();
