@@ -202,42 +202,23 @@ __host__ __device__ inline double rqi_refine(const double *V, double &lam, doubl
 template <int n>
 __host__ __device__ inline void ctl_eigh(const double *Ain, double *w, double *V);
 
-// Lowest two eigenpairs of a 2x2 / 3x3 symmetric V: FP32 Jacobi, then, with
-// refine, one FP64 Rayleigh-quotient-iteration step for the lowest pair.
-// Without refine the FP32 eigenvector is only normalised and its Rayleigh
-// quotient taken in FP64 (E_{t+1} accurate to the square of the vector's
-// error); the solver uses refine on every path: with FP32 step coefficients
-// the components of order 1e-7 along y and z that each step then injects slow
-// the last approach to Eq. S61 (measured: the fourth H10 state needed 147
-// H-products instead of 84).  The second pair only seeds the next state's start vector
+// Lowest two eigenpairs of a 2x2 / 3x3 symmetric V: FP32 Jacobi, then one
+// FP64 Rayleigh-quotient-iteration step for the lowest pair (E_{t+1} and the
+// step coefficients need FP64 accuracy: with FP32 coefficients, each step
+// injects components of order 1e-7 along y and z that slow the last approach
+// to Eq. S61).  The second pair only seeds the next state's start vector
 // (S1.4), whose H-image is formed from the same coefficients, so its FP32
-// accuracy is kept.  Falls back to the FP64 Jacobi solver when a refined
+// accuracy is kept.  Falls back to the FP64 Jacobi solver when the refined
 // residual is not at rounding level or the order is lost.
 template <int n>
-__host__ __device__ inline void ctl_eigh_fast(const double *V, double *w, double *U, bool refine) {
+__host__ __device__ inline void ctl_eigh_fast(const double *V, double *w, double *U) {
   float wf[3], Uf[9];
   eigh_f32<n>(V, wf, Uf);
+  double scale = 0.0;
+  for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(V[i]));
   double v[3], lam = (double)wf[0];
   for (int i = 0; i < n; ++i) v[i] = (double)Uf[i * n];
-  bool ok = true;
-  if (refine) {
-    double scale = 0.0;
-    for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(V[i]));
-    const double r = rqi_refine<n>(V, lam, v);
-    ok = r <= 1e-26 * scale * scale;
-  } else {
-    double nn = 0.0;
-    for (int i = 0; i < n; ++i) nn = fma(v[i], v[i], nn);
-    const double inv = f_rsqrt(nn);
-    for (int i = 0; i < n; ++i) v[i] *= inv;
-    double l = 0.0;
-    for (int i = 0; i < n; ++i) {
-      double t = 0.0;
-      for (int j = 0; j < n; ++j) t = fma(V[i * n + j], v[j], t);
-      l = fma(v[i], t, l);
-    }
-    lam = l;
-  }
+  const double r = rqi_refine<n>(V, lam, v);
   w[0] = lam;
   for (int i = 0; i < n; ++i) U[i * n] = v[i];
   w[1] = (double)wf[1];
@@ -246,7 +227,7 @@ __host__ __device__ inline void ctl_eigh_fast(const double *V, double *w, double
     w[2] = (double)wf[2];
     for (int i = 0; i < n; ++i) U[i * n + 2] = (double)Uf[i * n + 2];
   }
-  if (!ok || !(w[0] <= w[1])) ctl_eigh<n>(V, w, U);
+  if (!(r <= 1e-26 * scale * scale) || !(w[0] <= w[1])) ctl_eigh<n>(V, w, U);
 }
 
 template <int n>
@@ -335,7 +316,7 @@ __host__ __device__ inline void ctl_first_step(const CtlHead &s, StepOut &o) {
   V[0] = Hxx;
   V[1] = V[2] = Bx * Hxx + Bz * Hxz;
   V[3] = Bx * Bx * Hxx + Bz * Bz * Hzz + 2.0 * Bx * Bz * Hxz;
-  ctl_eigh_fast<2>(V, w, U, true);
+  ctl_eigh_fast<2>(V, w, U);
   const double vx = U[0], vz = U[2];
   o.E = w[0];
   const double den = f_recip(vx + vz * Bx);
@@ -368,7 +349,7 @@ __host__ __device__ inline void ctl_later_step(const CtlHead &s, StepOut &o) {
     V[0] = Ax * Ax * Hxx;
     V[1] = V[2] = Ax * (Bx * Hxx + By * Hxy);
     V[3] = Bx * Bx * Hxx + By * By * Hyy + 2.0 * Bx * By * Hxy;
-    ctl_eigh_fast<2>(V, w, U, true);
+    ctl_eigh_fast<2>(V, w, U);
     const double vx = U[0], vy = U[2];
     o.k = f_recip(vx * Ax + vy * Bx);
     o.b = vy * By * o.k;
@@ -394,7 +375,7 @@ __host__ __device__ inline void ctl_later_step(const CtlHead &s, StepOut &o) {
   V[5] = V[7] = Bx * hx + By * hy;                             // S44e
   V[8] = Cx * Cx * Hxx + Cy * Cy * Hyy + Cz * Cz * Hzz + 2.0 * Cx * Cy * Hxy +
          2.0 * Cx * Cz * Hxz + 2.0 * Cy * Cz * Hyz;            // S44f
-  ctl_eigh_fast<3>(V, w, U, true);
+  ctl_eigh_fast<3>(V, w, U);
   const double vx = U[0], vy = U[3], vz = U[6];
   const double iden = f_recip(vx * Ax + vy * Bx + vz * Cx);
   o.E = w[0];
