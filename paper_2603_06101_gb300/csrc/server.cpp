@@ -60,6 +60,7 @@ struct SolveSlot {
   cudaEvent_t ev = nullptr;
   bool in_flight = false;
   bool batched = false;  // advanced by the batch graph instead of its own graph
+  bool host_pending = false;  // halted: its host work runs while the next round computes
   double t_admit = 0.0;
 };
 
@@ -329,7 +330,7 @@ sbci_status launch_batch_round(sbci_server *sv) {
   t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
   for (int i = 0; i < (int)sv->slots.size(); ++i) {
     SolveSlot &sl = sv->slots[i];
-    if (!sl.used || !sl.batched || nj >= kMaxBatch) continue;
+    if (!sl.used || !sl.batched || sl.host_pending || nj >= kMaxBatch) continue;
     if (!ctx_batch_job(sl.ctx, &t.job[nj])) {
       // no longer batchable (its state fell back to FP64 sigma): own graph loop from now on
       sl.batched = false;
@@ -388,9 +389,19 @@ sbci_status progress_batch(sbci_server *sv) {
       set_error("a bounded device wait ran out (batched tensor-core kernel)");
       return SBCI_ERR_TIMEOUT;
     }
-    for (int j = 0; j < (int)sv->batch_slots.size(); ++j) {
-      if (!sv->h_table->halted[j]) continue;  // still running: stays in the next round as is
-      SolveSlot &sl = sv->slots[sv->batch_slots[j]];
+    // the halted solves sit out one round: the round of the others is launched
+    // first, and their host work (FP64 re-syncs, verification, next state)
+    // runs on their own streams while it computes
+    std::vector<int> halted;
+    for (int j = 0; j < (int)sv->batch_slots.size(); ++j)
+      if (sv->h_table->halted[j]) {
+        halted.push_back(sv->batch_slots[j]);
+        sv->slots[sv->batch_slots[j]].host_pending = true;
+      }
+    sbci_status lst = launch_batch_round(sv);
+    for (int i : halted) {
+      SolveSlot &sl = sv->slots[i];
+      sl.host_pending = false;
       int done = 0;
       const sbci_status st = solve_round_finish(sl.ctx, &done, false);
       if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
@@ -399,6 +410,9 @@ sbci_status progress_batch(sbci_server *sv) {
       }
       if (done) retire(sv, sl, SBCI_OK);
     }
+    if (lst != SBCI_OK) return lst;
+    if (!sv->batch_in_flight) return launch_batch_round(sv);  // every solve had halted
+    return SBCI_OK;
   }
   return launch_batch_round(sv);
 }
