@@ -56,6 +56,8 @@ def parse():
                     help="H10 solves per step, solved together by the batched persistent kernels "
                          "(1: one solve per step through its own graph loop)")
     ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--davidson", action="store_true",
+                    help="SBCI1 vs block Davidson-Liu on the same FP64 sigma: time, H-products, memory")
     return ap.parse_args()
 
 
@@ -465,6 +467,68 @@ def run_ncu_solve(args):
                       "sigma": sum(r.n_sigma for r in R)}))
 
 
+def run_davidson(args):
+    """The paper's comparison (Fig. 4, Tables S2-S19: time, steps and memory of
+    SBCI vs the Davidson method) on the bench workload, one GPU: SBCI1 with FP64
+    and with TF32x3 sigma against block Davidson-Liu with FP64 sigma at two
+    subspace limits.  Times are host wall-clock per solve (best of --reps after
+    one warm-up solve); the vectors are the device buffers each solver holds."""
+    import torch
+
+    from paper_2603_06101_gb300 import sbci
+
+    I = workload()
+    ctx = sbci.Context.from_integrals(I)
+    ndet = ctx.ndet
+    k = NSTATES
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best, out = None, None
+        for _ in range(max(1, args.reps)):
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best, out
+
+    rows = {}
+    for name, prec in [("sbci1_fp64", sbci.SBCI_FP64), ("sbci1_tf32x3", sbci.SBCI_TF32X3)]:
+        p = sbci.params(sector=1, prec=prec)
+        dt, (E, _, R, st) = timed(lambda: ctx.solve(k, p))
+        # x, X, y, Y, w, z[2], Z[2], the k stored states and the preconditioner:
+        # 10 + k FP64 vectors, plus the FP32 copy of z in the split mode
+        nb = (10 + k) * 8 * ndet + (4 * ndet if prec != sbci.SBCI_FP64 else 0)
+        rows[name] = {"ms_per_solve": 1e3 * dt, "status": st, "energies": [float(e) for e in E],
+                      "sigma_per_solve": int(sum(r.n_sigma for r in R)),
+                      "fp64_sigma_per_solve": int(sum(r.n_sigma_fp64 for r in R)),
+                      "steps": int(sum(r.n_step for r in R)), "vector_bytes": int(nb)}
+    for ms in (0, 40):
+        p = sbci.params(sector=1)
+        dt, (E, _, R, st, nb) = timed(lambda: ctx.davidson(k, p, max_space=ms))
+        rows[f"davidson_max_space_{ms or max(12, 4 * k)}"] = {
+            "ms_per_solve": 1e3 * dt, "status": st, "energies": [float(e) for e in E],
+            "sigma_per_solve": int(R[0].n_sigma), "iterations": int(R[0].n_step),
+            "collapses": int(R[0].n_restart[0]), "vector_bytes": int(nb)}
+    # kernel families of one solve each (launch counts and CUDA-event time)
+    kernels = {}
+    for name, fn in [("sbci1_fp64", lambda: ctx.solve(k, sbci.params(sector=1))),
+                     ("davidson_max_space_16", lambda: ctx.davidson(k, sbci.params(sector=1)))]:
+        ctx.profile(True)
+        fn()
+        torch.cuda.synchronize()
+        kernels[name] = {f: {"launches": n, "ms": round(ms, 3)} for f, (n, ms) in ctx.profile_read().items() if n}
+        ctx.profile(False)
+    ref = np.array(rows["sbci1_fp64"]["energies"])
+    for r in rows.values():
+        r["max_energy_diff_vs_sbci1_fp64"] = float(np.abs(np.array(r["energies"]) - ref).max())
+    print(json.dumps({"comparison": "SBCI1 vs block Davidson-Liu (same FP64 sigma, same thresholds)",
+                      "workload": WORKLOAD, "states": k, "ndet": int(ndet), "rows": rows,
+                      "kernels_one_solve": kernels}))
+
+
 def run_serving(args):
     """Serving stream over H6/H8/H10/H12 chains (1-4 states, spacing 0.7-3.0 A).
 
@@ -573,6 +637,9 @@ def main():
     args = parse()
     if args.serving:
         run_serving(args)
+        return
+    if args.davidson:
+        run_davidson(args)
         return
     if args.sigma_only:
         sigma_only(args)

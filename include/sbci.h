@@ -215,6 +215,38 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
 sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
                              sbci_report *rep, long long *launches);
 
+/* Lowest k eigenpairs by block Davidson-Liu (Davidson 1975; Liu 1978) on the
+ * same FP64 sigma: the method the paper compares SBCI with (Introduction;
+ * Materials and Methods, where it runs with the preconditioner
+ * (D - E^0 I)^-1).  It keeps the whole subspace V and H V (up to max_space
+ * vectors each) where SBCI1 keeps x, y, z and their H-images.  Schedule:
+ *   start: determinants by ascending (D_I, I), symmetrised when
+ *     params->sector = 1, Gram-Schmidt orthonormalised (dropped below gs_tol),
+ *     until max(k, n_init or 2) vectors;
+ *   each iteration: Ritz pairs of (T + T^T)/2, T = V^T H V; residuals
+ *     r_a = H x_a - theta_a x_a; state a has converged when
+ *     |theta_a - theta_a(previous iteration)| < eps0 and |r_a| < r0 (Eq. S61);
+ *   when m + (unconverged states) > max_space, V and H V collapse onto the
+ *     k Ritz vectors;
+ *   per unconverged state, in order: t = r_a / (D - theta_a) (|D_I - theta_a| <
+ *     guard -> sign * guard), symmetrised in the sector, projected twice against
+ *     V, dropped if |t|^2 < gs_tol |t_0|^2, normalised, appended (one sigma);
+ *   an iteration that appends nothing ends the solve (converged if every
+ *     |r_a| < r0); so does the cap of max_sigma * k H-products.
+ * params: NULL for defaults; eps0, r0, guard, gs_tol, sector, n_init and
+ *   max_sigma are used, the other fields ignored (sigma is always FP64).
+ * max_space: subspace limit, 0 -> max(12, 4k); 2k <= max_space <= 64.
+ * k: 1..8.  energies: host [k] totals.  vecs: host [k*Ndet] Ritz vectors or
+ * NULL.  rep: host [k] or NULL -- residual |r_a|, converged, n_sigma (total
+ * H-products of the solve), n_step (iterations), n_restart[0] (collapses).
+ * vector_bytes (nullable): device bytes of the subspace buffers
+ * (2 (max_space + k) Ndet doubles), allocated for the call and freed before
+ * it returns.  Returns SBCI_ERR_NOT_CONVERGED when it stops short (results
+ * written), SBCI_ERR_INVALID for bad arguments or fewer than k start vectors,
+ * SBCI_ERR_NOMEM when the buffers do not fit. */
+sbci_status sbci_davidson(sbci_ctx *ctx, int k, const sbci_params *params, int max_space,
+                          double *energies, double *vecs, sbci_report *rep, long long *vector_bytes);
+
 /* Copies up to cap trace records of the last solve; *n = records available. */
 sbci_status sbci_trace(const sbci_ctx *ctx, sbci_trace_record *buf, int cap, int *n);
 

@@ -57,10 +57,12 @@ namespace {
 
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
-enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF, K_COUNT };
+enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
+           K_DAVD, K_DAVC, K_DAVP, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
-                                       "sigma_gather_contract_tc", "sigma_symfinish"};
+                                       "sigma_gather_contract_tc", "sigma_symfinish",
+                                       "davidson_dots", "davidson_combine", "davidson_precond"};
 
 struct Prof {
   bool on = false;
@@ -805,6 +807,367 @@ sbci_status init_from_vector(sbci_ctx *c, const double *c0, double *E0) {
   return SBCI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Block Davidson-Liu (Davidson 1975; Liu 1978) on the same FP64 sigma: the
+// method the paper compares SBCI with (Introduction; Materials and Methods:
+// PySCF's Davidson with the preconditioner (D - E^0 I)^-1).  The paper does
+// not state its schedule; this one is fixed as follows:
+//  D1 start: determinants by ascending (D_I, I), symmetrised in the sector,
+//     Gram-Schmidt orthonormalised (dropped below gs_tol), until
+//     max(k, n_init or 2) vectors; one H-product each;
+//  D2 subspace matrix (T + T^T)/2, T = V^T (H V); Ritz values theta_a and
+//     residuals r_a = (H V) s_a - theta_a V s_a;
+//  D3 converged when |theta_a - previous theta_a| < eps0 and |r_a| < r0 for
+//     every a (the thresholds of Eq. S61);
+//  D4 collapse onto the k Ritz vectors (and their H-images) when the
+//     corrections would overflow max_space;
+//  D5 per unconverged a: t = r_a / guarded(D - theta_a), symmetrised in the
+//     sector, projected twice against V, dropped if |t|^2 < gs_tol |t_0|^2,
+//     normalised, appended, one H-product;
+//  D6 an iteration that adds no vector (all dropped, or the H-product cap
+//     max_sigma * k reached) ends the solve, converged if every |r_a| < r0.
+// The subspace lives in a pool of slot buffers (vector, H-image); the k
+// residuals take free slots and become the appended corrections in place.
+
+struct DavSolve {
+  sbci_ctx *c = nullptr;
+  std::vector<double *> vb, ab;  // slot buffers: subspace vector, its H-image
+  std::vector<int> V;            // the subspace, as slots in order
+  std::vector<int> free_slots;
+  double *partials = nullptr, *d_res = nullptr, *h_res = nullptr;
+  int grid = 1;
+  ~DavSolve() {
+    for (double *p : vb)
+      if (p) cudaFree(p);
+    for (double *p : ab)
+      if (p) cudaFree(p);
+    if (partials) cudaFree(partials);
+    if (d_res) cudaFree(d_res);
+    if (h_res) cudaFreeHost(h_res);
+  }
+  int take() {
+    const int sl = free_slots.back();
+    free_slots.pop_back();
+    return sl;
+  }
+};
+
+sbci_status dav_dots(DavSolve &d, const std::vector<const double *> &u, const std::vector<const double *> &v,
+                     std::vector<double> &out) {
+  sbci_ctx *c = d.c;
+  out.assign(u.size(), 0.0);
+  for (size_t p0 = 0; p0 < u.size(); p0 += kDavMaxPairs) {
+    const int np = (int)std::min<size_t>(kDavMaxPairs, u.size() - p0);
+    RET(timed(c, K_DAVD, [&] {
+      return launch_dav_dots(u.data() + p0, v.data() + p0, np, c->ndet, d.partials, d.grid, c->stream);
+    }));
+    RET(timed(c, K_RED, [&] { return launch_reduce(d.partials, d.grid, 0, np, d.d_res, c->stream); }));
+    CK(cudaMemcpyAsync(d.h_res, d.d_res, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < np; ++p) {
+      if (!std::isfinite(d.h_res[p])) {
+        set_error("non-finite dot product in a device reduction (Davidson)");
+        return SBCI_ERR_NUMERIC;
+      }
+      out[p0 + p] = d.h_res[p];
+    }
+  }
+  return SBCI_OK;
+}
+
+// out_j = sum_q coef[q * nout + j] in_q (an output may be one of the inputs)
+sbci_status dav_combine(DavSolve &d, const std::vector<double *> &out, const std::vector<const double *> &in,
+                        const std::vector<double> &coef) {
+  sbci_ctx *c = d.c;
+  return timed(c, K_DAVC, [&] {
+    return launch_dav_combine(out.data(), (int)out.size(), in.data(), (int)in.size(), coef.data(), c->ndet,
+                              c->nsm, c->stream);
+  });
+}
+
+// T[i][j] = V_i . (H V)_j for all i, j < m (row stride kDavMaxSpace)
+sbci_status dav_full_T(DavSolve &d, std::vector<double> &T) {
+  const int m = (int)d.V.size();
+  std::vector<const double *> u, v;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      u.push_back(d.vb[d.V[i]]);
+      v.push_back(d.ab[d.V[j]]);
+    }
+  std::vector<double> r;
+  RET(dav_dots(d, u, v, r));
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) T[(size_t)i * kDavMaxSpace + j] = r[(size_t)i * m + j];
+  return SBCI_OK;
+}
+
+sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space, double *energies, double *vecs,
+                         sbci_report *rep, long long *vector_bytes) {
+  const long long N = c->ndet;
+  // D1: start vectors
+  const int n_v = std::max(k, p.n_init > 0 ? p.n_init : 2);
+  std::vector<double> D(N);
+  CK(cudaMemcpyAsync(D.data(), c->d_diag, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  typedef std::pair<double, long long> Key;
+  typedef std::map<long long, double> Sparse;
+  std::vector<Sparse> basis;
+  long long ncand = std::min<long long>(N, 2LL * n_v + 2);
+  for (;;) {
+    std::priority_queue<Key> heap;  // the ncand smallest (D_I, I)
+    for (long long i = 0; i < N; ++i) {
+      const Key kk(D[i], i);
+      if ((long long)heap.size() < ncand) heap.push(kk);
+      else if (kk < heap.top()) {
+        heap.pop();
+        heap.push(kk);
+      }
+    }
+    std::vector<Key> sel;
+    while (!heap.empty()) {
+      sel.push_back(heap.top());
+      heap.pop();
+    }
+    std::sort(sel.begin(), sel.end());
+    basis.clear();
+    for (const Key &kk : sel) {
+      if ((int)basis.size() >= n_v) break;
+      Sparse e;
+      const long long I = kk.second;
+      if (p.sector) {
+        const long long ia = I / c->Nb, ib = I % c->Nb;
+        e[I] += 0.5;
+        e[ib * c->Nb + ia] += 0.5;
+      } else {
+        e[I] = 1.0;
+      }
+      for (const Sparse &b : basis) {
+        double ov = 0.0;
+        for (auto &kv : e) {
+          auto it = b.find(kv.first);
+          if (it != b.end()) ov += it->second * kv.second;
+        }
+        for (auto &kv : b) e[kv.first] -= ov * kv.second;
+      }
+      double nrm = 0.0;
+      for (auto &kv : e) nrm += kv.second * kv.second;
+      nrm = std::sqrt(nrm);
+      if (nrm < p.gs_tol) continue;
+      for (auto &kv : e) kv.second /= nrm;
+      basis.push_back(e);
+    }
+    if ((int)basis.size() >= n_v || ncand >= N) break;
+    ncand = std::min(N, 2 * ncand);
+  }
+  if ((int)basis.size() < k) {
+    set_error("sbci_davidson: the space holds fewer than k start vectors");
+    return SBCI_ERR_INVALID;
+  }
+  // slot pool: the subspace plus the k residuals / corrections
+  DavSolve d;
+  d.c = c;
+  const int cap = max_space + k;
+  d.vb.assign(cap, nullptr);
+  d.ab.assign(cap, nullptr);
+  for (int sl = 0; sl < cap; ++sl) {
+    RET(dmalloc(&d.vb[sl], (size_t)N));
+    RET(dmalloc(&d.ab[sl], (size_t)N));
+  }
+  for (int sl = cap - 1; sl >= 0; --sl) d.free_slots.push_back(sl);
+  d.grid = dav_dots_grid(N, c->nsm);
+  RET(dmalloc(&d.partials, (size_t)kDavMaxPairs * d.grid));
+  RET(dmalloc(&d.d_res, (size_t)kDavMaxPairs));
+  CK(cudaMallocHost((void **)&d.h_res, sizeof(double) * kDavMaxPairs));
+  if (vector_bytes) *vector_bytes = 2LL * cap * N * (long long)sizeof(double);
+  for (const Sparse &b : basis) {
+    const int sl = d.take();
+    CK(cudaMemsetAsync(d.vb[sl], 0, sizeof(double) * N, c->stream));
+    for (auto &kv : b)
+      CK(cudaMemcpyAsync(d.vb[sl] + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    d.V.push_back(sl);
+  }
+  const long long max_sigma = (long long)p.max_sigma * k;
+  long long n_sigma = 0;
+  for (int sl : d.V) {
+    RET(run_sigma(c, d.vb[sl], d.ab[sl], SBCI_FP64));
+    ++n_sigma;
+  }
+  std::vector<double> T((size_t)kDavMaxSpace * kDavMaxSpace, 0.0);
+  RET(dav_full_T(d, T));
+  std::vector<double> theta(k), theta_prev(k), rn(k), S, r;
+  std::vector<int> R(k, -1);
+  bool have_prev = false, converged = false;
+  int n_iter = 0, n_collapse = 0;
+  for (;;) {
+    ++n_iter;
+    int m = (int)d.V.size();
+    // D2: Ritz pairs of the symmetrised subspace matrix
+    std::vector<double> A((size_t)m * m), w(m), U((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        A[(size_t)i * m + j] = 0.5 * (T[(size_t)i * kDavMaxSpace + j] + T[(size_t)j * kDavMaxSpace + i]);
+    jacobi_eigh(m, A.data(), w.data(), U.data());
+    S.assign((size_t)m * k, 0.0);  // S[i * k + a]
+    for (int a = 0; a < k; ++a) {
+      theta[a] = w[a];
+      for (int i = 0; i < m; ++i) S[(size_t)i * k + a] = U[(size_t)i * m + a];
+    }
+    // residuals r_a = (H V) s_a - theta_a V s_a, in free slots
+    std::vector<double *> Rout(k);
+    for (int a = 0; a < k; ++a) {
+      R[a] = d.take();
+      Rout[a] = d.vb[R[a]];
+    }
+    {
+      std::vector<const double *> in;
+      for (int i = 0; i < m; ++i) in.push_back(d.ab[d.V[i]]);
+      RET(dav_combine(d, Rout, in, S));
+      std::vector<const double *> in2;
+      std::vector<double> co((size_t)(k + m) * k, 0.0);
+      for (int a = 0; a < k; ++a) {
+        in2.push_back(Rout[a]);
+        co[(size_t)a * k + a] = 1.0;
+      }
+      for (int i = 0; i < m; ++i) {
+        in2.push_back(d.vb[d.V[i]]);
+        for (int a = 0; a < k; ++a) co[(size_t)(k + i) * k + a] = -theta[a] * S[(size_t)i * k + a];
+      }
+      RET(dav_combine(d, Rout, in2, co));
+      std::vector<const double *> u(Rout.begin(), Rout.end());
+      RET(dav_dots(d, u, u, r));
+      for (int a = 0; a < k; ++a) rn[a] = std::sqrt(r[a]);
+    }
+    // D3
+    std::vector<int> unconv;
+    for (int a = 0; a < k; ++a) {
+      const bool ok = have_prev && std::fabs(theta[a] - theta_prev[a]) < p.eps0 && rn[a] < p.r0;
+      if (!ok) unconv.push_back(a);
+    }
+    if (unconv.empty()) {
+      converged = true;
+      break;
+    }
+    theta_prev = theta;
+    have_prev = true;
+    // D4: collapse in place onto the k Ritz vectors
+    if (m + (int)unconv.size() > max_space) {
+      std::vector<double *> outv, outa;
+      std::vector<const double *> inv, ina;
+      for (int a = 0; a < k; ++a) {
+        outv.push_back(d.vb[d.V[a]]);
+        outa.push_back(d.ab[d.V[a]]);
+      }
+      for (int i = 0; i < m; ++i) {
+        inv.push_back(d.vb[d.V[i]]);
+        ina.push_back(d.ab[d.V[i]]);
+      }
+      RET(dav_combine(d, outv, inv, S));
+      RET(dav_combine(d, outa, ina, S));
+      for (int i = k; i < m; ++i) d.free_slots.push_back(d.V[i]);
+      d.V.resize(k);
+      m = k;
+      S.assign((size_t)k * k, 0.0);
+      for (int a = 0; a < k; ++a) S[(size_t)a * k + a] = 1.0;
+      RET(dav_full_T(d, T));
+      ++n_collapse;
+    }
+    // D5: corrections, one at a time against the growing subspace
+    int added = 0;
+    for (int a : unconv) {
+      if (n_sigma >= max_sigma) break;
+      const int ts = R[a];
+      double *t = d.vb[ts];
+      RET(timed(c, K_DAVP, [&] { return launch_dav_precond(t, c->d_diag, theta[a], p.guard, N, c->nsm, c->stream); }));
+      if (p.sector) RET(timed(c, K_DAVP, [&] { return launch_symmetrize(t, c->Na, c->stream); }));
+      RET(dav_dots(d, {t}, {t}, r));
+      const double n0 = r[0];
+      for (int pass = 0; pass < 2; ++pass) {
+        std::vector<const double *> u, v, in{t};
+        for (int i = 0; i < m; ++i) {
+          u.push_back(d.vb[d.V[i]]);
+          v.push_back(t);
+          in.push_back(d.vb[d.V[i]]);
+        }
+        RET(dav_dots(d, u, v, r));
+        std::vector<double> co(1 + m);
+        co[0] = 1.0;
+        for (int i = 0; i < m; ++i) co[1 + i] = -r[i];
+        RET(dav_combine(d, {t}, in, co));
+      }
+      RET(dav_dots(d, {t}, {t}, r));
+      const double nt = r[0];
+      if (!(nt > 0.0 && nt >= p.gs_tol * n0)) continue;
+      RET(dav_combine(d, {t}, {t}, {1.0 / std::sqrt(nt)}));
+      RET(run_sigma(c, t, d.ab[ts], SBCI_FP64));
+      ++n_sigma;
+      d.V.push_back(ts);
+      R[a] = -1;
+      ++m;
+      ++added;
+      // new row and column of T
+      const int j = m - 1;
+      std::vector<const double *> u, v;
+      for (int i = 0; i <= j; ++i) {
+        u.push_back(d.vb[d.V[i]]);
+        v.push_back(d.ab[ts]);
+      }
+      for (int i = 0; i < j; ++i) {
+        u.push_back(t);
+        v.push_back(d.ab[d.V[i]]);
+      }
+      RET(dav_dots(d, u, v, r));
+      for (int i = 0; i <= j; ++i) T[(size_t)i * kDavMaxSpace + j] = r[i];
+      for (int i = 0; i < j; ++i) T[(size_t)j * kDavMaxSpace + i] = r[j + 1 + i];
+    }
+    for (int a = 0; a < k; ++a)
+      if (R[a] >= 0) {
+        d.free_slots.push_back(R[a]);
+        R[a] = -1;
+      }
+    if (added == 0) {  // D6
+      converged = true;
+      for (int a = 0; a < k; ++a) converged = converged && rn[a] < p.r0;
+      break;
+    }
+  }
+  // results: Ritz vectors V s_a (the residual slots are no longer needed)
+  for (int a = 0; a < k; ++a)
+    if (R[a] >= 0) {
+      d.free_slots.push_back(R[a]);
+      R[a] = -1;
+    }
+  if (vecs) {
+    const int m = (int)d.V.size();
+    std::vector<double *> out;
+    std::vector<const double *> in;
+    for (int a = 0; a < k; ++a) out.push_back(d.vb[d.take()]);
+    for (int i = 0; i < m; ++i) in.push_back(d.vb[d.V[i]]);
+    RET(dav_combine(d, out, in, S));
+    for (int a = 0; a < k; ++a)
+      CK(cudaMemcpyAsync(vecs + (size_t)a * N, out[a], sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  for (int a = 0; a < k; ++a) {
+    energies[a] = theta[a] + c->e_core;
+    if (rep) {
+      sbci_report &o = rep[a];
+      o = sbci_report{};
+      o.energy = energies[a];
+      o.residual = rn[a];
+      o.converged = converged ? 1 : 0;
+      o.n_sigma = (int)n_sigma;
+      o.n_sigma_fp64 = (int)n_sigma;
+      o.n_step = n_iter;
+      o.n_restart[0] = n_collapse;
+    }
+  }
+  if (!converged) {
+    set_error("sbci_davidson: stopped before every state converged");
+    return SBCI_ERR_NOT_CONVERGED;
+  }
+  return SBCI_OK;
+}
+
 }  // namespace
 
 // Asynchronous rounds of a solve, for the serving layer: launch the graph loop
@@ -1323,6 +1686,32 @@ sbci_status sbci_solve(sbci_ctx *c, int k, const sbci_params *params, const doub
     if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
   }
   return sbci_finish(c, energies, vecs, rep);
+}
+
+sbci_status sbci_davidson(sbci_ctx *c, int k, const sbci_params *params, int max_space, double *energies,
+                          double *vecs, sbci_report *rep, long long *vector_bytes) {
+  if (!c || k < 1 || k > kDavMaxOut || !energies) {
+    set_error("sbci_davidson: need a context, 1 <= k <= 8 and energies");
+    return SBCI_ERR_INVALID;
+  }
+  sbci_params p;
+  if (params) p = *params;
+  else sbci_params_init(&p);
+  if (max_space == 0) max_space = std::max(12, 4 * k);
+  if (max_space < 2 * k || max_space > kDavMaxSpace) {
+    set_error("sbci_davidson: need 2k <= max_space <= 64");
+    return SBCI_ERR_INVALID;
+  }
+  if (p.sector && c->ne_a != c->ne_b) {
+    set_error("sector = 1 needs nalpha == nbeta");
+    return SBCI_ERR_INVALID;
+  }
+  if ((long long)k > c->ndet) {
+    set_error("sbci_davidson: more states than determinants");
+    return SBCI_ERR_INVALID;
+  }
+  RET(ensure_G(c, SBCI_FP64));
+  return davidson_run(c, k, p, max_space, energies, vecs, rep, vector_bytes);
 }
 
 sbci_status sbci_trace(const sbci_ctx *c, sbci_trace_record *buf, int cap, int *n) {

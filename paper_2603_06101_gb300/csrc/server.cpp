@@ -502,13 +502,18 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
   }
   unsigned long long bodies = 0;
   sbci_status worst = SBCI_OK;
+  // a solve that halted sits out the next round: that round is launched first
+  // and the solve's host work (FP64 re-syncs, verification, next state) runs on
+  // its own stream while the others compute
+  std::vector<int> pending;
+  std::vector<char> is_pending(n, 0);
   for (;;) {
     BatchTable &t = *eng.h_table;
     std::vector<int> row;
     int nj = 0;
     t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
     for (int i = 0; i < n; ++i) {
-      if (done[i]) continue;
+      if (done[i] || is_pending[i]) continue;
       if (!ctx_batch_job(ctx[i], &t.job[nj])) {  // not batchable: solve it on its own
         double *E = energies + (size_t)i * k;
         sbci_status st = SBCI_OK;
@@ -530,24 +535,45 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       row.push_back(i);
       ++nj;
     }
-    if (nj == 0) break;
+    if (nj == 0 && pending.empty()) break;
     t.njobs = nj;
     t.tc_next = 0;
     t.bodies = 0;
     int status = 0;
     unsigned long long round_bodies = 0;
-    if (cudaMemcpyAsync(eng.d_table, eng.h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, eng.stream) !=
-            cudaSuccess ||
-        engine_round(eng) != cudaSuccess ||
-        cudaMemcpyAsync(t.halted, eng.d_table->halted, sizeof(int) * kMaxBatch, cudaMemcpyDeviceToHost,
-                        eng.stream) != cudaSuccess ||
-        cudaMemcpyAsync(&status, eng.d_status, sizeof(int), cudaMemcpyDeviceToHost, eng.stream) != cudaSuccess ||
-        cudaMemcpyAsync(&round_bodies, &eng.d_table->bodies, sizeof(round_bodies), cudaMemcpyDeviceToHost,
-                        eng.stream) != cudaSuccess ||
-        cudaStreamSynchronize(eng.stream) != cudaSuccess) {
+    if (nj > 0 &&
+        (cudaMemcpyAsync(eng.d_table, eng.h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, eng.stream) !=
+             cudaSuccess ||
+         engine_round(eng) != cudaSuccess ||
+         cudaMemcpyAsync(t.halted, eng.d_table->halted, sizeof(int) * kMaxBatch, cudaMemcpyDeviceToHost,
+                         eng.stream) != cudaSuccess ||
+         cudaMemcpyAsync(&status, eng.d_status, sizeof(int), cudaMemcpyDeviceToHost, eng.stream) != cudaSuccess ||
+         cudaMemcpyAsync(&round_bodies, &eng.d_table->bodies, sizeof(round_bodies), cudaMemcpyDeviceToHost,
+                         eng.stream) != cudaSuccess)) {
+      cudaStreamSynchronize(eng.stream);
       set_error("sbci_solve_batch: batch round failed");
       return SBCI_ERR_CUDA;
     }
+    sbci_status host_st = SBCI_OK;
+    for (int i : pending) {
+      is_pending[i] = 0;
+      if (host_st != SBCI_OK) continue;
+      const sbci_status st = solve_round_finish(ctx[i], &done[i], false);
+      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
+        host_st = st;
+        continue;
+      }
+      if (done[i]) {
+        const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
+        if (fs != SBCI_OK) worst = fs;
+      }
+    }
+    pending.clear();
+    if (nj > 0 && cudaStreamSynchronize(eng.stream) != cudaSuccess) {
+      set_error("sbci_solve_batch: batch round failed");
+      return SBCI_ERR_CUDA;
+    }
+    if (host_st != SBCI_OK) return host_st;
     bodies += round_bodies;
     if (status) {
       set_error("a bounded device wait ran out (batched tensor-core kernel)");
@@ -555,13 +581,8 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     }
     for (int j = 0; j < nj; ++j) {
       if (!t.halted[j]) continue;
-      const int i = row[j];
-      const sbci_status st = solve_round_finish(ctx[i], &done[i], false);
-      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
-      if (done[i]) {
-        const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
-        if (fs != SBCI_OK) worst = fs;
-      }
+      pending.push_back(row[j]);
+      is_pending[row[j]] = 1;
     }
   }
   if (launches) {

@@ -8,6 +8,7 @@
 // for l occupied (ascending) and k unoccupied or k == l (ascending).
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "sbci_internal.h"
 
@@ -83,8 +84,7 @@ void build_strings(int norb, int nelec, StringSet &out) {
 }
 
 void jacobi_eigh(int n, const double *Ain, double *w, double *V) {
-  double A[64];
-  std::memcpy(A, Ain, sizeof(double) * n * n);
+  std::vector<double> A(Ain, Ain + (size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 100; ++sweep) {
