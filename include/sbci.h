@@ -215,6 +215,29 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
 sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
                              sbci_report *rep, long long *launches);
 
+/* SBCI2 (Algorithm 2, Sections S2.1-S2.5, Fig. 1B): the k lowest states,
+ * found one by one from the lowest while the pair (alpha, alpha+1) is updated
+ * together (two H-products per step, a 6x6 canonically orthogonalised
+ * subspace, coefficients of Eqs. S93, S112, S116, S117, S121, restarts S130a-c
+ * and max_cycle2); the highest state runs SBCI1.  FP64 sigma.  Readings where
+ * the paper is silent: start vectors from max(k, n_init or 2) lowest-diagonal
+ * vectors (S74-S76); a later pair's upper start is projected against the
+ * stored states and the new lower vector, normalised, with X_0 = H x_0 by one
+ * H-product and E_0 its Rayleigh quotient; the preconditioner shift is E_t of
+ * state 0 in the ground pair, E_c^0 afterwards; x_{t+1} and X_{t+1} are taken
+ * as k v and its H-image (the vectors Eqs. S124-S125 give in exact arithmetic);
+ * undefined later-step coefficients take the first-step path; a restart keeps
+ * x/|x|, X/|x| and takes the first-step path.
+ * params: NULL for defaults; needs prec = SBCI_FP64, init = 0, start_noise = 0
+ * (else SBCI_ERR_INVALID).  max_cycle2: restart period of the pairs, 0 -> 10
+ * (Section S2.5); params->max_cycle applies to the last state.  Energies are
+ * in the order the states were found (the pair's lower state first); rep as
+ * sbci_solve (per state: H-products and steps while it was the lower state);
+ * sbci_trace gives the step records of the pairs (b, c, k: b^{aa}, c^{aa},
+ * k_0) followed by the last state's. */
+sbci_status sbci_solve_sbci2(sbci_ctx *ctx, int k, const sbci_params *params, int max_cycle2,
+                             double *energies, double *vecs, sbci_report *rep);
+
 /* Lowest k eigenpairs by block Davidson-Liu (Davidson 1975; Liu 1978) on the
  * same FP64 sigma: the method the paper compares SBCI with (Introduction;
  * Materials and Methods, where it runs with the preconditioner

@@ -829,21 +829,38 @@ sbci_status init_from_vector(sbci_ctx *c, const double *c0, double *E0) {
 // The subspace lives in a pool of slot buffers (vector, H-image); the k
 // residuals take free slots and become the appended corrections in place.
 
-struct DavSolve {
+// Block dot products and linear combinations of whole vectors for the
+// host-driven solvers (Davidson-Liu, SBCI2): reduction scratch and a pinned
+// result buffer.
+struct VecScratch {
   sbci_ctx *c = nullptr;
+  double *partials = nullptr, *d_res = nullptr, *h_res = nullptr;
+  int grid = 1;
+  ~VecScratch() {
+    if (partials) cudaFree(partials);
+    if (d_res) cudaFree(d_res);
+    if (h_res) cudaFreeHost(h_res);
+  }
+};
+
+sbci_status scratch_init(VecScratch &d, sbci_ctx *c) {
+  d.c = c;
+  d.grid = dav_dots_grid(c->ndet, c->nsm);
+  RET(dmalloc(&d.partials, (size_t)kDavMaxPairs * d.grid));
+  RET(dmalloc(&d.d_res, (size_t)kDavMaxPairs));
+  CK(cudaMallocHost((void **)&d.h_res, sizeof(double) * kDavMaxPairs));
+  return SBCI_OK;
+}
+
+struct DavSolve : VecScratch {
   std::vector<double *> vb, ab;  // slot buffers: subspace vector, its H-image
   std::vector<int> V;            // the subspace, as slots in order
   std::vector<int> free_slots;
-  double *partials = nullptr, *d_res = nullptr, *h_res = nullptr;
-  int grid = 1;
   ~DavSolve() {
     for (double *p : vb)
       if (p) cudaFree(p);
     for (double *p : ab)
       if (p) cudaFree(p);
-    if (partials) cudaFree(partials);
-    if (d_res) cudaFree(d_res);
-    if (h_res) cudaFreeHost(h_res);
   }
   int take() {
     const int sl = free_slots.back();
@@ -852,7 +869,7 @@ struct DavSolve {
   }
 };
 
-sbci_status dav_dots(DavSolve &d, const std::vector<const double *> &u, const std::vector<const double *> &v,
+sbci_status dav_dots(VecScratch &d, const std::vector<const double *> &u, const std::vector<const double *> &v,
                      std::vector<double> &out) {
   sbci_ctx *c = d.c;
   out.assign(u.size(), 0.0);
@@ -876,7 +893,7 @@ sbci_status dav_dots(DavSolve &d, const std::vector<const double *> &u, const st
 }
 
 // out_j = sum_q coef[q * nout + j] in_q (an output may be one of the inputs)
-sbci_status dav_combine(DavSolve &d, const std::vector<double *> &out, const std::vector<const double *> &in,
+sbci_status dav_combine(VecScratch &d, const std::vector<double *> &out, const std::vector<const double *> &in,
                         const std::vector<double> &coef) {
   sbci_ctx *c = d.c;
   return timed(c, K_DAVC, [&] {
@@ -901,17 +918,18 @@ sbci_status dav_full_T(DavSolve &d, std::vector<double> &T) {
   return SBCI_OK;
 }
 
-sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space, double *energies, double *vecs,
-                         sbci_report *rep, long long *vector_bytes) {
+typedef std::map<long long, double> Sparse;
+
+// Start vectors of the host-driven solvers (Davidson D1, SBCI2 Q1):
+// determinants by ascending (D_I, I), symmetrised in the sector (c = c^T),
+// Gram-Schmidt orthonormalised (dropped below gs_tol), until n_v vectors hold
+// or the space is exhausted.
+sbci_status lowest_diagonal_basis(sbci_ctx *c, int n_v, const sbci_params &p, std::vector<Sparse> &basis) {
   const long long N = c->ndet;
-  // D1: start vectors
-  const int n_v = std::max(k, p.n_init > 0 ? p.n_init : 2);
   std::vector<double> D(N);
   CK(cudaMemcpyAsync(D.data(), c->d_diag, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   typedef std::pair<double, long long> Key;
-  typedef std::map<long long, double> Sparse;
-  std::vector<Sparse> basis;
   long long ncand = std::min<long long>(N, 2LL * n_v + 2);
   for (;;) {
     std::priority_queue<Key> heap;  // the ncand smallest (D_I, I)
@@ -959,13 +977,31 @@ sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space
     if ((int)basis.size() >= n_v || ncand >= N) break;
     ncand = std::min(N, 2 * ncand);
   }
+  return SBCI_OK;
+}
+
+// dense copy of a sparse vector into a device buffer
+sbci_status upload_sparse(sbci_ctx *c, const Sparse &b, double *dst) {
+  CK(cudaMemsetAsync(dst, 0, sizeof(double) * c->ndet, c->stream));
+  for (auto &kv : b)
+    CK(cudaMemcpyAsync(dst + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return SBCI_OK;
+}
+
+sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space, double *energies, double *vecs,
+                         sbci_report *rep, long long *vector_bytes) {
+  const long long N = c->ndet;
+  // D1: start vectors
+  const int n_v = std::max(k, p.n_init > 0 ? p.n_init : 2);
+  std::vector<Sparse> basis;
+  RET(lowest_diagonal_basis(c, n_v, p, basis));
   if ((int)basis.size() < k) {
     set_error("sbci_davidson: the space holds fewer than k start vectors");
     return SBCI_ERR_INVALID;
   }
   // slot pool: the subspace plus the k residuals / corrections
   DavSolve d;
-  d.c = c;
+  RET(scratch_init(d, c));
   const int cap = max_space + k;
   d.vb.assign(cap, nullptr);
   d.ab.assign(cap, nullptr);
@@ -974,16 +1010,10 @@ sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space
     RET(dmalloc(&d.ab[sl], (size_t)N));
   }
   for (int sl = cap - 1; sl >= 0; --sl) d.free_slots.push_back(sl);
-  d.grid = dav_dots_grid(N, c->nsm);
-  RET(dmalloc(&d.partials, (size_t)kDavMaxPairs * d.grid));
-  RET(dmalloc(&d.d_res, (size_t)kDavMaxPairs));
-  CK(cudaMallocHost((void **)&d.h_res, sizeof(double) * kDavMaxPairs));
   if (vector_bytes) *vector_bytes = 2LL * cap * N * (long long)sizeof(double);
   for (const Sparse &b : basis) {
     const int sl = d.take();
-    CK(cudaMemsetAsync(d.vb[sl], 0, sizeof(double) * N, c->stream));
-    for (auto &kv : b)
-      CK(cudaMemcpyAsync(d.vb[sl] + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    RET(upload_sparse(c, b, d.vb[sl]));
     d.V.push_back(sl);
   }
   const long long max_sigma = (long long)p.max_sigma * k;
@@ -1077,7 +1107,7 @@ sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space
       if (n_sigma >= max_sigma) break;
       const int ts = R[a];
       double *t = d.vb[ts];
-      RET(timed(c, K_DAVP, [&] { return launch_dav_precond(t, c->d_diag, theta[a], p.guard, N, c->nsm, c->stream); }));
+      RET(timed(c, K_DAVP, [&] { return launch_dav_precond(t, t, c->d_diag, theta[a], p.guard, N, c->nsm, c->stream); }));
       if (p.sector) RET(timed(c, K_DAVP, [&] { return launch_symmetrize(t, c->Na, c->stream); }));
       RET(dav_dots(d, {t}, {t}, r));
       const double n0 = r[0];
@@ -1164,6 +1194,547 @@ sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space
   if (!converged) {
     set_error("sbci_davidson: stopped before every state converged");
     return SBCI_ERR_NOT_CONVERGED;
+  }
+  return SBCI_OK;
+}
+
+// Everything a solve needs before its first start vector: parameters,
+// per-solve vectors, the controller's thresholds.
+sbci_status begin_common(sbci_ctx *c, int k, const sbci_params *params, const char *who) {
+  if (!c || k < 1 || k > kMaxStates) {
+    set_error(std::string(who) + ": need a context and 1 <= k <= 8");
+    return SBCI_ERR_INVALID;
+  }
+  Solver &s = c->s;
+  if (params) s.p = *params;
+  else sbci_params_init(&s.p);
+  if (s.p.sector && c->ne_a != c->ne_b) {
+    set_error("sector = 1 needs nalpha == nbeta");
+    return SBCI_ERR_INVALID;
+  }
+  RET(check_prec(c, s.p.prec));
+  if ((long long)k > c->ndet) {
+    set_error(std::string(who) + ": more states than determinants");
+    return SBCI_ERR_INVALID;
+  }
+  RET(alloc_solver(c, k));
+  RET(ensure_G(c, SBCI_FP64));
+  if (s.p.prec != SBCI_FP64) RET(ensure_G(c, s.p.prec));
+  s.k = k;
+  s.done = false;
+  s.Ec.clear();
+  s.trace.clear();
+  s.rep.assign(k, sbci_report{});
+  s.any_unconverged = 0;
+  s.active = true;
+  CtlState &h = *s.h_ctl;
+  h.p.eps0 = s.p.eps0;
+  h.p.r0 = s.p.r0;
+  h.p.b_th = s.p.b_th;
+  h.p.eps1 = s.p.eps1;
+  h.p.x_th1 = s.p.x_th1;
+  h.p.x_th2 = s.p.x_th2;
+  h.p.r1 = s.p.r1;
+  h.p.guard = s.p.guard;
+  h.p.gs_tol = s.p.gs_tol;
+  h.p.mixed_eps = s.p.mixed_eps;
+  h.p.mixed_r = s.p.mixed_r;
+  h.p.max_cycle = s.p.max_cycle;
+  h.p.max_sigma = s.p.max_sigma;
+  h.p.refine_max_sigma = s.p.refine_max_sigma;
+  h.p.user_prec = s.p.prec;
+  return SBCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SBCI2 (Algorithm 2, Sections S2.1-S2.5): the pair (alpha, alpha+1) advances
+// together, the lower state is stored when it converges, and the highest
+// state runs SBCI1 on the device controller (Fig. 1B).  Pair steps are
+// host-driven: two FP64 H-products, one batch of dot products (overlap S and
+// T = B^T [H B] of the step's basis), the 6x6 canonical orthogonalisation and
+// eigen-problem on the host, and one in-place combination kernel for x, X, y,
+// Y and the new residuals.  Readings Q1-Q10 (as the oracle):
+//  Q1 start vectors from max(k, n_init or 2) lowest-diagonal vectors (S74-S76);
+//  Q2 a later pair's upper start: projected against the stored states and the
+//     new lower vector, normalised, E_0 its Rayleigh quotient;
+//  Q3 preconditioner shift E_t of state 0 in the ground pair, E_c^0 after;
+//  Q4 subspace matrix (T + T^T)/2;  Q5 overlap eigenvalues below 1e-14 dropped;
+//  Q6 undefined later-step coefficients: first-step path from the same x, z;
+//  Q7 restart: x/|x|, X/|x|, E_0 = E_{t+1}, y = 0, first-step path;
+//  Q8 max_sigma H-products per lower state;
+//  Q9 x_{t+1} = k v, X_{t+1} = k [H-images] V' (no cancellation of S124);
+//  Q10 the upper start of a later pair gets X_0 by one H-product.
+
+struct DevBuffers {
+  std::vector<double *> v;
+  ~DevBuffers() {
+    for (double *p : v)
+      if (p) cudaFree(p);
+  }
+  sbci_status get(sbci_ctx *c, double **out) {
+    double *p = nullptr;
+    RET(dmalloc(&p, (size_t)c->ndet));
+    v.push_back(p);
+    *out = p;
+    return SBCI_OK;
+  }
+};
+
+struct PairCoef {
+  bool first;                 // first-step path (Eq. S93): basis x^a, x^b, z^a, z^b
+  int nb;                     // basis vectors (4 or 6)
+  double Vp[6][2];            // V' = P V, columns of the two lowest Ritz vectors
+  double w[2];                // E_{t+1}^a, E_{t+1}^b
+  double A[2][2], B[2][2], C[2][2], k[2];
+};
+
+// Canonical orthogonalisation, subspace eigen-problem and coefficients of one
+// pair step.  S6 and T6 are the 6x6 overlap and T of (x^a, x^b, y^a, y^b, z^a,
+// z^b) (rows and columns of y unused on the first path).  Returns false if the
+// step is undefined on the requested path.
+bool pair_step(const double *S6, const double *T6, bool first, PairCoef *pc) {
+  static const int kFirst[4] = {0, 1, 4, 5}, kLater[6] = {0, 1, 2, 3, 4, 5};
+  const int nb = first ? 4 : 6;
+  const int *ix = first ? kFirst : kLater;
+  double S[36], Hs[36], s[6], U[36];
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      S[i * nb + j] = S6[ix[i] * 6 + ix[j]];
+      Hs[i * nb + j] = 0.5 * (T6[ix[i] * 6 + ix[j]] + T6[ix[j] * 6 + ix[i]]);
+    }
+  jacobi_eigh(nb, S, s, U);
+  double P[36];  // nb x r
+  int r = 0;
+  for (int c = 0; c < nb; ++c) {
+    if (!(s[c] >= 1e-14)) continue;
+    const double f = 1.0 / std::sqrt(s[c]);
+    for (int i = 0; i < nb; ++i) P[i * 6 + r] = U[i * nb + c] * f;
+    ++r;
+  }
+  if (r < 2) return false;
+  double Hh[36], w[6], V[36];
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      double acc = 0.0;
+      for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) acc += P[i * 6 + a] * Hs[i * nb + j] * P[j * 6 + b];
+      Hh[a * r + b] = acc;
+    }
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < a; ++b) Hh[a * r + b] = Hh[b * r + a] = 0.5 * (Hh[a * r + b] + Hh[b * r + a]);
+  jacobi_eigh(r, Hh, w, V);
+  pc->first = first;
+  pc->nb = nb;
+  for (int i = 0; i < nb; ++i)
+    for (int col = 0; col < 2; ++col) {
+      double acc = 0.0;
+      for (int a = 0; a < r; ++a) acc += P[i * 6 + a] * V[a * r + col];
+      pc->Vp[i][col] = acc;
+    }
+  pc->w[0] = w[0];
+  pc->w[1] = w[1];
+  const auto &Vp = pc->Vp;
+  double a_ab, a_ba, k0, k1;
+  if (first) {  // Eq. S93
+    k0 = 1.0 / Vp[0][0];
+    k1 = 1.0 / Vp[1][1];
+    a_ab = Vp[1][0] / Vp[0][0];
+    a_ba = Vp[0][1] / Vp[1][1];
+    pc->C[0][0] = -Vp[2][0] / Vp[0][0];
+    pc->C[0][1] = -Vp[3][0] / Vp[0][0];
+    pc->C[1][0] = -Vp[2][1] / Vp[1][1];
+    pc->C[1][1] = -Vp[3][1] / Vp[1][1];
+    pc->B[0][0] = pc->B[1][1] = 1.0;
+    pc->B[0][1] = pc->B[1][0] = 0.0;
+  } else {  // Eqs. S116, S117, S112, S121
+    a_ab = Vp[1][0] / Vp[2][0];
+    a_ba = Vp[0][1] / Vp[3][1];
+    k0 = 1.0 / (Vp[0][0] - Vp[3][0] * a_ba);
+    k1 = 1.0 / (Vp[1][1] - Vp[2][1] * a_ab);
+    pc->B[0][0] = k0 * Vp[2][0];
+    pc->B[0][1] = k0 * Vp[3][0];
+    pc->B[1][0] = k1 * Vp[2][1];
+    pc->B[1][1] = k1 * Vp[3][1];
+    const double m00 = Vp[2][0], m01 = Vp[3][0], m10 = Vp[2][1], m11 = Vp[3][1];
+    const double det = m00 * m11 - m01 * m10;
+    if (!(std::isfinite(det) && det != 0.0)) return false;
+    const double r00 = Vp[4][0], r01 = Vp[5][0], r10 = Vp[4][1], r11 = Vp[5][1];
+    // C = -M^-1 R
+    pc->C[0][0] = -(m11 * r00 - m01 * r10) / det;
+    pc->C[0][1] = -(m11 * r01 - m01 * r11) / det;
+    pc->C[1][0] = -(-m10 * r00 + m00 * r10) / det;
+    pc->C[1][1] = -(-m10 * r01 + m00 * r11) / det;
+  }
+  pc->A[0][0] = pc->A[1][1] = 0.0;
+  pc->A[0][1] = a_ab;
+  pc->A[1][0] = a_ba;
+  pc->k[0] = k0;
+  pc->k[1] = k1;
+  const double chk[] = {k0, k1, a_ab, a_ba, pc->B[0][0], pc->B[0][1], pc->B[1][0], pc->B[1][1],
+                        pc->C[0][0], pc->C[0][1], pc->C[1][0], pc->C[1][1], w[0], w[1]};
+  for (double v : chk)
+    if (!std::isfinite(v)) return false;
+  return true;
+}
+
+struct PairVecs {
+  double *x[2], *X[2], *y[2], *Y[2], *z[2], *Z[2];  // z holds z' between steps
+};
+
+sbci_status sbci2_pair(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2], int max_cycle2) {
+  Solver &s = c->s;
+  const sbci_params &p = s.p;
+  const long long N = c->ndet;
+  std::vector<double> r;
+  const double *xc = s.xc;
+  auto xcv = [&](int j) { return xc + (size_t)j * N; };
+  // Algorithm 2 line 1, Eqs. S77-S80
+  if (alpha > 0) {
+    std::vector<const double *> u, v;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < alpha; ++j) {
+        u.push_back(xcv(j));
+        v.push_back(P.x[i]);
+      }
+    RET(dav_dots(vs, u, v, r));
+    std::vector<const double *> in{P.x[0], P.x[1], P.X[0], P.X[1]};
+    for (int j = 0; j < alpha; ++j) in.push_back(xcv(j));
+    std::vector<double> co(in.size() * 4, 0.0);
+    for (int q = 0; q < 4; ++q) co[q * 4 + q] = 1.0;
+    for (int j = 0; j < alpha; ++j)
+      for (int i = 0; i < 2; ++i) {
+        co[(4 + j) * 4 + i] = -r[(size_t)i * alpha + j];
+        co[(4 + j) * 4 + 2 + i] = -s.Ec[j] * r[(size_t)i * alpha + j];
+      }
+    RET(dav_combine(vs, {P.x[0], P.x[1], P.X[0], P.X[1]}, in, co));
+  }
+  RET(dav_dots(vs, {P.x[0], P.x[1]}, {P.x[0], P.x[1]}, r));
+  {
+    const double n0 = std::sqrt(r[0]), n1 = std::sqrt(r[1]);
+    std::vector<double> co(16, 0.0);
+    co[0 * 4 + 0] = 1.0 / n0;
+    co[1 * 4 + 1] = 1.0 / n1;
+    co[2 * 4 + 2] = 1.0 / n0;
+    co[3 * 4 + 3] = 1.0 / n1;
+    RET(dav_combine(vs, {P.x[0], P.x[1], P.X[0], P.X[1]}, {P.x[0], P.x[1], P.X[0], P.X[1]}, co));
+  }
+  // line 3: z'_0 = X_0 - E_0 x_0
+  RET(dav_combine(vs, {P.z[0], P.z[1]}, {P.x[0], P.x[1], P.X[0], P.X[1]},
+                  {-E[0], 0.0, 0.0, -E[1], 1.0, 0.0, 0.0, 1.0}));
+  bool first = true;
+  int t = 0, nstep = 0, restarts[4] = {0, 0, 0, 0};
+  long long sigma = 0;
+  for (;;) {
+    sbci_report &rep = s.rep[alpha];
+    if (sigma >= p.max_sigma) {  // Q8: the lower state ends unconverged
+      RET(dav_dots(vs, {P.x[0], P.x[1]}, {P.x[0], P.x[1]}, r));
+      const double n0 = std::sqrt(r[0]), n1 = std::sqrt(r[1]);
+      RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / n0}));
+      s.Ec.push_back(E[0]);
+      rep = sbci_report{};
+      rep.energy = E[0] + c->e_core;
+      rep.converged = 0;
+      rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
+      rep.n_step = nstep;
+      for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
+      s.any_unconverged = 1;
+      RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / n1, 0.0, 0.0, 1.0 / n1}));
+      E[0] = E[1];
+      return SBCI_OK;
+    }
+    const double E_pre = alpha == 0 ? E[0] : s.Ec[0];  // Q3
+    for (int i = 0; i < 2; ++i) {  // Eqs. S81 / S101
+      RET(timed(c, K_DAVP, [&] {
+        return launch_dav_precond(P.z[i], P.z[i], c->d_diag, E_pre, p.guard, N, c->nsm, c->stream);
+      }));
+      if (p.sector) RET(timed(c, K_DAVP, [&] { return launch_symmetrize(P.z[i], c->Na, c->stream); }));
+    }
+    if (alpha > 0) {
+      std::vector<const double *> u, v;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < alpha; ++j) {
+          u.push_back(xcv(j));
+          v.push_back(P.z[i]);
+        }
+      RET(dav_dots(vs, u, v, r));
+      std::vector<const double *> in{P.z[0], P.z[1]};
+      for (int j = 0; j < alpha; ++j) in.push_back(xcv(j));
+      std::vector<double> co(in.size() * 2, 0.0);
+      co[0] = co[3] = 1.0;
+      for (int j = 0; j < alpha; ++j)
+        for (int i = 0; i < 2; ++i) co[(2 + j) * 2 + i] = -r[(size_t)i * alpha + j];
+      RET(dav_combine(vs, {P.z[0], P.z[1]}, in, co));
+    }
+    for (int i = 0; i < 2; ++i) {  // Eqs. S82 / S102
+      RET(run_sigma(c, P.z[i], P.Z[i], SBCI_FP64));
+      ++sigma;
+    }
+    // overlap and T of the basis (x^a, x^b, y^a, y^b, z^a, z^b)
+    const double *Bv[6] = {P.x[0], P.x[1], P.y[0], P.y[1], P.z[0], P.z[1]};
+    const double *HB[6] = {P.X[0], P.X[1], P.Y[0], P.Y[1], P.Z[0], P.Z[1]};
+    static const int kUse4[4] = {0, 1, 4, 5};
+    const int nuse = first ? 4 : 6;
+    std::vector<int> use;
+    for (int i = 0; i < nuse; ++i) use.push_back(first ? kUse4[i] : i);
+    std::vector<const double *> u, v;
+    for (int a = 0; a < nuse; ++a)
+      for (int b = a; b < nuse; ++b) {
+        u.push_back(Bv[use[a]]);
+        v.push_back(Bv[use[b]]);
+      }
+    const size_t ns = u.size();
+    for (int a = 0; a < nuse; ++a)
+      for (int b = 0; b < nuse; ++b) {
+        u.push_back(Bv[use[a]]);
+        v.push_back(HB[use[b]]);
+      }
+    RET(dav_dots(vs, u, v, r));
+    double S6[36] = {0}, T6[36] = {0};
+    size_t q = 0;
+    for (int a = 0; a < nuse; ++a)
+      for (int b = a; b < nuse; ++b, ++q) S6[use[a] * 6 + use[b]] = S6[use[b] * 6 + use[a]] = r[q];
+    for (int a = 0; a < nuse; ++a)
+      for (int b = 0; b < nuse; ++b, ++q) T6[use[a] * 6 + use[b]] = r[q];
+    (void)ns;
+    PairCoef pc;
+    bool ok = false;
+    if (!first) ok = pair_step(S6, T6, false, &pc);
+    if (!ok) ok = pair_step(S6, T6, true, &pc);  // first step, or Q6
+    if (!ok) {
+      set_error("SBCI2: the pair step is undefined (subspace rank below 2)");
+      return SBCI_ERR_NUMERIC;
+    }
+    const bool undef = pc.first && !first;
+    // one combination: x, X (Q9), y, Y (Eqs. S94-S95 / S122-S123), z' (Eqs. S98, S100 / S126, S128)
+    {
+      std::vector<const double *> in;
+      std::vector<int> basis_ix;  // position in the 6-basis of each vector input
+      for (int i = 0; i < 6; ++i) {
+        if (pc.first && (i == 2 || i == 3)) continue;
+        basis_ix.push_back(i);
+      }
+      const int nb = (int)basis_ix.size();
+      for (int i : basis_ix) in.push_back(Bv[i]);
+      for (int i : basis_ix) in.push_back(HB[i]);
+      const int nout = 10;
+      std::vector<double> co((size_t)2 * nb * nout, 0.0);
+      auto C = [&](int qin, int out) -> double & { return co[(size_t)qin * nout + out]; };
+      auto pos = [&](int b6) {
+        for (int j = 0; j < nb; ++j)
+          if (basis_ix[j] == b6) return j;
+        return -1;
+      };
+      for (int i = 0; i < 2; ++i) {
+        for (int j = 0; j < nb; ++j) {
+          C(j, i) = pc.k[i] * pc.Vp[j][i];            // x_{t+1}^i
+          C(nb + j, 2 + i) = pc.k[i] * pc.Vp[j][i];   // X_{t+1}^i
+          C(j, 8 + i) = -pc.w[i] * pc.Vp[j][i];       // z'^i = sum_j V'_{j,i} (H b_j - E b_j)
+          C(nb + j, 8 + i) = pc.Vp[j][i];
+        }
+        // y_{t+1}^i = y_t^i - C_{i0} z^a - C_{i1} z^b + A_{i,1-i} x^{1-i}
+        if (!pc.first) {
+          C(pos(2 + i), 4 + i) = 1.0;
+          C(nb + pos(2 + i), 6 + i) = 1.0;
+        }
+        for (int j = 0; j < 2; ++j) {
+          C(pos(4 + j), 4 + i) = -pc.C[i][j];
+          C(nb + pos(4 + j), 6 + i) = -pc.C[i][j];
+        }
+        C(pos(1 - i), 4 + i) = pc.A[i][1 - i];
+        C(nb + pos(1 - i), 6 + i) = pc.A[i][1 - i];
+      }
+      RET(dav_combine(vs, {P.x[0], P.x[1], P.X[0], P.X[1], P.y[0], P.y[1], P.Y[0], P.Y[1], P.z[0], P.z[1]}, in,
+                      co));
+    }
+    ++nstep;
+    RET(dav_dots(vs, {P.z[0], P.z[1], P.x[0], P.x[1]}, {P.z[0], P.z[1], P.x[0], P.x[1]}, r));
+    const double dz = std::sqrt(r[0]);
+    const double nx0 = std::sqrt(r[2]), nx1 = std::sqrt(r[3]);  // |x_{t+1}| (= |k| up to rounding)
+    const double dE = std::fabs(pc.w[0] - E[0]);
+    sbci_trace_record rec{};
+    rec.state = alpha;
+    rec.t = t;
+    rec.energy = pc.w[0];
+    rec.b = pc.B[0][0];
+    rec.c = pc.C[0][0];
+    rec.k = pc.k[0];
+    rec.dE = dE;
+    rec.dz = dz;
+    rec.event = undef ? 8 : 0;
+    rec.prec = SBCI_FP64;
+    const double ak0 = std::fabs(pc.k[0]), ak1 = std::fabs(pc.k[1]);
+    if (dE < p.eps0 && dz < p.r0) {  // Eq. S99 / S127
+      rec.event = 1;
+      s.trace.push_back(rec);
+      RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / nx0}));
+      s.Ec.push_back(pc.w[0]);
+      rep = sbci_report{};
+      rep.energy = pc.w[0] + c->e_core;
+      rep.residual = dz;
+      rep.converged = 1;
+      rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
+      rep.n_step = nstep;
+      for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
+      // the normalised upper vector starts the next pair (or the last state)
+      RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / nx1, 0.0, 0.0, 1.0 / nx1}));
+      E[0] = pc.w[1];
+      return SBCI_OK;
+    }
+    int cause = -1;  // Section S2.5
+    if ((std::fabs(pc.B[0][0]) < p.b_th || std::fabs(pc.B[1][1]) < p.b_th) && dE < p.eps1) cause = 0;
+    else if (std::min(ak0, ak1) < p.x_th1 || std::max(ak0, ak1) > p.x_th2) cause = 1;
+    else if (dz > p.r1 && t > 0) cause = 2;
+    else if (t + 1 >= max_cycle2) cause = 3;
+    E[0] = pc.w[0];
+    E[1] = pc.w[1];
+    if (cause >= 0) {  // Q7
+      ++restarts[cause];
+      rec.event = 2 + cause;
+      s.trace.push_back(rec);
+      // x, X normalised; z'_0 = X_0 - E_0 x_0 = z'_{t+1} k / |x_{t+1}|
+      std::vector<double> co(36, 0.0);
+      const double f[6] = {1.0 / nx0, 1.0 / nx1, 1.0 / nx0, 1.0 / nx1, pc.k[0] / nx0, pc.k[1] / nx1};
+      for (int q2 = 0; q2 < 6; ++q2) co[q2 * 6 + q2] = f[q2];
+      RET(dav_combine(vs, {P.x[0], P.x[1], P.X[0], P.X[1], P.z[0], P.z[1]},
+                      {P.x[0], P.x[1], P.X[0], P.X[1], P.z[0], P.z[1]}, co));
+      first = true;
+      t = 0;
+      continue;
+    }
+    s.trace.push_back(rec);
+    first = false;
+    ++t;
+  }
+}
+
+sbci_status sbci2_run(sbci_ctx *c, int k, int max_cycle2) {
+  Solver &s = c->s;
+  const sbci_params &p = s.p;
+  const long long N = c->ndet;
+  VecScratch vs;
+  RET(scratch_init(vs, c));
+  DevBuffers buf;
+  // Q1, Eqs. S74-S76: start vectors and their H-images
+  std::vector<Sparse> basis;
+  RET(lowest_diagonal_basis(c, std::max(k, p.n_init > 0 ? p.n_init : 2), p, basis));
+  const int m = (int)basis.size();
+  if (m < k) {
+    set_error("sbci_solve_sbci2: the space holds fewer than k start vectors");
+    return SBCI_ERR_INVALID;
+  }
+  if (m > kDavMaxIn / 2) {
+    set_error("sbci_solve_sbci2: n_init too large");
+    return SBCI_ERR_INVALID;
+  }
+  std::vector<double *> e(m), He(m), xs(k), Xs(k);
+  for (int j = 0; j < m; ++j) {
+    RET(buf.get(c, &e[j]));
+    RET(buf.get(c, &He[j]));
+    RET(upload_sparse(c, basis[j], e[j]));
+    RET(run_sigma(c, e[j], He[j], SBCI_FP64));
+  }
+  std::vector<double> r, A((size_t)m * m), w(m), U((size_t)m * m);
+  {
+    std::vector<const double *> u, v;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        u.push_back(e[i]);
+        v.push_back(He[j]);
+      }
+    RET(dav_dots(vs, u, v, r));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = 0.5 * (r[(size_t)i * m + j] + r[(size_t)j * m + i]);
+    jacobi_eigh(m, A.data(), w.data(), U.data());
+  }
+  for (int i = 0; i < k; ++i) {
+    RET(buf.get(c, &xs[i]));
+    RET(buf.get(c, &Xs[i]));
+  }
+  {
+    std::vector<const double *> in;
+    for (int j = 0; j < m; ++j) in.push_back(e[j]);
+    for (int j = 0; j < m; ++j) in.push_back(He[j]);
+    for (int i0 = 0; i0 < k; i0 += kDavMaxOut / 2) {
+      const int ni = std::min(kDavMaxOut / 2, k - i0);
+      std::vector<double *> out;
+      std::vector<double> co((size_t)2 * m * 2 * ni, 0.0);
+      for (int i = 0; i < ni; ++i) out.push_back(xs[i0 + i]);
+      for (int i = 0; i < ni; ++i) out.push_back(Xs[i0 + i]);
+      for (int j = 0; j < m; ++j)
+        for (int i = 0; i < ni; ++i) {
+          co[(size_t)j * 2 * ni + i] = U[(size_t)j * m + i0 + i];
+          co[(size_t)(m + j) * 2 * ni + ni + i] = U[(size_t)j * m + i0 + i];
+        }
+      RET(dav_combine(vs, out, in, co));
+    }
+  }
+  PairVecs P;
+  for (int i = 0; i < 2; ++i) {
+    RET(buf.get(c, &P.x[i]));
+    RET(buf.get(c, &P.X[i]));
+    RET(buf.get(c, &P.y[i]));
+    RET(buf.get(c, &P.Y[i]));
+    RET(buf.get(c, &P.z[i]));
+    RET(buf.get(c, &P.Z[i]));
+  }
+  double E[2] = {w[0], k > 1 ? w[1] : 0.0};
+  RET(dav_combine(vs, {P.x[0], P.X[0]}, {xs[0], Xs[0]}, {1.0, 0.0, 0.0, 1.0}));
+  for (int alpha = 0; alpha + 1 < k; ++alpha) {
+    if (alpha == 0) {
+      RET(dav_combine(vs, {P.x[1], P.X[1]}, {xs[1], Xs[1]}, {1.0, 0.0, 0.0, 1.0}));
+      E[1] = w[1];
+    } else {  // Q2, Q10
+      std::vector<const double *> u, v, in{xs[alpha + 1]};
+      for (int j = 0; j < alpha; ++j) {
+        u.push_back(s.xc + (size_t)j * N);
+        v.push_back(xs[alpha + 1]);
+      }
+      RET(dav_dots(vs, u, v, r));
+      std::vector<double> co{1.0};
+      for (int j = 0; j < alpha; ++j) {
+        in.push_back(s.xc + (size_t)j * N);
+        co.push_back(-r[j]);
+      }
+      RET(dav_combine(vs, {P.x[1]}, in, co));
+      RET(dav_dots(vs, {P.x[0]}, {P.x[1]}, r));
+      RET(dav_combine(vs, {P.x[1]}, {P.x[1], P.x[0]}, {1.0, -r[0]}));
+      RET(dav_dots(vs, {P.x[1]}, {P.x[1]}, r));
+      RET(dav_combine(vs, {P.x[1]}, {P.x[1]}, {1.0 / std::sqrt(r[0])}));
+      RET(run_sigma(c, P.x[1], P.X[1], SBCI_FP64));
+      RET(dav_dots(vs, {P.x[1]}, {P.X[1]}, r));
+      E[1] = r[0];
+    }
+    RET(sbci2_pair(c, vs, P, alpha, E, max_cycle2));
+  }
+  // the highest state: SBCI1 from the last pair's normalised upper vector
+  // (Fig. 1B), projected against the stored states (Eqs. S4-S7)
+  CK(cudaMemcpyAsync(s.x, P.x[0], sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(s.X, P.X[0], sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+  const int last = k - 1;
+  if (last > 0) {
+    std::vector<const double *> u, v;
+    for (int i = 0; i < last; ++i) {
+      u.push_back(s.xc + (size_t)i * N);
+      v.push_back(s.x);
+    }
+    RET(dav_dots(vs, u, v, r));
+    std::vector<const double *> in{s.x, s.X};
+    std::vector<double> co{1.0, 0.0, 0.0, 1.0};
+    for (int i = 0; i < last; ++i) {
+      in.push_back(s.xc + (size_t)i * N);
+      co.push_back(-r[i]);
+      co.push_back(-s.Ec[i] * r[i]);
+    }
+    RET(dav_combine(vs, {s.x, s.X}, in, co));
+  }
+  RET(dav_dots(vs, {s.x}, {s.x}, r));
+  const double nrm = std::sqrt(r[0]);
+  RET(dav_combine(vs, {s.x, s.X}, {s.x, s.X}, {1.0 / nrm, 0.0, 0.0, 1.0 / nrm}));
+  RET(start_state(c, last, E[0]));
+  while (!s.done) {
+    RET(run_until_halt(c));
+    const sbci_status st = handle_halt(c);
+    if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) return st;
   }
   return SBCI_OK;
 }
@@ -1570,52 +2141,12 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
 }
 
 sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const double *c0) {
-  if (!c || k < 1 || k > kMaxStates) {
-    set_error("sbci_begin: need a context and 1 <= k <= 8");
-    return SBCI_ERR_INVALID;
-  }
-  Solver &s = c->s;
-  if (params) s.p = *params;
-  else sbci_params_init(&s.p);
-  if (s.p.sector && c->ne_a != c->ne_b) {
-    set_error("sector = 1 needs nalpha == nbeta");
-    return SBCI_ERR_INVALID;
-  }
-  if (s.p.init == 1 && !c0) {
+  if (c && params && params->init == 1 && !c0) {
     set_error("init = 1 needs c0");
     return SBCI_ERR_INVALID;
   }
-  RET(check_prec(c, s.p.prec));
-  if ((long long)k > c->ndet) {
-    set_error("sbci_begin: more states than determinants");
-    return SBCI_ERR_INVALID;
-  }
-  RET(alloc_solver(c, k));
-  RET(ensure_G(c, SBCI_FP64));
-  if (s.p.prec != SBCI_FP64) RET(ensure_G(c, s.p.prec));
-  s.k = k;
-  s.done = false;
-  s.Ec.clear();
-  s.trace.clear();
-  s.rep.assign(k, sbci_report{});
-  s.any_unconverged = 0;
-  s.active = true;
-  CtlState &h = *s.h_ctl;
-  h.p.eps0 = s.p.eps0;
-  h.p.r0 = s.p.r0;
-  h.p.b_th = s.p.b_th;
-  h.p.eps1 = s.p.eps1;
-  h.p.x_th1 = s.p.x_th1;
-  h.p.x_th2 = s.p.x_th2;
-  h.p.r1 = s.p.r1;
-  h.p.guard = s.p.guard;
-  h.p.gs_tol = s.p.gs_tol;
-  h.p.mixed_eps = s.p.mixed_eps;
-  h.p.mixed_r = s.p.mixed_r;
-  h.p.max_cycle = s.p.max_cycle;
-  h.p.max_sigma = s.p.max_sigma;
-  h.p.refine_max_sigma = s.p.refine_max_sigma;
-  h.p.user_prec = s.p.prec;
+  RET(begin_common(c, k, params, "sbci_begin"));
+  Solver &s = c->s;
   double E0 = 0.0;
   if (s.p.init == 1) RET(init_from_vector(c, c0, &E0));
   else RET(initial_guess(c, k, &E0));
@@ -1628,6 +2159,7 @@ sbci_status sbci_begin(sbci_ctx *c, int k, const sbci_params *params, const doub
   }
   return start_state(c, 0, E0);
 }
+
 
 sbci_status sbci_step(sbci_ctx *c, sbci_trace_record *rec, int *done) {
   if (!c || !c->s.active) {
@@ -1688,9 +2220,28 @@ sbci_status sbci_solve(sbci_ctx *c, int k, const sbci_params *params, const doub
   return sbci_finish(c, energies, vecs, rep);
 }
 
+sbci_status sbci_solve_sbci2(sbci_ctx *c, int k, const sbci_params *params, int max_cycle2, double *energies,
+                             double *vecs, sbci_report *rep) {
+  if (params && (params->prec != SBCI_FP64 || params->init != 0 || params->start_noise > 0.0)) {
+    set_error("sbci_solve_sbci2: needs prec = SBCI_FP64, init = 0 and start_noise = 0");
+    return SBCI_ERR_INVALID;
+  }
+  if (max_cycle2 < 0) {
+    set_error("sbci_solve_sbci2: max_cycle2 must be >= 0");
+    return SBCI_ERR_INVALID;
+  }
+  RET(begin_common(c, k, params, "sbci_solve_sbci2"));
+  const sbci_status st = sbci2_run(c, k, max_cycle2 > 0 ? max_cycle2 : 10);
+  if (st != SBCI_OK) {
+    c->s.active = false;
+    return st;
+  }
+  return sbci_finish(c, energies, vecs, rep);
+}
+
 sbci_status sbci_davidson(sbci_ctx *c, int k, const sbci_params *params, int max_space, double *energies,
                           double *vecs, sbci_report *rep, long long *vector_bytes) {
-  if (!c || k < 1 || k > kDavMaxOut || !energies) {
+  if (!c || k < 1 || k > kMaxStates || !energies) {
     set_error("sbci_davidson: need a context, 1 <= k <= 8 and energies");
     return SBCI_ERR_INVALID;
   }

@@ -1,7 +1,8 @@
-// Kernels of the block Davidson-Liu solver (Davidson 1975; Liu 1978), the
-// method the paper compares SBCI with: dot products over lists of vector
-// pairs, linear combinations of subspace vectors, and the diagonal
-// preconditioner (D - theta)^-1.  These are the "inner products and
+// Kernels of the host-driven solvers: the block Davidson-Liu solver
+// (Davidson 1975; Liu 1978), the method the paper compares SBCI with, and the
+// SBCI2 pair steps (Algorithm 2).  Dot products over lists of vector pairs,
+// linear combinations of whole vectors, and the diagonal preconditioner
+// (D - theta)^-1.  For Davidson these are the "inner products and
 // matrix-product constructions" over the stored subspace that SBCI avoids
 // (Introduction); each is one streaming pass over its vectors.
 //
@@ -89,14 +90,16 @@ __global__ void __launch_bounds__(kDavThreads) k_dav_combine(const __grid_consta
   }
 }
 
-// t_i <- t_i / d_i, d_i = D_i - shift with |d_i| < guard replaced by
+// out_i = in_i / d_i, d_i = D_i - shift with |d_i| < guard replaced by
 // sign(d_i) guard (d_i = 0 -> +guard), the guard SBCI uses (Eqs. 6-7).
-__global__ void k_dav_precond(double *t, const double *diag, double shift, double guard, long long n) {
+// out may be in.
+__global__ void k_dav_precond(double *out, const double *in, const double *diag, double shift, double guard,
+                              long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double d = diag[i] - shift;
     if (fabs(d) < guard) d = d < 0.0 ? -guard : guard;
-    t[i] = t[i] / d;
+    out[i] = in[i] / d;
   }
 }
 
@@ -145,9 +148,9 @@ cudaError_t launch_dav_combine(double *const *out, int nout, const double *const
   return cudaGetLastError();
 }
 
-cudaError_t launch_dav_precond(double *t, const double *diag, double shift, double guard, long long n, int nsm,
-                               cudaStream_t s) {
-  k_dav_precond<<<dav_grid(n, 8 * nsm), kDavThreads, 0, s>>>(t, diag, shift, guard, n);
+cudaError_t launch_dav_precond(double *out, const double *in, const double *diag, double shift, double guard,
+                               long long n, int nsm, cudaStream_t s) {
+  k_dav_precond<<<dav_grid(n, 8 * nsm), kDavThreads, 0, s>>>(out, in, diag, shift, guard, n);
   return cudaGetLastError();
 }
 

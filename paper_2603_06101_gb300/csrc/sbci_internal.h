@@ -195,11 +195,12 @@ cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s);
 // r[I] = SplitMix64 vector of (seed, alpha) in [-1, 1)
 cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s);
 
-// Kernels of the block Davidson-Liu solver (kernels_dav.cu).
+// Kernels of the block Davidson-Liu solver and of the SBCI2 pair steps
+// (kernels_dav.cu).
 constexpr int kDavMaxSpace = 64;                  // subspace vectors
 constexpr int kDavMaxPairs = 2 * kDavMaxSpace;    // dot pairs per launch
 constexpr int kDavMaxIn = kDavMaxSpace + 8;       // inputs of one combination
-constexpr int kDavMaxOut = 8;                     // outputs of one combination
+constexpr int kDavMaxOut = 12;                    // outputs of one combination
 int dav_dots_grid(long long n, int nsm);
 // partials[p * grid + b] = block b's part of u_p . v_p (finish with launch_reduce).
 cudaError_t launch_dav_dots(const double *const *u, const double *const *v, int npairs, long long n,
@@ -207,9 +208,9 @@ cudaError_t launch_dav_dots(const double *const *u, const double *const *v, int 
 // out_j = sum_q coef[q * nout + j] in_q; an output may be one of the inputs.
 cudaError_t launch_dav_combine(double *const *out, int nout, const double *const *in, int nin,
                                const double *coef, long long n, int nsm, cudaStream_t s);
-// t <- t / guarded(D - shift)
-cudaError_t launch_dav_precond(double *t, const double *diag, double shift, double guard, long long n, int nsm,
-                               cudaStream_t s);
+// out <- in / guarded(D - shift) (out may be in)
+cudaError_t launch_dav_precond(double *out, const double *in, const double *diag, double shift, double guard,
+                               long long n, int nsm, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small dense symmetric eigen-solver (cyclic Jacobi), ascending eigenvalues,

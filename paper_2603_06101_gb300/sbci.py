@@ -74,7 +74,7 @@ _lib = None
 
 EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_table",
            "sbci_diagonal", "sbci_sigma", "sbci_begin", "sbci_step", "sbci_finish", "sbci_solve",
-           "sbci_trace", "sbci_davidson", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
+           "sbci_trace", "sbci_solve_sbci2", "sbci_davidson", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
            "sbci_server_create", "sbci_server_submit", "sbci_server_progress", "sbci_server_poll",
            "sbci_server_set_batching", "sbci_server_destroy", "sbci_solve_batch", "sbci_batch_profile",
            "sbci_batch_profile_read", "sbci_batch_classes", "sbci_last_error", "sbci_destroy"]
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.sbci_solve.argtypes = [P, I, C.POINTER(sbci_params), P, P, P, P]
     lib.sbci_trace.argtypes = [P, C.POINTER(sbci_trace_record), I, C.POINTER(I)]
     lib.sbci_davidson.argtypes = [P, I, C.POINTER(sbci_params), I, P, P, P, C.POINTER(LL)]
+    lib.sbci_solve_sbci2.argtypes = [P, I, C.POINTER(sbci_params), I, P, P, P]
     lib.sbci_sigma_noalloc.argtypes = [P, P, P, P]
     lib.sbci_server_create.argtypes = [C.POINTER(P), C.c_size_t, I]
     lib.sbci_server_submit.argtypes = [P, I, I, I, P, P, D, I, C.POINTER(sbci_params), C.POINTER(LL)]
@@ -271,6 +272,18 @@ class Context:
         st = self._lib.sbci_solve(self._h, int(k), C.byref(p) if p is not None else None, pc,
                                   E.ctypes.data_as(C.c_void_p),
                                   V.ctypes.data_as(C.c_void_p) if V is not None else None, R)
+        _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
+        self._k = k
+        return E, V, list(R), st
+
+    def solve_sbci2(self, k, p: sbci_params | None = None, max_cycle2: int = 0, want_vectors=False):
+        """SBCI2 (sbci_solve_sbci2): pairs of states, the last one by SBCI1."""
+        E = np.zeros(k)
+        V = np.zeros((k, self.ndet)) if want_vectors else None
+        R = (sbci_report * k)()
+        st = self._lib.sbci_solve_sbci2(self._h, int(k), C.byref(p) if p is not None else None, int(max_cycle2),
+                                        E.ctypes.data_as(C.c_void_p),
+                                        V.ctypes.data_as(C.c_void_p) if V is not None else None, R)
         _check(st, allow=(SBCI_ERR_NOT_CONVERGED,))
         self._k = k
         return E, V, list(R), st

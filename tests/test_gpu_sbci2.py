@@ -1,0 +1,134 @@
+"""GPU SBCI2 (sbci_solve_sbci2) against the oracle SBCI2, exact eigen-solvers
+and GPU SBCI1.
+
+Tolerances: energies within 1e-8 hartree of the exact values and of the oracle
+(the FP64 target); pair-step Ritz energies within 1e-9 of the oracle's while
+both runs take the same decisions (restart causes, convergence).  Where two
+Ritz values of a step coincide (a degenerate pair), the two eigen-solvers may
+return different rotations of that pair and the runs then part ways; energies
+are compared as sets.
+"""
+import numpy as np
+import pytest
+
+from oracle import sbci as osb
+from oracle import sbci2 as osb2
+from oracle import slater_condon as sc
+
+from gpu_common import make_integrals, oracle_sigma, require_lib
+
+pytestmark = pytest.mark.gpu
+
+EVENTS = {"": 0, "converged": 1, "restart:a": 2, "restart:b": 3, "restart:c": 4, "restart:max": 5, "undef": 8}
+
+
+def _oracle(key, k, **kw):
+    I = make_integrals(key)
+    ora = oracle_sigma(key)
+    D = sc.diagonal_by_occupation(I.h1, I.eri, I.nalpha, I.nbeta)
+    run = osb2.SBCI2(ora.apply, D, (ora.Na, ora.Nb), osb.SBCIParams(**kw))
+    res = run.solve(k)
+    return run, res
+
+
+def _sector_eigs(H, n):
+    cols = []
+    for a in range(n):
+        for b in range(a, n):
+            v = np.zeros((n, n))
+            if a == b:
+                v[a, a] = 1.0
+            else:
+                v[a, b] = v[b, a] = 1.0 / np.sqrt(2.0)
+            cols.append(v.reshape(-1))
+    B = np.column_stack(cols)
+    return np.linalg.eigvalsh(B.T @ H @ B)
+
+
+def _pair_trace_parity(gpu_trace, ora_trace):
+    """Leading pair steps whose Ritz energy agrees within 1e-9 and whose event
+    is the same.  Late steps can part by rounding: the canonical
+    orthogonalisation keeps overlap eigenvalues down to 1e-14 and amplifies
+    rounding-order differences by up to s^-1/2."""
+    n = 0
+    for rg, ro in zip(gpu_trace, ora_trace):
+        if rg.state != ro.state or abs(rg.energy - ro.energies[0]) >= 1e-9 or rg.event != EVENTS[ro.event]:
+            break
+        n += 1
+    return n
+
+
+@pytest.mark.parametrize("sector", [0, 1])
+def test_h6_four_states_against_oracle(sector):
+    sbci = require_lib()
+    key = ("chain", 6, 1.0)
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    E, V, R, st = ctx.solve_sbci2(4, sbci.params(sector=sector), want_vectors=True)
+    assert st == sbci.SBCI_OK and all(r.converged for r in R)
+    run, res = _oracle(key, 4, sector=sector)
+    Eo = np.array([r.energy for r in res]) + I.e_core
+    assert np.abs(np.sort(E) - np.sort(Eo)).max() < 1e-8
+    H = sc.dense_hamiltonian(I.h1, I.eri, 3, 3)
+    w = (np.linalg.eigvalsh(H) if sector == 0 else _sector_eigs(H, 20))[:4] + I.e_core
+    assert np.abs(np.sort(E) - w).max() < 1e-8
+    # stored states orthonormal, each an eigenvector to the residual threshold
+    assert np.abs(V @ V.T - np.eye(4)).max() < 1e-7
+    for a in range(4):
+        assert np.linalg.norm(H @ V[a] - (E[a] - I.e_core) * V[a]) < 1e-4
+    tr = ctx.trace()
+    assert {r.state for r in tr} == {0, 1, 2, 3}
+    if sector == 1:
+        # (in sector 0 the two start vectors of H6 are degenerate, and the two
+        # eigen-solvers return different rotations of them: energies only)
+        assert _pair_trace_parity(tr, run.trace) >= 20
+
+
+def test_h8_sector_three_states():
+    sbci = require_lib()
+    key = ("chain", 8, 1.3)
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    p = sbci.params(sector=1)
+    E, _, R, st = ctx.solve_sbci2(3, p)
+    assert st == sbci.SBCI_OK
+    run, res = _oracle(key, 3, sector=1)
+    Eo = np.sort([r.energy for r in res]) + I.e_core
+    assert np.abs(np.sort(E) - Eo).max() < 1e-8
+    Es, _, _, st1 = ctx.solve(3, p)
+    assert st1 == sbci.SBCI_OK
+    assert np.abs(np.sort(E) - np.sort(Es)).max() < 1e-8
+
+
+def test_h10_four_states_same_set_as_sbci1():
+    """The H10 workload (1.2 A, four singlet-sector states) by SBCI2 and SBCI1."""
+    sbci = require_lib()
+    key = ("chain", 10, 1.2)
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    p = sbci.params(sector=1)
+    E, V, R, st = ctx.solve_sbci2(4, p, want_vectors=True)
+    assert st == sbci.SBCI_OK and all(r.converged for r in R)
+    Es, _, _, st1 = ctx.solve(4, p)
+    assert np.abs(np.sort(E) - np.sort(Es)).max() < 1e-8
+    S = ctx.sigma(V, prec=sbci.SBCI_FP64)
+    res = np.linalg.norm(S.reshape(4, -1) - (E - I.e_core)[:, None] * V, axis=1)
+    assert res.max() < 1e-4
+    for a in range(4):
+        m = V[a].reshape(252, 252)
+        assert np.abs(m - m.T).max() < 1e-10
+
+
+def test_one_state_is_sbci1_and_bad_arguments():
+    sbci = require_lib()
+    key = ("chain", 6, 1.0)
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    E, _, R, st = ctx.solve_sbci2(1, sbci.params())
+    H = sc.dense_hamiltonian(I.h1, I.eri, 3, 3)
+    assert st == sbci.SBCI_OK and abs(E[0] - (np.linalg.eigvalsh(H)[0] + I.e_core)) < 1e-8
+    assert all(r.state == 0 for r in ctx.trace())
+    for kw, mc in [(dict(prec=sbci.SBCI_TF32X3), 0), (dict(), -1), (dict(start_noise=0.1), 0)]:
+        with pytest.raises(sbci.SbciError) as e:
+            ctx.solve_sbci2(2, sbci.params(**kw), max_cycle2=mc)
+        assert e.value.status == sbci.SBCI_ERR_INVALID
