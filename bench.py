@@ -181,6 +181,24 @@ def oracle_solve_time(I, nstates, max_steps=None):
     return time.perf_counter() - t0, run.n_sigma, done
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest of every rank's x (the job ends when its slowest rank does);
+    x itself with one rank."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs the same independent replicas)."""
+    return world * units_per_rank / seconds_max
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -273,12 +291,8 @@ def run_gb300(args, rank, world, local_rank):
     clocks = sampler.stop()
     stats = ctx.profile_read()
     launches = sum(v[0] for v in stats.values()) if B == 1 else one_solve.launches
-    t_max = t_ms
-    if dist:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * B * args.steps / (t_max / 1000.0)
+    t_max = max_over_ranks(t_ms, dist)
+    value = whole_job_rate(world, B * args.steps, t_max / 1000.0)
     # ---------------- one solve alone (latency), same event timing
     single = None
     if B > 1:
@@ -390,8 +404,8 @@ def run_gb300(args, rank, world, local_rank):
             for c2 in cs:
                 c2.close()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        e2e = {"value": B * args.steps / te, "unit": "solves/s",
+        te = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": whole_job_rate(world, B * args.steps, te), "unit": "solves/s",
                "h2d_bytes_per_step": int(B * (h1.nbytes + eri.nbytes)),
                "d2h_bytes_per_step": int(d2h)}
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
