@@ -362,6 +362,23 @@ def run_gb300(args, rank, world, local_rank):
             roof = {"bound": "hbm", **hbm, "other_ceiling": {"bound": "tensor", **tensor}}
         else:
             roof = {"bound": "tensor", **tensor, "other_ceiling": {"bound": "hbm", **hbm}}
+    elif base == "sigma_gather_contract_os":
+        # FP64 contraction by exact BF16 slices: the HBM traffic it must move (G
+        # written in FP64, 8 B per pair, and c read, 8 B, per determinant) and the
+        # tensor work it executes (34 slice products of 2 Kp Np flops, Kp = Np = 64)
+        bytes_alg = float(8 * npair + 8) * ndet * units
+        xflops = 34.0 * 2 * 64 * 64 * ndet * units
+        tpeak = pk.get("bf16_tflops", 1900.0)
+        hbm = {"achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": bytes_alg / avg_s / 1e9 / pk["hbm_gbs"], "algorithmic_per_launch": bytes_alg,
+               "peak_kind": pk_kind, "algorithmic_note": f"{8 * npair + 8} B per determinant (FP64 G write + c read)"}
+        tensor = {"achieved": xflops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                  "frac": xflops / avg_s / 1e12 / tpeak, "algorithmic_per_launch": xflops,
+                  "peak_kind": f"{pk_kind} bf16; executed slice products (34 of 2 x 64 x 64 flops per determinant)"}
+        if bytes_alg / (pk["hbm_gbs"] * 1e9) >= xflops / (tpeak * 1e12):
+            roof = {"bound": "hbm", **hbm, "other_ceiling": {"bound": "tensor", **tensor}}
+        else:
+            roof = {"bound": "tensor", **tensor, "other_ceiling": {"bound": "hbm", **hbm}}
     elif base == "sigma_gather_contract" and args.prec == "fp64":
         peak = 4.0 * 152 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA per clock per SM (1.25 TF/s at 2.07 GHz)
         roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",

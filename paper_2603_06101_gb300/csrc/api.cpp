@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <queue>
@@ -58,11 +59,12 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
-                                       "davidson_dots", "davidson_combine", "davidson_precond"};
+                                       "davidson_dots", "davidson_combine", "davidson_precond",
+                                       "sigma_gather_contract_os"};
 
 struct Prof {
   bool on = false;
@@ -113,6 +115,9 @@ struct sbci_ctx {
   float *d_Wf = nullptr;
   float *d_cf = nullptr;      // FP32 copy of a plain sigma's input (tensor-core mode)
   uint32_t *d_Wtc = nullptr;  // TF32 hi/lo operand B of the tensor-core sigma (nullptr: unsupported)
+  void *d_Wos = nullptr;      // BF16 integer slices of W for the FP64 tensor-core contraction (nullptr: off)
+  int *d_fexp = nullptr;      // their per-output-pair exponents
+  int os_grid = 0;
   double *d_diag = nullptr;
   double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
   void *d_G = nullptr;
@@ -237,6 +242,10 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
     CK(launch_to_float(in, c->d_cf, c->ndet, c->stream));
     a.cf = c->d_cf;
     RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
+  } else if (prec == SBCI_FP64 && c->d_Wos) {
+    RET(timed(c, K_GCOS, [&] {
+      return launch_gather_contract_os(a, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
+    }));
   } else {
     RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
   }
@@ -383,6 +392,10 @@ sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool tim
   RET(L(K_PROJ, [&] { return launch_project_ctl(st, g, c->stream); }));
   if (prec == SBCI_TF32X3)
     RET(L(K_GCTC, [&] { return launch_gather_contract_tc(sa, c->d_status, c->tc_grid, c->stream); }));
+  else if (prec == SBCI_FP64 && c->d_Wos)
+    RET(L(K_GCOS, [&] {
+      return launch_gather_contract_os(sa, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
+    }));
   else
     RET(L(K_GC, [&] { return launch_gather_contract(sa, p32, c->stream); }));
   RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
@@ -435,7 +448,7 @@ sbci_status run_until_halt(sbci_ctx *c) {
     Prof &pf = c->prof;
     pf.launches[K_UPD] += bodies;
     pf.launches[K_PROJ] += bodies;
-    pf.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
+    pf.launches[prec == SBCI_TF32X3 ? K_GCTC : (prec == SBCI_FP64 && c->d_Wos ? K_GCOS : K_GC)] += bodies;
     pf.launches[K_SC] += bodies;
     if (use_symfin(c)) pf.launches[K_SF] += bodies;
     s.h_ctl->iters = 0;
@@ -1761,7 +1774,7 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
   if (own_graph) {  // the solve's own graph ran four kernels per body
     c->prof.launches[K_UPD] += bodies;
     c->prof.launches[K_PROJ] += bodies;
-    c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : K_GC] += bodies;
+    c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : (prec == SBCI_FP64 && c->d_Wos ? K_GCOS : K_GC)] += bodies;
     c->prof.launches[K_SC] += bodies;
     if (use_symfin(c)) c->prof.launches[K_SF] += bodies;
   }
@@ -1870,8 +1883,9 @@ void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_cf, c->d_diag, c->d_ea, c->d_eb,
-                  c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in, c->d_tmp_out};
+  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wos, c->d_fexp, c->d_cf,
+                  c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
+                  c->d_tmp_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
@@ -2048,6 +2062,18 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
     if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) {
       TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
+    }
+  }
+  {
+    // FP64 contraction on the tensor cores by exact slices where the operands
+    // fit (npair <= 55); SBCI_FP64_CONTRACTION=dfma keeps the FP64 FMA kernel
+    const char *mode = std::getenv("SBCI_FP64_CONTRACTION");
+    const bool dfma = mode && std::strcmp(mode, "dfma") == 0;
+    if (!dfma && os_supported(c->npair) && prepare_os_kernel(c->npair) == cudaSuccess) {
+      TRY(cuda_ok(cudaMalloc(&c->d_Wos, os_W_bytes()), "cudaMalloc"));
+      TRY(cuda_ok(cudaMalloc((void **)&c->d_fexp, sizeof(int) * 64), "cudaMalloc"));
+      TRY(cuda_ok(launch_split_W_os(c->d_W, c->npair, c->d_Wos, c->d_fexp, c->stream), "slice kernel"));
+      c->os_grid = os_grid(c->ndet, c->nsm);
     }
   }
   TRY(cuda_ok(launch_diagonal(c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_mask_b, c->Na, c->Nb, n,

@@ -53,7 +53,7 @@ namespace sbci {
 
 // Largest dynamic shared memory a launch of kernel f may opt into on the
 // current device: the per-block opt-in limit minus f's static shared memory.
-static cudaError_t max_dynamic_smem(const void *f, int *bytes) {
+cudaError_t max_dynamic_smem(const void *f, int *bytes) {
   int dev = 0, optin = 0;
   cudaFuncAttributes fa{};
   cudaError_t e = cudaGetDevice(&dev);

@@ -195,6 +195,21 @@ cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s);
 // r[I] = SplitMix64 vector of (seed, alpha) in [-1, 1)
 cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s);
 
+// Largest dynamic shared memory a launch of kernel f may opt into on the
+// current device (the opt-in limit minus f's static shared memory).
+cudaError_t max_dynamic_smem(const void *f, int *bytes);
+
+// FP64 gather + contract on the tensor cores by exact BF16 integer slices
+// (kernels_os.cu), for npair <= 55.  W slices: os_W_bytes() bytes plus 64
+// column exponents, made once per context by launch_split_W_os.
+bool os_supported(int npair);
+size_t os_W_bytes();
+cudaError_t launch_split_W_os(const double *W, int npair, void *out, int *fexp, cudaStream_t s);
+cudaError_t prepare_os_kernel(int npair);
+int os_grid(long long ndet, int nsm);
+cudaError_t launch_gather_contract_os(const SigmaArgs &a, const void *Wos, const int *fexp, int *status, int grid,
+                                      cudaStream_t s);
+
 // Kernels of the block Davidson-Liu solver and of the SBCI2 pair steps
 // (kernels_dav.cu).
 constexpr int kDavMaxSpace = 64;                  // subspace vectors
