@@ -94,17 +94,45 @@ __device__ __forceinline__ long long fixed56(double x, int emax) {
   return (b >> 63) ? -F : F;
 }
 
-// Balanced base-2^8 digits of F, most significant first.
+// Digits of F (|F| < 2^56) in base 2^8, most significant first: m_2..m_7 in
+// [-128, 127] are the six low bytes of F + 0x808080808080 less 128 each, m_1
+// (|m_1| <= 256) the rest, so that F = sum_s m_s 2^(56 - 8s).
 __device__ __forceinline__ void digits(long long F, int (&m)[kOsSlices]) {
-#pragma unroll
-  for (int s = 0; s < kOsSlices; ++s) {
-    const int sh = 56 - kOsBeta * (s + 1);
-    long long d;
-    if (sh > 0) d = (F + (1LL << (sh - 1))) >> sh;
-    else d = F;
-    F -= d * (1LL << sh);
-    m[s] = (int)d;
+  const long long G = F + 0x808080808080LL;
+  m[0] = (int)(G >> 48);
+  const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
+  m[1] = (int)((hi >> 8) & 0xFF) - 128;
+  m[2] = (int)(hi & 0xFF) - 128;
+  m[3] = (int)(lo >> 24) - 128;
+  m[4] = (int)((lo >> 16) & 0xFF) - 128;
+  m[5] = (int)((lo >> 8) & 0xFF) - 128;
+  m[6] = (int)(lo & 0xFF) - 128;
+}
+
+// BF16 bits of a small integer (|d| <= 256, exact in FP32 and in BF16): the
+// FP32 value through the 1.5 * 2^23 bias, then its upper half.
+__device__ __forceinline__ uint32_t bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// v * 2^k as FP64, rounded to nearest even, by integer operations (v != 0,
+// |v| < 2^63; the result in the normal range, else through ldexp).
+__device__ __forceinline__ double scaled_ll_to_double(long long v, int k) {
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;  // leading bit at 63
+  unsigned long long m = a >> 11;
+  const unsigned long long rem = a & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ++m;
+  int E = 1023 + (63 - lz) + k;
+  if (m == (1ull << 53)) {
+    m >>= 1;
+    ++E;
   }
+  if (E <= 0 || E >= 2047) return ldexp((double)v, k);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 // Operand B: the slices of W (K-major, output pair P = row n, input pair q = k)
@@ -129,6 +157,7 @@ struct OsSmem {
   __nv_bfloat16 *B;  // [7][Np x Kp]
   double *D;         // [128][npair]
   int *eI;           // [128] biased row exponents
+  int *eHalf;        // [2][128] exponents of the row halves
   int *fP;           // [Np]
   uint64_t *bar;
   uint32_t *tmem_slot;
@@ -143,7 +172,8 @@ __global__ void __launch_bounds__(kOsThreads, 1)
   sm.B = sm.A + kOsSlices * kTcM * kOsKp;
   sm.D = reinterpret_cast<double *>(sm.B + kOsSlices * kOsNp * kOsKp);
   sm.eI = reinterpret_cast<int *>(sm.D + kTcM * npair);
-  sm.fP = sm.eI + kTcM;
+  sm.eHalf = sm.eI + kTcM;
+  sm.fP = sm.eHalf + 2 * kTcM;
   sm.bar = reinterpret_cast<uint64_t *>(sm.fP + kOsNp);
   sm.tmem_slot = reinterpret_cast<uint32_t *>(sm.bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -187,36 +217,76 @@ __global__ void __launch_bounds__(kOsThreads, 1)
   uint32_t phase = 0;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // 1. gather: thread r < 128 builds row r of D in FP64 (both spins)
-    if (tid < kTcM) {
-      const int r = tid;
-      double *row = sm.D + (size_t)r * npair;
+    // 1. gather: thread r < 128 builds the alpha part of row r of D in FP64,
+    //    thread 128 + r the beta part in the A-slice area (free until the
+    //    slices are written; the previous tile's MMAs have completed)
+    {
+      const int r = tid & (kTcM - 1), h = tid >> 7;
+      double *row = h ? reinterpret_cast<double *>(sm.A) + (size_t)r * npair : sm.D + (size_t)r * npair;
       for (int q = 0; q < npair; ++q) row[q] = 0.0;
       const long long I = tile * kTcM + r;
       if (I < a.ndet) {
         int ia, ib;
         split_det(I, a.nb, ia, ib);
-        const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-        const double *ccol = cin + ib;
-        for_links<8, double>(
-            la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
-            [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
-        const uint32_t *lb = a.link_bT + ib;
-        const double *crow = cin + (size_t)ia * a.nb;
-        for_links<8, double>(
-            lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-            [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
+        if (h == 0) {
+          const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+          const double *ccol = cin + ib;
+          for_links<8, double>(
+              la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+              [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
+        } else {
+          const uint32_t *lb = a.link_bT + ib;
+          const double *crow = cin + (size_t)ia * a.nb;
+          for_links<8, double>(
+              lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+              [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
+        }
       }
-      // 2. the row exponent and the seven digit slices of the row
+    }
+    __syncthreads();
+    // D = alpha part + beta part (alpha first, as the FP64 SIMT kernel adds
+    // them); two threads per row, each half of the columns
+    {
+      const int r = tid & (kTcM - 1), h = tid >> 7;
+      const int half = ((npair + 15) / 16) * 8;  // split at a multiple of 8 columns
+      const int q0 = h ? half : 0, q1 = h ? npair : min(half, npair);
+      double *row = sm.D + (size_t)r * npair;
+      const double *rb = reinterpret_cast<const double *>(sm.A) + (size_t)r * npair;
       int emax = 0;
-      for (int q = 0; q < npair; ++q) emax = max(emax, bexp(row[q]));
-      sm.eI[r] = emax;
-      for (int q = 0; q < npair; ++q) {
-        int m[kOsSlices] = {0, 0, 0, 0, 0, 0, 0};
-        if (emax > 0) digits(fixed56(row[q], emax), m);
+      for (int q = q0; q < q1; ++q) {
+        const double d = row[q] + rb[q];
+        row[q] = d;
+        emax = max(emax, bexp(d));
+      }
+      sm.eHalf[h * kTcM + r] = emax;
+    }
+    __syncthreads();
+    // 2. the seven digit slices: each thread 8 consecutive columns of a row at
+    //    a time (one core-matrix row: a 16-byte store per slice), up to the
+    //    padded width (the beta staging overwrote the padding columns)
+    {
+      const int r = tid & (kTcM - 1), h = tid >> 7;
+      const int half = ((npair + 15) / 16) * 8;
+      const int q0 = h ? half : 0, q_end = h ? kOsKp : half, q1 = npair;
+      const int emax = max(sm.eHalf[r], sm.eHalf[kTcM + r]);
+      if (h == 0) sm.eI[r] = emax;
+      const double *row = sm.D + (size_t)r * npair;
+      for (int qc = q0; qc < q_end; qc += 8) {
+        uint32_t w[kOsSlices][4];
 #pragma unroll
-        for (int s = 0; s < kOsSlices; ++s)
-          sm.A[(size_t)s * kTcM * kOsKp + opnd16(r, q, kOsKp)] = __float2bfloat16_rn((float)m[s]);
+        for (int sl = 0; sl < kOsSlices; ++sl) w[sl][0] = w[sl][1] = w[sl][2] = w[sl][3] = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          int m[kOsSlices] = {0, 0, 0, 0, 0, 0, 0};
+          if (qc + j < q1 && emax > 0) digits(fixed56(row[qc + j], emax), m);
+#pragma unroll
+          for (int sl = 0; sl < kOsSlices; ++sl) w[sl][j >> 1] |= bf16_of_int(m[sl]) << ((j & 1) * 16);
+        }
+        const int off = opnd16(r, qc, kOsKp);  // 8-element aligned: a 16-byte core-matrix row
+#pragma unroll
+        for (int sl = 0; sl < kOsSlices; ++sl)
+          *reinterpret_cast<uint4 *>(sm.A + (size_t)sl * kTcM * kOsKp + off) =
+              make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
       }
     }
     fence_async_smem();
@@ -282,12 +352,8 @@ __global__ void __launch_bounds__(kOsThreads, 1)
             }
             double out = 0.0;
             const int fP = sm.fP[P];
-            if (acc != 0 && eI > 0 && fP > 0) {
-              // value = acc 2^(e_I + f_P - 56) with e = biased - 1022
-              const double g = (double)acc;
-              const int k = (eI - 1022) + (fP - 1022) - 56;
-              out = ldexp(g, k);
-            }
+            if (acc != 0 && eI > 0 && fP > 0)  // acc 2^(e_I + f_P - 56), e = biased - 1022
+              out = scaled_ll_to_double(acc, (eI - 1022) + (fP - 1022) - 56);
             G[(size_t)P * a.ndet + I] = out;
           }
         }
@@ -310,7 +376,7 @@ __global__ void __launch_bounds__(kOsThreads, 1)
 
 size_t os_smem_bytes(int npair) {
   return (size_t)kOsSlices * kTcM * kOsKp * 2 + (size_t)kOsSlices * kOsNp * kOsKp * 2 +
-         (size_t)kTcM * npair * 8 + (size_t)(kTcM + kOsNp) * 4 + 16;
+         (size_t)kTcM * npair * 8 + (size_t)(3 * kTcM + kOsNp) * 4 + 16;
 }
 
 }  // namespace
