@@ -19,7 +19,8 @@
 //    2^(e_I + f_P - 8L) and one accumulator; the largest level sum (L = 8:
 //    two pairs with a first digit, five without) stays below
 //    55 (2 * 2^15 + 5 * 2^14) < 2^23, still exact.  Levels 2..9 are kept (34
-//    of the 49 pairs); the dropped levels weigh below 2^-64 of the first.
+//    of the 49 pairs); the dropped levels weigh about 2^-56 of
+//    max|W| max|D|, the rounding of the inputs at most 2^-55 per term.
 //  * The epilogue adds the eight levels as 64-bit integers (shifted to a
 //    common scale 2^(e_I + f_P - 56)), converts once to FP64 and sets the
 //    exponent: besides the 56-bit inputs, that conversion is the only
