@@ -1114,53 +1114,134 @@ sbci_status davidson_run(sbci_ctx *c, int k, const sbci_params &p, int max_space
       RET(dav_full_T(d, T));
       ++n_collapse;
     }
-    // D5: corrections, one at a time against the growing subspace
+    // D5 in block form (the same vectors as one correction at a time in exact
+    // arithmetic): all corrections, projected twice against V, then
+    // orthonormalised among themselves in order (drop rule of D5) by classical
+    // Gram-Schmidt on their Gram matrix, twice; one dot-product batch and one
+    // combination per pass instead of a host round trip per correction
     int added = 0;
-    for (int a : unconv) {
-      if (n_sigma >= max_sigma) break;
-      const int ts = R[a];
-      double *t = d.vb[ts];
-      RET(timed(c, K_DAVP, [&] { return launch_dav_precond(t, t, c->d_diag, theta[a], p.guard, N, c->nsm, c->stream); }));
+    std::vector<int> ca;  // states whose correction is formed
+    for (int a : unconv)
+      if (n_sigma + (long long)ca.size() < max_sigma) ca.push_back(a);
+    const int nu = (int)ca.size();
+    std::vector<double *> tv(nu);
+    for (int j = 0; j < nu; ++j) {
+      tv[j] = d.vb[R[ca[j]]];
+      double *t = tv[j];
+      const double sh = theta[ca[j]];
+      RET(timed(c, K_DAVP, [&] { return launch_dav_precond(t, t, c->d_diag, sh, p.guard, N, c->nsm, c->stream); }));
       if (p.sector) RET(timed(c, K_DAVP, [&] { return launch_symmetrize(t, c->Na, c->stream); }));
-      RET(dav_dots(d, {t}, {t}, r));
-      const double n0 = r[0];
-      for (int pass = 0; pass < 2; ++pass) {
-        std::vector<const double *> u, v, in{t};
-        for (int i = 0; i < m; ++i) {
-          u.push_back(d.vb[d.V[i]]);
-          v.push_back(t);
-          in.push_back(d.vb[d.V[i]]);
-        }
+    }
+    std::vector<double> n0(nu, 0.0);
+    if (nu > 0) {
+      for (int pass = 0; pass < 2; ++pass) {  // T <- T - V (V^T T)
+        std::vector<const double *> u, v;
+        for (int j = 0; j < nu; ++j)
+          for (int i = 0; i < m; ++i) {
+            u.push_back(d.vb[d.V[i]]);
+            v.push_back(tv[j]);
+          }
+        if (pass == 0)
+          for (int j = 0; j < nu; ++j) {
+            u.push_back(tv[j]);
+            v.push_back(tv[j]);
+          }
         RET(dav_dots(d, u, v, r));
-        std::vector<double> co(1 + m);
-        co[0] = 1.0;
-        for (int i = 0; i < m; ++i) co[1 + i] = -r[i];
-        RET(dav_combine(d, {t}, in, co));
+        if (pass == 0)
+          for (int j = 0; j < nu; ++j) n0[j] = r[(size_t)nu * m + j];
+        std::vector<const double *> in(tv.begin(), tv.end());
+        for (int i = 0; i < m; ++i) in.push_back(d.vb[d.V[i]]);
+        std::vector<double> co((size_t)(nu + m) * nu, 0.0);
+        for (int j = 0; j < nu; ++j) {
+          co[(size_t)j * nu + j] = 1.0;
+          for (int i = 0; i < m; ++i) co[(size_t)(nu + i) * nu + j] = -r[(size_t)j * m + i];
+        }
+        RET(dav_combine(d, tv, in, co));
       }
-      RET(dav_dots(d, {t}, {t}, r));
-      const double nt = r[0];
-      if (!(nt > 0.0 && nt >= p.gs_tol * n0)) continue;
-      RET(dav_combine(d, {t}, {t}, {1.0 / std::sqrt(nt)}));
-      RET(run_sigma(c, t, d.ab[ts], SBCI_FP64));
+    }
+    // among themselves: coefficients Q = T C (C upper triangular over the
+    // kept columns), from the Gram matrix G = T^T T, twice
+    std::vector<int> keep;
+    for (int j = 0; j < nu; ++j) keep.push_back(j);
+    for (int pass = 0; pass < 2 && !keep.empty(); ++pass) {
+      const int nk = (int)keep.size();
+      std::vector<const double *> u, v;
+      for (int a2 = 0; a2 < nk; ++a2)
+        for (int b2 = 0; b2 <= a2; ++b2) {
+          u.push_back(tv[keep[a2]]);
+          v.push_back(tv[keep[b2]]);
+        }
+      RET(dav_dots(d, u, v, r));
+      std::vector<double> G((size_t)nk * nk);
+      size_t qi = 0;
+      for (int a2 = 0; a2 < nk; ++a2)
+        for (int b2 = 0; b2 <= a2; ++b2, ++qi) G[(size_t)a2 * nk + b2] = G[(size_t)b2 * nk + a2] = r[qi];
+      std::vector<std::vector<double>> Cq;  // coefficient vectors (length nk) of the kept q's
+      std::vector<int> kept_next;
+      for (int a2 = 0; a2 < nk; ++a2) {
+        std::vector<double> uvec(nk, 0.0);
+        uvec[a2] = 1.0;
+        std::vector<double> proj(Cq.size());
+        for (size_t b2 = 0; b2 < Cq.size(); ++b2) {  // q_b . t_a from the original t_a
+          double acc = 0.0;
+          for (int c2 = 0; c2 < nk; ++c2) acc += Cq[b2][c2] * G[(size_t)c2 * nk + a2];
+          proj[b2] = acc;
+        }
+        for (size_t b2 = 0; b2 < Cq.size(); ++b2)
+          for (int c2 = 0; c2 < nk; ++c2) uvec[c2] -= proj[b2] * Cq[b2][c2];
+        double nrm2 = 0.0;
+        for (int c2 = 0; c2 < nk; ++c2)
+          for (int e2 = 0; e2 < nk; ++e2) nrm2 += uvec[c2] * G[(size_t)c2 * nk + e2] * uvec[e2];
+        const double ref = pass == 0 ? n0[keep[a2]] : 1.0;
+        if (!(nrm2 > 0.0 && nrm2 >= p.gs_tol * ref)) continue;
+        const double f = 1.0 / std::sqrt(nrm2);
+        for (double &x : uvec) x *= f;
+        Cq.push_back(uvec);
+        kept_next.push_back(keep[a2]);
+      }
+      // q's into the slots of the kept corrections, in place
+      const int nq = (int)Cq.size();
+      if (nq > 0) {
+        std::vector<double *> out;
+        std::vector<const double *> in;
+        for (int a2 = 0; a2 < nq; ++a2) out.push_back(tv[kept_next[a2]]);
+        for (int c2 = 0; c2 < nk; ++c2) in.push_back(tv[keep[c2]]);
+        std::vector<double> co((size_t)nk * nq, 0.0);
+        for (int a2 = 0; a2 < nq; ++a2)
+          for (int c2 = 0; c2 < nk; ++c2) co[(size_t)c2 * nq + a2] = Cq[a2][c2];
+        RET(dav_combine(d, out, in, co));
+      }
+      keep = kept_next;
+    }
+    // the kept corrections join V with their H-images
+    const int m_old = m;
+    for (int j : keep) {
+      const int ts = R[ca[j]];
+      RET(run_sigma(c, d.vb[ts], d.ab[ts], SBCI_FP64));
       ++n_sigma;
       d.V.push_back(ts);
-      R[a] = -1;
+      R[ca[j]] = -1;
       ++m;
       ++added;
-      // new row and column of T
-      const int j = m - 1;
+    }
+    if (added > 0) {  // new rows and columns of T
       std::vector<const double *> u, v;
-      for (int i = 0; i <= j; ++i) {
-        u.push_back(d.vb[d.V[i]]);
-        v.push_back(d.ab[ts]);
-      }
-      for (int i = 0; i < j; ++i) {
-        u.push_back(t);
-        v.push_back(d.ab[d.V[i]]);
-      }
+      for (int j = m_old; j < m; ++j)
+        for (int i = 0; i < m; ++i) {
+          u.push_back(d.vb[d.V[i]]);
+          v.push_back(d.ab[d.V[j]]);
+        }
+      for (int j = m_old; j < m; ++j)
+        for (int i = 0; i < m_old; ++i) {
+          u.push_back(d.vb[d.V[j]]);
+          v.push_back(d.ab[d.V[i]]);
+        }
       RET(dav_dots(d, u, v, r));
-      for (int i = 0; i <= j; ++i) T[(size_t)i * kDavMaxSpace + j] = r[i];
-      for (int i = 0; i < j; ++i) T[(size_t)j * kDavMaxSpace + i] = r[j + 1 + i];
+      size_t qi = 0;
+      for (int j = m_old; j < m; ++j)
+        for (int i = 0; i < m; ++i) T[(size_t)i * kDavMaxSpace + j] = r[qi++];
+      for (int j = m_old; j < m; ++j)
+        for (int i = 0; i < m_old; ++i) T[(size_t)j * kDavMaxSpace + i] = r[qi++];
     }
     for (int a = 0; a < k; ++a)
       if (R[a] >= 0) {
