@@ -50,7 +50,13 @@ typedef enum {
 
 /* Arithmetic of the two-electron contraction inside sigma. */
 typedef enum {
-  SBCI_FP64 = 0,   /* FP64 gather, FP64 contraction (DFMA), FP64 scatter */
+  SBCI_FP64 = 0,   /* FP64 gather, FP64 contraction, FP64 scatter.  For
+                      npair <= 55 the contraction runs on the tensor cores by
+                      exact BF16 integer slices of 56-bit scaled inputs (error-
+                      free splitting, Ozaki, Ogita & Oishi 2012; FP64 accuracy);
+                      else FP64 FMAs.  The environment variable
+                      SBCI_FP64_CONTRACTION=dfma, read when a context is
+                      created, selects the FMAs for every size. */
   SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
   SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores, FP32 accumulation */
   SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */
