@@ -56,7 +56,12 @@ typedef enum {
                       free splitting, Ozaki, Ogita & Oishi 2012; FP64 accuracy);
                       else FP64 FMAs.  The environment variable
                       SBCI_FP64_CONTRACTION=dfma, read when a context is
-                      created, selects the FMAs for every size. */
+                      created, selects the FMAs for every size.  With
+                      density-fitted integrals (W of rank r, 2r < 0.9 npair)
+                      and npair > 55, the FP64 FMA contraction uses the
+                      low-rank form W = U L U^T, 2 r npair instead of npair^2
+                      multiply-adds; SBCI_LOWRANK=0, read when a context is
+                      created, turns it off. */
   SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
   SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores, FP32 accumulation */
   SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */

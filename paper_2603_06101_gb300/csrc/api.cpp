@@ -28,6 +28,7 @@
 #include "../../include/sbci.h"
 #include "ctl.h"
 #include "batch.h"
+#include "lowrank.h"
 #include "sbci_internal.h"
 #include "step.h"
 
@@ -59,12 +60,12 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
                                        "davidson_dots", "davidson_combine", "davidson_precond",
-                                       "sigma_gather_contract_os"};
+                                       "sigma_gather_contract_os", "sigma_gather_contract_lr"};
 
 struct Prof {
   bool on = false;
@@ -118,6 +119,9 @@ struct sbci_ctx {
   void *d_Wos = nullptr;      // BF16 integer slices of W for the FP64 tensor-core contraction (nullptr: off)
   int *d_fexp = nullptr;      // their per-output-pair exponents
   int os_grid = 0;
+  // low-rank form W = U_r L_r U_r^T of the FP64 SIMT contraction (lowrank.h); 0: off
+  int lr_rank = 0;
+  void *d_lrUt64 = nullptr, *d_lrUL64 = nullptr;
   double *d_diag = nullptr;
   double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
   void *d_G = nullptr;
@@ -214,6 +218,27 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
   return SBCI_ERR_INVALID;
 }
 
+// The gather + contract kernel family of a sigma precision, and its launch.
+int gc_kid(const sbci_ctx *c, int prec) {
+  if (prec == SBCI_TF32X3) return K_GCTC;
+  if (prec == SBCI_FP64 && c->d_Wos) return K_GCOS;
+  if (prec == SBCI_FP64 && c->lr_rank > 0) return K_GCLR;
+  return K_GC;
+}
+
+cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
+  switch (gc_kid(c, prec)) {
+    case K_GCTC:
+      return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream);
+    case K_GCOS:
+      return launch_gather_contract_os(a, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
+    case K_GCLR:
+      return launch_gather_contract_lr(a, 0, c->d_lrUt64, c->d_lrUL64, c->lr_rank, c->stream);
+    default:
+      return launch_gather_contract(a, prec == SBCI_FP64 ? 0 : 1, c->stream);
+  }
+}
+
 sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   RET(check_prec(c, prec));
   RET(ensure_G(c, prec));
@@ -241,14 +266,8 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
     if (!c->d_cf) RET(dmalloc(&c->d_cf, (size_t)c->ndet));
     CK(launch_to_float(in, c->d_cf, c->ndet, c->stream));
     a.cf = c->d_cf;
-    RET(timed(c, K_GCTC, [&] { return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream); }));
-  } else if (prec == SBCI_FP64 && c->d_Wos) {
-    RET(timed(c, K_GCOS, [&] {
-      return launch_gather_contract_os(a, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
-    }));
-  } else {
-    RET(timed(c, K_GC, [&] { return launch_gather_contract(a, p32, c->stream); }));
   }
+  RET(timed(c, gc_kid(c, prec), [&] { return launch_gc(c, a, prec); }));
   RET(timed(c, K_SC, [&] { return launch_scatter(a, p32, c->stream); }));
   return SBCI_OK;
 }
@@ -390,14 +409,7 @@ sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool tim
   };
   RET(L(K_UPD, [&] { return launch_update_ctl(st, g, c->stream); }));
   RET(L(K_PROJ, [&] { return launch_project_ctl(st, g, c->stream); }));
-  if (prec == SBCI_TF32X3)
-    RET(L(K_GCTC, [&] { return launch_gather_contract_tc(sa, c->d_status, c->tc_grid, c->stream); }));
-  else if (prec == SBCI_FP64 && c->d_Wos)
-    RET(L(K_GCOS, [&] {
-      return launch_gather_contract_os(sa, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
-    }));
-  else
-    RET(L(K_GC, [&] { return launch_gather_contract(sa, p32, c->stream); }));
+  RET(L(gc_kid(c, prec), [&] { return launch_gc(c, sa, prec); }));
   RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
   if (sa.symA) RET(L(K_SF, [&] { return launch_symfin(sa, p32, c->stream); }));
   return SBCI_OK;
@@ -448,7 +460,7 @@ sbci_status run_until_halt(sbci_ctx *c) {
     Prof &pf = c->prof;
     pf.launches[K_UPD] += bodies;
     pf.launches[K_PROJ] += bodies;
-    pf.launches[prec == SBCI_TF32X3 ? K_GCTC : (prec == SBCI_FP64 && c->d_Wos ? K_GCOS : K_GC)] += bodies;
+    pf.launches[gc_kid(c, prec)] += bodies;
     pf.launches[K_SC] += bodies;
     if (use_symfin(c)) pf.launches[K_SF] += bodies;
     s.h_ctl->iters = 0;
@@ -1855,7 +1867,7 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
   if (own_graph) {  // the solve's own graph ran four kernels per body
     c->prof.launches[K_UPD] += bodies;
     c->prof.launches[K_PROJ] += bodies;
-    c->prof.launches[prec == SBCI_TF32X3 ? K_GCTC : (prec == SBCI_FP64 && c->d_Wos ? K_GCOS : K_GC)] += bodies;
+    c->prof.launches[gc_kid(c, prec)] += bodies;
     c->prof.launches[K_SC] += bodies;
     if (use_symfin(c)) c->prof.launches[K_SF] += bodies;
   }
@@ -1966,7 +1978,7 @@ void sbci_destroy(sbci_ctx *c) {
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wos, c->d_fexp, c->d_cf,
                   c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
-                  c->d_tmp_out};
+                  c->d_tmp_out, c->d_lrUt64, c->d_lrUL64};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
@@ -2143,6 +2155,67 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
     if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) {
       TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
+    }
+  }
+  // low-rank form of W for the FP64 SIMT contraction (lowrank.h): worth it when
+  // 2 r < 0.9 npair (density-fitted integrals), not for full-rank W.  A
+  // pivoted Cholesky of the PSD pair matrix (ij|kl) bounds the rank first
+  // (rank W <= rank (ij|kl) + 2), so full-rank spaces skip the eigen-solver.
+  auto eri_rank = [&](int np) {
+    std::vector<double> V((size_t)np * np), d(np);
+    for (int i = 0, P = 0; i < n; ++i)
+      for (int j = 0; j <= i; ++j, ++P)
+        for (int k = 0, Q = 0; k < n; ++k)
+          for (int l = 0; l <= k; ++l, ++Q) V[(size_t)P * np + Q] = E4(i, j, k, l);
+    double dmax = 0.0;
+    for (int P = 0; P < np; ++P) dmax = std::max(dmax, d[P] = V[(size_t)P * np + P]);
+    std::vector<double> L;  // columns of the factor, np each
+    std::vector<char> used(np, 0);
+    int r = 0;
+    while (r < np) {
+      int piv = -1;
+      double best = 1e-13 * dmax;
+      for (int P = 0; P < np; ++P)
+        if (!used[P] && d[P] > best) best = d[P], piv = P;
+      if (piv < 0) break;
+      used[piv] = 1;
+      const double s = std::sqrt(d[piv]);
+      std::vector<double> col(np);
+      for (int P = 0; P < np; ++P) {
+        double v = V[(size_t)P * np + piv];
+        for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + piv];
+        col[P] = v / s;
+      }
+      for (int P = 0; P < np; ++P) d[P] -= col[P] * col[P];
+      L.insert(L.end(), col.begin(), col.end());
+      ++r;
+    }
+    return r;
+  };
+  const char *lr_mode = std::getenv("SBCI_LOWRANK");  // "0": keep the full contraction
+  const bool lr_off = lr_mode && std::strcmp(lr_mode, "0") == 0;
+  if (!lr_off && c->npair > 55 && 2.0 * (eri_rank(c->npair) + 2) < 0.9 * c->npair) {
+    const int np = c->npair;
+    std::vector<double> Wsq((size_t)np * np), lam(np), U((size_t)np * np);
+    for (int P = 0; P < np; ++P)
+      for (int Q = 0; Q < np; ++Q) Wsq[(size_t)P * np + Q] = c->W_host[(size_t)P * np + Q];
+    jacobi_eigh(np, Wsq.data(), lam.data(), U.data());
+    double lmax = 0.0;
+    for (double l : lam) lmax = std::max(lmax, std::fabs(l));
+    std::vector<int> keep;
+    for (int k = 0; k < np; ++k)
+      if (std::fabs(lam[k]) > 1e-13 * lmax) keep.push_back(k);
+    const int r = (int)keep.size();
+    if (r >= 1 && 2.0 * r < 0.9 * np) {
+      std::vector<double> Ut((size_t)r * np), UL((size_t)np * r);
+      for (int k = 0; k < r; ++k)
+        for (int q = 0; q < np; ++q) {
+          Ut[(size_t)k * np + q] = U[(size_t)q * np + keep[k]];
+          UL[(size_t)q * r + k] = U[(size_t)q * np + keep[k]] * lam[keep[k]];
+        }
+      TRY(up(&c->d_lrUt64, Ut.data(), Ut.size() * 8));
+      TRY(up(&c->d_lrUL64, UL.data(), UL.size() * 8));
+      c->lr_rank = r;
     }
   }
   {

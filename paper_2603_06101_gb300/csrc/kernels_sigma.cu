@@ -16,6 +16,7 @@
 
 #include "ctl.h"
 #include "devreduce.cuh"
+#include "lowrank.h"
 #include "sbci_internal.h"
 
 namespace sbci {
@@ -89,6 +90,59 @@ __global__ void __launch_bounds__(kTile) k_gather_contract(SigmaArgs a) {
   }
 }
 
+// Phase 1 in the low-rank form of W (lowrank.h): t = U_r^T D into shared
+// memory after the D column, then G = (U_r L_r) t.  Same gather.
+template <typename AccT>
+__global__ void __launch_bounds__(kTile) k_gather_contract_lr(SigmaArgs a, const AccT *Ut, const AccT *UL, int r) {
+  extern __shared__ unsigned char smem_raw[];
+  AccT *sD = reinterpret_cast<AccT *>(smem_raw);  // [npair][kTile]
+  AccT *sT = sD + (size_t)a.npair * kTile;        // [r][kTile]
+  const int tid = threadIdx.x;
+  const double *cin = a.c;
+  const float *cinf = nullptr;
+  if (a.ctl) {
+    if (a.ctl->halt) return;
+    cin = a.ctl->zn;
+    if constexpr (sizeof(AccT) == 4) cinf = a.ctl->zf;
+  }
+  const long long ntiles = (a.ndet + kTile - 1) / kTile;
+  AccT *G = reinterpret_cast<AccT *>(a.G);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long I = tile * kTile + tid;
+    if (I >= a.ndet) continue;
+    if (cinf) simt_gather<AccT, float>(a, cinf, I, tid, sD);
+    else simt_gather<AccT, double>(a, cin, I, tid, sD);
+    for (int R0 = 0; R0 < r; R0 += kRows) {
+      AccT acc[kRows];
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) acc[k] = (AccT)0;
+      for (int q = 0; q < a.npair; ++q) {
+        const AccT d = sD[q * kTile + tid];
+#pragma unroll
+        for (int k = 0; k < kRows; ++k)
+          if (R0 + k < r) acc[k] = fma(__ldg(Ut + (size_t)(R0 + k) * a.npair + q), d, acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kRows; ++k)
+        if (R0 + k < r) sT[(R0 + k) * kTile + tid] = acc[k];
+    }
+    for (int P0 = 0; P0 < a.npair; P0 += kRows) {
+      AccT acc[kRows];
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) acc[k] = (AccT)0;
+      for (int q = 0; q < r; ++q) {
+        const AccT t = sT[q * kTile + tid];
+#pragma unroll
+        for (int k = 0; k < kRows; ++k)
+          if (P0 + k < a.npair) acc[k] = fma(__ldg(UL + (size_t)(P0 + k) * r + q), t, acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kRows; ++k)
+        if (P0 + k < a.npair) G[(size_t)(P0 + k) * a.ndet + I] = acc[k];
+    }
+  }
+}
+
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec) {
   const size_t el = (prec == 0) ? sizeof(double) : sizeof(float);
   return el * (size_t)npair * (size_t)ndet;
@@ -108,8 +162,29 @@ static cudaError_t launch_gc_t(const SigmaArgs &a, cudaStream_t s) {
 cudaError_t prepare_sigma_kernels() {
   const int big = 227 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_gather_contract<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gather_contract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gather_contract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gather_contract_lr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gather_contract_lr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
+}
+
+template <typename AccT>
+static cudaError_t launch_lr_t(const SigmaArgs &a, const AccT *Ut, const AccT *UL, int r, cudaStream_t s) {
+  const long long ntiles = (a.ndet + kTile - 1) / kTile;
+  const int grid1 = (int)(ntiles < 65535LL * 16 ? ntiles : 65535LL * 16);
+  const size_t smem = sizeof(AccT) * (size_t)(a.npair + r) * kTile;
+  k_gather_contract_lr<AccT><<<grid1, kTile, smem, s>>>(a, Ut, UL, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_contract_lr(const SigmaArgs &a, int prec, const void *Ut, const void *UL, int r,
+                                      cudaStream_t s) {
+  if (r < 1) return cudaErrorInvalidValue;
+  return prec == 0 ? launch_lr_t<double>(a, (const double *)Ut, (const double *)UL, r, s)
+                   : launch_lr_t<float>(a, (const float *)Ut, (const float *)UL, r, s);
 }
 
 cudaError_t launch_gather_contract(const SigmaArgs &a, int prec, cudaStream_t s) {
