@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(kOsThreads, 1)
             }
             double out = 0.0;
             const int fP = sm.fP[P];
-            if (acc != 0 && eI > 0 && fP > 0)  // acc 2^(e_I + f_P - 56), e = biased - 1022
+            if (eI == 2047)  // a NaN or infinity in the row: propagate it as the FMA kernel would
+              out = __longlong_as_double(0x7FF8000000000000LL);
+            else if (acc != 0 && eI > 0 && fP > 0)  // acc 2^(e_I + f_P - 56), e = biased - 1022
               out = scaled_ll_to_double(acc, (eI - 1022) + (fP - 1022) - 56);
             G[(size_t)P * a.ndet + I] = out;
           }

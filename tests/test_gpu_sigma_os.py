@@ -97,3 +97,19 @@ def test_larger_spaces_keep_the_fma_kernel():
     stats = ctx.profile_read()
     ctx.profile(False)
     assert stats["sigma_gather_contract_os"][0] == 0 and stats["sigma_gather_contract"][0] == 1
+
+
+def test_non_finite_input_propagates():
+    """A NaN in a device input vector reaches sigma as non-finite values (the
+    controller's numeric checks rely on it), as with the FMA kernel."""
+    torch = pytest.importorskip("torch")
+    sbci = require_lib()
+    ctx = _ctx(("chain", 6, 1.0))
+    c = torch.randn(ctx.ndet, dtype=torch.float64, device="cuda")
+    c[37] = float("nan")
+    s = torch.empty_like(c)
+    ctx.sigma(c, s, prec=sbci.SBCI_FP64)
+    assert not bool(torch.isfinite(s).all())
+    c[37] = 0.0
+    ctx.sigma(c, s, prec=sbci.SBCI_FP64)
+    assert bool(torch.isfinite(s).all())
