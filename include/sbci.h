@@ -57,11 +57,12 @@ typedef enum {
                       else FP64 FMAs.  The environment variable
                       SBCI_FP64_CONTRACTION=dfma, read when a context is
                       created, selects the FMAs for every size.  With
-                      density-fitted integrals (W of rank r, 2r < 0.9 npair)
-                      and npair > 55, the FP64 FMA contraction uses the
-                      low-rank form W = U L U^T, 2 r npair instead of npair^2
-                      multiply-adds; SBCI_LOWRANK=0, read when a context is
-                      created, turns it off. */
+                      density-fitted integrals ((ij|kl) of rank r by a pivoted
+                      Cholesky, 2 (r + 2) < 0.9 npair) and npair > 55, the
+                      FP64 FMA contraction uses the factored form
+                      W = F M F^T, F = [L | kappa | delta], 2 (r + 2) npair
+                      instead of npair^2 multiply-adds; SBCI_LOWRANK=0, read
+                      when a context is created, turns it off. */
   SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
   SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores, FP32 accumulation */
   SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */
@@ -91,8 +92,12 @@ typedef struct {
   double mixed_eps; /* end of the low-precision stage: dE < mixed_eps ... ; 1e-8 */
   double mixed_r;   /* ... and |z'| < mixed_r; 1e-4 */
   int refine_max_sigma; /* H-products of the low-precision refinement stage per
-                           state; when spent, the state continues with FP64
-                           sigma up to max_sigma; 300 */
+                           state; X is made exact (one FP64 sigma) after every
+                           max_cycle refinement steps, and when the budget is
+                           spent, or two such windows end without Eq. S61 (the
+                           low-precision sigma sits at its noise floor), the
+                           state continues with FP64 sigma up to max_sigma;
+                           300 */
   double start_noise; /* eta >= 0: every state's start becomes x0/|x0| + eta r/|r| with
                          r a seeded SplitMix64 vector in [-1,1) (X by one FP64 sigma of
                          r) and E_0 its Rayleigh quotient, before the projection of Eqs.

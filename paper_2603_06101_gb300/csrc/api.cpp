@@ -488,6 +488,7 @@ sbci_status start_iteration(sbci_ctx *c, double sx, double E, int stage, int pre
   h.t = 0;
   h.E = E;
   h.stage = stage;
+  h.n_sync = 0;
   h.prec = prec >= 0 ? prec : s.p.prec;
   h.zf = h.prec != SBCI_FP64 ? s.zf : nullptr;
   h.up.sx = sx;
@@ -617,7 +618,7 @@ sbci_status handle_halt(sbci_ctx *c) {
     case H_NUMERIC:
       set_error("non-finite values in the SB step");
       return SBCI_ERR_NUMERIC;
-    case H_SWITCH: {  // end of the low-precision stage: exact H-image, then stage 1
+    case H_SWITCH: {  // end of the low-precision stage or of a refinement window: exact H-image, stage 1
       double xx, xX, XX;
       RET(resync(c, &xx, &xX, &XX));
       return start_iteration(c, 1.0 / std::sqrt(xx), xX / xx, 1);
@@ -2157,11 +2158,18 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
     }
   }
-  // low-rank form of W for the FP64 SIMT contraction (lowrank.h): worth it when
-  // 2 r < 0.9 npair (density-fitted integrals), not for full-rank W.  A
-  // pivoted Cholesky of the PSD pair matrix (ij|kl) bounds the rank first
-  // (rank W <= rank (ij|kl) + 2), so full-rank spaces skip the eigen-solver.
-  auto eri_rank = [&](int np) {
+  // low-rank form of W for the FP64 SIMT contraction (lowrank.h).  A pivoted
+  // Cholesky of the PSD pair matrix V = (ij|kl) gives V = L L^T up to 1e-13 of
+  // its largest diagonal; with kappa_P = k_ij and delta_P = [i == j],
+  //   W = 1/2 L L^T + (kappa delta^T + delta kappa^T) / (2N) = F M F^T,
+  //   F = [L | kappa | delta],  M = diag(1/2 I_r, [[0, 1/(2N)], [1/(2N), 0]]),
+  // a factor of rank r + 2 (density-fitted integrals: r <= naux).  Worth it
+  // when 2 (r + 2) < 0.9 npair; the factorisation stops as soon as r passes
+  // that bound, so full-rank spaces pay O(npair r^2) and keep the full form.
+  const char *lr_mode = std::getenv("SBCI_LOWRANK");  // "0": keep the full contraction
+  const bool lr_off = lr_mode && std::strcmp(lr_mode, "0") == 0;
+  if (!lr_off && c->npair > 55) {
+    const int np = c->npair;
     std::vector<double> V((size_t)np * np), d(np);
     for (int i = 0, P = 0; i < n; ++i)
       for (int j = 0; j <= i; ++j, ++P)
@@ -2172,12 +2180,14 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
     std::vector<double> L;  // columns of the factor, np each
     std::vector<char> used(np, 0);
     int r = 0;
-    while (r < np) {
+    bool low = dmax > 0.0;
+    while (low) {
       int piv = -1;
       double best = 1e-13 * dmax;
       for (int P = 0; P < np; ++P)
         if (!used[P] && d[P] > best) best = d[P], piv = P;
       if (piv < 0) break;
+      if (!(2.0 * (r + 1 + 2) < 0.9 * np)) low = false;  // no gain over the full form
       used[piv] = 1;
       const double s = std::sqrt(d[piv]);
       std::vector<double> col(np);
@@ -2190,32 +2200,35 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       L.insert(L.end(), col.begin(), col.end());
       ++r;
     }
-    return r;
-  };
-  const char *lr_mode = std::getenv("SBCI_LOWRANK");  // "0": keep the full contraction
-  const bool lr_off = lr_mode && std::strcmp(lr_mode, "0") == 0;
-  if (!lr_off && c->npair > 55 && 2.0 * (eri_rank(c->npair) + 2) < 0.9 * c->npair) {
-    const int np = c->npair;
-    std::vector<double> Wsq((size_t)np * np), lam(np), U((size_t)np * np);
-    for (int P = 0; P < np; ++P)
-      for (int Q = 0; Q < np; ++Q) Wsq[(size_t)P * np + Q] = c->W_host[(size_t)P * np + Q];
-    jacobi_eigh(np, Wsq.data(), lam.data(), U.data());
-    double lmax = 0.0;
-    for (double l : lam) lmax = std::max(lmax, std::fabs(l));
-    std::vector<int> keep;
-    for (int k = 0; k < np; ++k)
-      if (std::fabs(lam[k]) > 1e-13 * lmax) keep.push_back(k);
-    const int r = (int)keep.size();
-    if (r >= 1 && 2.0 * r < 0.9 * np) {
-      std::vector<double> Ut((size_t)r * np), UL((size_t)np * r);
-      for (int k = 0; k < r; ++k)
-        for (int q = 0; q < np; ++q) {
-          Ut[(size_t)k * np + q] = U[(size_t)q * np + keep[k]];
-          UL[(size_t)q * r + k] = U[(size_t)q * np + keep[k]] * lam[keep[k]];
+    // V that is not positive semi-definite leaves more than the small diagonal
+    // behind: check the whole remainder before trusting the factor
+    for (int P = 0; low && P < np; ++P)
+      for (int Q = 0; Q <= P; ++Q) {
+        double v = V[(size_t)P * np + Q];
+        for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + Q];
+        if (!(std::fabs(v) <= 1e-12 * dmax)) {
+          low = false;
+          break;
+        }
+      }
+    if (low) {
+      const int rr = r + 2;
+      std::vector<double> Ut((size_t)rr * np), UL((size_t)np * rr);
+      for (int i = 0, P = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j, ++P) {
+          const double kap = kmat[i * n + j], del = (i == j) ? 1.0 : 0.0;
+          for (int q = 0; q < r; ++q) {
+            Ut[(size_t)q * np + P] = L[(size_t)q * np + P];
+            UL[(size_t)P * rr + q] = 0.5 * L[(size_t)q * np + P];
+          }
+          Ut[(size_t)r * np + P] = kap;
+          Ut[(size_t)(r + 1) * np + P] = del;
+          UL[(size_t)P * rr + r] = del / (2.0 * N);
+          UL[(size_t)P * rr + r + 1] = kap / (2.0 * N);
         }
       TRY(up(&c->d_lrUt64, Ut.data(), Ut.size() * 8));
       TRY(up(&c->d_lrUL64, UL.data(), UL.size() * 8));
-      c->lr_rank = r;
+      c->lr_rank = rr;
     }
   }
   {

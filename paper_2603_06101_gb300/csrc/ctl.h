@@ -52,6 +52,7 @@ struct CtlHead {
   int stage;       // 0: low-precision stage (ends with H_SWITCH); 1: to Eq. S61
   int pinv_ready;  // the step arguments' pinv holds 1 / guarded(D - Ec0) for this state
   int n_stage1;    // H-products spent in stage 1 of this state
+  int n_sync;      // stage-1 H-products since X was last made exact (FP64 H x)
   double sx_pending;
   double E;        // E_t
   double E_solve;  // E_{t+1} of the last subspace solve
@@ -444,9 +445,20 @@ __host__ __device__ inline void ctl_check(CtlHead &s) {
       s.t = 0;
     }
   }
-  if (s.n_sigma >= s.p.max_sigma ||
-      (s.p.user_prec != SBCI_FP64 && s.prec != SBCI_FP64 && s.n_stage1 >= s.p.refine_max_sigma))
+  const bool low = s.p.user_prec != SBCI_FP64 && s.prec != SBCI_FP64;
+  if (s.n_sigma >= s.p.max_sigma || (low && s.n_stage1 >= s.p.refine_max_sigma)) {
     s.halt = H_CAP;
+  } else if (low && s.stage == 1 && s.n_sync >= s.p.max_cycle) {
+    // The low-precision refinement carries X = H x by low-precision images
+    // of y and z; where y or z is nearly dependent the update coefficients
+    // grow (|b| up to 1e10 seen) and carry that rounding into X, so SB
+    // energies can fall below the ground state and run away.  X is made
+    // exact (one FP64 sigma) after every max_cycle refinement steps; after
+    // two such windows without Eq. S61 the low-precision sigma is taken to
+    // sit at its noise floor above the FP64 thresholds, and the state goes
+    // on with FP64 sigma.
+    s.halt = s.n_stage1 >= 2 * s.p.max_cycle ? H_CAP : H_SWITCH;
+  }
 }
 
 // After sigma of the next z: subspace solve, parameters of the next update.
@@ -475,7 +487,10 @@ __host__ __device__ inline void ctl_solve(CtlHead &s) {
   }
   s.n_sigma += 1;
   if (s.prec == SBCI_FP64) s.n_sigma_fp64 += 1;
-  if (s.stage == 1) s.n_stage1 += 1;
+  if (s.stage == 1) {
+    s.n_stage1 += 1;
+    s.n_sync += 1;
+  }
   s.n_step += 1;
   sbci_trace_record r;
   r.state = s.alpha;

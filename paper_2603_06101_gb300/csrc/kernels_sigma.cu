@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kTile) k_gather_contract(SigmaArgs a) {
   }
 }
 
-// Phase 1 in the low-rank form of W (lowrank.h): t = U_r^T D into shared
-// memory after the D column, then G = (U_r L_r) t.  Same gather.
+// Phase 1 in the low-rank form of W (lowrank.h): t = F^T D into shared
+// memory after the D column, then G = (F M) t.  Same gather.
 template <typename AccT>
 __global__ void __launch_bounds__(kTile) k_gather_contract_lr(SigmaArgs a, const AccT *Ut, const AccT *UL, int r) {
   extern __shared__ unsigned char smem_raw[];

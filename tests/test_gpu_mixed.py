@@ -125,3 +125,24 @@ def test_refinement_budget_falls_back_to_fp64():
     server.close()
     for c in ctxs:
         c.close()
+
+
+def test_stagnating_refinement_falls_back_to_fp64():
+    """Stretched H12 (2.96 A, nearly degenerate) with a seeded start: the
+    TF32x3 refinement stalls at its noise floor (|z'| ~ 2e-5, above r0), and
+    its large-|b| steps carry low-precision rounding into X.  X is made exact
+    after every max_cycle refinement steps and, after two windows without
+    convergence, the state goes on with FP64 sigma (before, the refinement
+    spent its budget while X drifted from H x until the energies ran away).
+    All three states meet the FP64 solve's energies."""
+    sbci = require_lib()
+    I = inputs.h_chain(12, 2.959854009887736)
+    ctx = sbci.Context.from_integrals(I)
+    E64, _, _, st = ctx.solve(3, sbci.params(prec=sbci.SBCI_FP64, start_noise=1e-2, noise_seed=2603))
+    assert st == sbci.SBCI_OK
+    p = sbci.params(prec=sbci.SBCI_TF32X3, start_noise=1e-2, noise_seed=2603)
+    E, _, R, st = ctx.solve(3, p)
+    assert st == sbci.SBCI_OK and all(r.converged for r in R)
+    assert np.abs(E - E64).max() < 1e-8
+    tr = ctx.trace()
+    assert min(t.energy for t in tr) > E64[0] - I.e_core - 1e-4  # no run-away below the ground state

@@ -1,11 +1,12 @@
 """Low-rank (density-fitting) form of the FP64 SIMT sigma contraction
-(lowrank.h): W = U_r L_r U_r^T from the context's eigen-decomposition of the
-packed operator, G = (U_r L_r)(U_r^T D).  Used beyond the exact-slice kernel's
-size (npair > 55) when the two-electron integrals are density-fitted
-(rank W <= naux + 2 < 0.45 npair: from n = 14 orbitals with naux = 3n).
+(lowrank.h): W = F M F^T with F = [L | kappa | delta] from a pivoted Cholesky
+of the pair matrix (ij|kl) = L L^T and the one-electron part, G = (F M)(F^T D).
+Used beyond the exact-slice kernel's size (npair > 55) when the two-electron
+integrals are density-fitted (rank W <= naux + 2 < 0.45 npair: from n = 14
+orbitals with naux = 3n).
 
-Tolerance as for the full contraction: FP64 1e-12 of max|sigma| (the dropped
-eigenvalues are below 1e-13 of the largest).
+Tolerance as for the full contraction: FP64 1e-12 of max|sigma| (the
+Cholesky remainder is below 1e-13 of the largest diagonal of (ij|kl)).
 """
 import numpy as np
 import pytest
