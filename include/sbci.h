@@ -64,7 +64,8 @@ typedef enum {
                       instead of npair^2 multiply-adds; SBCI_LOWRANK=0, read
                       when a context is created, turns it off. */
   SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
-  SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores, FP32 accumulation */
+  SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores: reserved, not built;
+                      every call with it returns SBCI_ERR_INVALID */
   SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */
 } sbci_precision;
 

@@ -203,7 +203,8 @@ sbci_status timed(sbci_ctx *c, int kid, F &&launch) {
   return SBCI_OK;
 }
 
-// sigma of one device vector, optional epilogue dots against u[0..2].
+// SBCI_ERR_INVALID for a precision this context cannot run (TF32x3 beyond
+// n = 14, the reserved BF16x3).
 sbci_status check_prec(const sbci_ctx *c, int prec) {
   if (prec == SBCI_FP64 || prec == SBCI_FP32) return SBCI_OK;
   if (prec == SBCI_TF32X3) {
@@ -239,6 +240,7 @@ cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
   }
 }
 
+// sigma of one device vector in the given precision (out = H in).
 sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   RET(check_prec(c, prec));
   RET(ensure_G(c, prec));
