@@ -130,8 +130,9 @@ typedef struct {
   double dE, dz;      /* |E_{t+1}-E_t| and |z'_{t+1}| */
   int event;          /* 0 none, 1 converged, 2..5 restart S62a/b/c/max_cycle,
                          6 low-precision stage ended: switch to FP64 refinement,
-                         7 refinement budget spent: the state continues with
-                           FP64 sigma from an exact X (host record),
+                         7 refinement budget, or two of its re-sync windows,
+                           spent: the state continues with FP64 sigma from an
+                           exact X (host record),
                          8 later-step coefficients undefined (zero denominator
                            in Eqs. S53-S55): the step was taken on the
                            first-step path from x */
@@ -222,7 +223,7 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
                        double *energies, double *vecs, sbci_report *rep);
 
 /* Solves n contexts (1 <= n <= 64) for their k lowest states together: the
- * solves with a TF32x3 sigma and n_orb <= 12 advance in one CUDA-graph loop of
+ * solves with a TF32x3 sigma and n_orb <= 14 advance in one CUDA-graph loop of
  * batched persistent kernels over a device job table (see sbci_server_*);
  * others are solved one after the other.  params as in sbci_solve (init must
  * be 0).  energies: host [n][k] totals; rep: host [n][k] or NULL; launches
