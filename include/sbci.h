@@ -367,7 +367,7 @@ sbci_status sbci_server_progress(sbci_server *sv, int *n_active, int *n_queued);
 sbci_status sbci_server_poll(sbci_server *sv, long long ticket, int *done, double *energies,
                              sbci_report *rep, double *times);
 
-/* on = 1 (the default): admitted solves with a TF32x3 sigma and n <= 12 are
+/* on = 1 (the default): admitted solves with a TF32x3 sigma and n <= 14 are
  * advanced together by one CUDA-graph loop of batched persistent kernels that
  * walk a device job table (a work queue of (solve, block) items); on = 0: every
  * solve runs its own graph loop on its own stream.  Only while no solve is
