@@ -227,7 +227,7 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
  * batched persistent kernels over a device job table (see sbci_server_*);
  * others are solved one after the other.  params as in sbci_solve (init must
  * be 0).  energies: host [n][k] totals; rep: host [n][k] or NULL; launches
- * (nullable): kernels this call launched (five per batched loop body plus the
+ * (nullable): kernels this call launched (six per batched loop body plus the
  * host-driven ones).  Each context afterwards holds its finished solve
  * (sbci_finish, sbci_trace). */
 sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
@@ -309,7 +309,7 @@ sbci_status sbci_profile_read(sbci_ctx *ctx, sbci_kernel_stat *out, int cap, int
 
 /* Kernel timing of the batch engine that sbci_solve_batch uses on the current
  * device (no counterpart in the paper).  Resets its statistics; enable = 1
- * makes later sbci_solve_batch calls on this device launch the five kernels of
+ * makes later sbci_solve_batch calls on this device launch the six kernels of
  * every batched loop body one by one, each bracketed by CUDA events on the
  * engine's stream, instead of through the graph loop (same arithmetic). */
 sbci_status sbci_batch_profile(int enable);
