@@ -1,4 +1,6 @@
-"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+"""The C-ABI library builds, loads without a GPU and exports every declared
+symbol; the binding's structs and constants match the header as the C compiler
+lays it out."""
 import ctypes
 import os
 import re
@@ -67,3 +69,50 @@ def test_host_only_calls_without_gpu(lib_path):
     st = lib.sbci_init_integrals(ctypes.byref(h), 2, 1, 1, h1.ctypes.data_as(ctypes.c_void_p),
                                  eri.ctypes.data_as(ctypes.c_void_p), 0.0, None)
     assert st == sbci.SBCI_ERR_INVALID
+
+
+_STRUCTS = ["sbci_params", "sbci_report", "sbci_trace_record", "sbci_kernel_stat", "sbci_batch_class"]
+_CONSTS = ["SBCI_OK", "SBCI_ERR_INVALID", "SBCI_ERR_NOMEM", "SBCI_ERR_CUDA", "SBCI_ERR_NUMERIC",
+           "SBCI_ERR_NOT_CONVERGED", "SBCI_ERR_TIMEOUT", "SBCI_ERR_CANCELLED", "SBCI_FP64", "SBCI_TF32X3",
+           "SBCI_BF16X3", "SBCI_FP32"]
+
+
+def test_binding_layouts_match_the_c_compiler(tmp_path):
+    """Every struct of the binding has the C compiler's size and field offsets,
+    and every constant its value (a layout mismatch would corrupt arguments
+    silently)."""
+    import shutil
+    import subprocess
+
+    from paper_2603_06101_gb300 import sbci
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sbci.h"', "int main(void) {"]
+    for s in _STRUCTS:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for name, _ in getattr(sbci, s)._fields_:
+            lines.append(f'  printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    for k in _CONSTS:
+        lines.append(f'  printf("const {k} %d\\n", (int){k});')
+    lines.append('  printf("const NOALLOC %u\\n", (unsigned)SBCI_NOALLOC_SCRATCH_BYTES);')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        a, b, v = line.split()
+        if a == "const":
+            want = sbci.NOALLOC_SCRATCH_BYTES if b == "NOALLOC" else getattr(sbci, b)
+            assert int(v) == want, line
+        elif b == "size":
+            assert ctypes.sizeof(getattr(sbci, a)) == int(v), line
+        else:
+            assert getattr(getattr(sbci, a), b).offset == int(v), line
+        seen += 1
+    assert seen == len(_CONSTS) + 1 + sum(1 + len(getattr(sbci, s)._fields_) for s in _STRUCTS)
+
