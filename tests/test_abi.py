@@ -116,3 +116,45 @@ def test_binding_layouts_match_the_c_compiler(tmp_path):
         seen += 1
     assert seen == len(_CONSTS) + 1 + sum(1 + len(getattr(sbci, s)._fields_) for s in _STRUCTS)
 
+
+
+def _prototypes():
+    src = open(os.path.join(ROOT, "include", "sbci.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = {}
+    for ret, name, args in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(sbci_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+        args = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        out[name] = (" ".join(ret.split()), args)
+    return out
+
+
+def _kind_c(decl):
+    if "*" in decl:
+        return "ptr"
+    words = decl.replace("const ", "").split()
+    base = " ".join(words[:-1])
+    return {"int": "int", "double": "double", "long long": "longlong", "size_t": "size_t"}[base]
+
+
+def _kind_ctypes(t):
+    if t is ctypes.c_void_p or t is ctypes.c_char_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    if t is ctypes.c_size_t:
+        return "size_t"
+    return {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_longlong: "longlong"}[t]
+
+
+def test_binding_prototypes_match_the_header(lib_path):
+    """Argument count and kind (pointer, int, double, long long, size_t) and the
+    return type of every bound entry point against its header prototype."""
+    from paper_2603_06101_gb300 import sbci
+
+    lib = sbci.load()
+    protos = _prototypes()
+    for name in sbci.EXPORTS:
+        ret, args = protos[name]
+        fn = getattr(lib, name)
+        assert [_kind_ctypes(t) for t in fn.argtypes] == [_kind_c(a) for a in args], name
+        want_ret = {"sbci_status": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p}[ret]
+        assert fn.restype is want_ret, (name, ret)
