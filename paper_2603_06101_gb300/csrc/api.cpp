@@ -2160,74 +2160,22 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
     }
   }
-  // low-rank form of W for the FP64 SIMT contraction (lowrank.h).  A pivoted
-  // Cholesky of the PSD pair matrix V = (ij|kl) gives V = L L^T up to 1e-13 of
-  // its largest diagonal; with kappa_P = k_ij and delta_P = [i == j],
-  //   W = 1/2 L L^T + (kappa delta^T + delta kappa^T) / (2N) = F M F^T,
-  //   F = [L | kappa | delta],  M = diag(1/2 I_r, [[0, 1/(2N)], [1/(2N), 0]]),
-  // a factor of rank r + 2 (density-fitted integrals: r <= naux).  Worth it
-  // when 2 (r + 2) < 0.9 npair; the factorisation stops as soon as r passes
-  // that bound, so full-rank spaces pay O(npair r^2) and keep the full form.
+  // low-rank form of W for the FP64 SIMT contraction (lowrank.h, df_factor)
   const char *lr_mode = std::getenv("SBCI_LOWRANK");  // "0": keep the full contraction
   const bool lr_off = lr_mode && std::strcmp(lr_mode, "0") == 0;
   if (!lr_off && c->npair > 55) {
     const int np = c->npair;
-    std::vector<double> V((size_t)np * np), d(np);
+    std::vector<double> V((size_t)np * np), kap(np), del(np);
     for (int i = 0, P = 0; i < n; ++i)
-      for (int j = 0; j <= i; ++j, ++P)
+      for (int j = 0; j <= i; ++j, ++P) {
+        kap[P] = kmat[i * n + j];
+        del[P] = (i == j) ? 1.0 : 0.0;
         for (int k = 0, Q = 0; k < n; ++k)
           for (int l = 0; l <= k; ++l, ++Q) V[(size_t)P * np + Q] = E4(i, j, k, l);
-    double dmax = 0.0;
-    for (int P = 0; P < np; ++P) dmax = std::max(dmax, d[P] = V[(size_t)P * np + P]);
-    std::vector<double> L;  // columns of the factor, np each
-    std::vector<char> used(np, 0);
-    int r = 0;
-    bool low = dmax > 0.0;
-    while (low) {
-      int piv = -1;
-      double best = 1e-13 * dmax;
-      for (int P = 0; P < np; ++P)
-        if (!used[P] && d[P] > best) best = d[P], piv = P;
-      if (piv < 0) break;
-      if (!(2.0 * (r + 1 + 2) < 0.9 * np)) low = false;  // no gain over the full form
-      used[piv] = 1;
-      const double s = std::sqrt(d[piv]);
-      std::vector<double> col(np);
-      for (int P = 0; P < np; ++P) {
-        double v = V[(size_t)P * np + piv];
-        for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + piv];
-        col[P] = v / s;
       }
-      for (int P = 0; P < np; ++P) d[P] -= col[P] * col[P];
-      L.insert(L.end(), col.begin(), col.end());
-      ++r;
-    }
-    // V that is not positive semi-definite leaves more than the small diagonal
-    // behind: check the whole remainder before trusting the factor
-    for (int P = 0; low && P < np; ++P)
-      for (int Q = 0; Q <= P; ++Q) {
-        double v = V[(size_t)P * np + Q];
-        for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + Q];
-        if (!(std::fabs(v) <= 1e-12 * dmax)) {
-          low = false;
-          break;
-        }
-      }
-    if (low) {
-      const int rr = r + 2;
-      std::vector<double> Ut((size_t)rr * np), UL((size_t)np * rr);
-      for (int i = 0, P = 0; i < n; ++i)
-        for (int j = 0; j <= i; ++j, ++P) {
-          const double kap = kmat[i * n + j], del = (i == j) ? 1.0 : 0.0;
-          for (int q = 0; q < r; ++q) {
-            Ut[(size_t)q * np + P] = L[(size_t)q * np + P];
-            UL[(size_t)P * rr + q] = 0.5 * L[(size_t)q * np + P];
-          }
-          Ut[(size_t)r * np + P] = kap;
-          Ut[(size_t)(r + 1) * np + P] = del;
-          UL[(size_t)P * rr + r] = del / (2.0 * N);
-          UL[(size_t)P * rr + r + 1] = kap / (2.0 * N);
-        }
+    std::vector<double> Ut, UL;
+    const int rr = df_factor(np, V.data(), kap.data(), del.data(), N, Ut, UL);
+    if (rr > 0) {
       TRY(up(&c->d_lrUt64, Ut.data(), Ut.size() * 8));
       TRY(up(&c->d_lrUL64, UL.data(), UL.size() * 8));
       c->lr_rank = rr;

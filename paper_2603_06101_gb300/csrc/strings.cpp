@@ -1,11 +1,14 @@
-// Host construction of occupation strings and single-excitation tables, and
-// a small Jacobi eigen-solver for the 2x2 / 3x3 / n_init subspace problems.
+// Host construction of occupation strings and single-excitation tables, a
+// small Jacobi eigen-solver for the subspace problems of the initial guess,
+// Davidson-Liu and SBCI2, and the density-fitted factor of the packed
+// two-electron operator.
 //
 // The paper represents H over Slater determinants (Results, SBCI1) and leaves
 // the determinant machinery to its host program; the conventions here are
 // stated in include/sbci.h: strings in increasing bitmask order, addressed by
 // the combinatorial number system, excitation entries a+_k a_l |I> = sign |J>
 // for l occupied (ascending) and k unoccupied or k == l (ascending).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -131,6 +134,72 @@ void jacobi_eigh(int n, const double *Ain, double *w, double *V) {
       for (int k = 0; k < n; ++k) std::swap(V[k * n + i], V[k * n + m]);
     }
   }
+}
+
+// Density-fitted factor of the packed operator (lowrank.h).  A pivoted
+// Cholesky of the PSD pair matrix V = (ij|kl) gives V = L L^T up to 1e-13 of
+// its largest diagonal; with kappa_P = k_ij and delta_P = [i == j],
+//   W = 1/2 L L^T + (kappa delta^T + delta kappa^T) / (2N) = F M F^T,
+//   F = [L | kappa | delta],  M = diag(1/2 I_r, [[0, 1/(2N)], [1/(2N), 0]]),
+// a factor of rank r + 2 (density-fitted integrals: r <= naux).  Worth it
+// when 2 (r + 2) < 0.9 npair; the factorisation stops as soon as r passes
+// that bound, so full-rank spaces pay O(npair r^2).  A V that is not positive
+// semi-definite leaves more than the small diagonal behind, so the whole
+// remainder is checked (1e-12 of the largest diagonal) before the factor is
+// trusted.  Returns r + 2 with Ut = F^T [r+2][np] and UL = F M [np][r+2], or
+// 0 (keep the full form).
+int df_factor(int np, const double *V, const double *kappa, const double *delta, int N,
+              std::vector<double> &Ut, std::vector<double> &UL) {
+  std::vector<double> d(np);
+  double dmax = 0.0;
+  for (int P = 0; P < np; ++P) dmax = std::max(dmax, d[P] = V[(size_t)P * np + P]);
+  std::vector<double> L;  // columns of the factor, np each
+  std::vector<char> used(np, 0);
+  int r = 0;
+  bool low = dmax > 0.0 && N > 0;
+  while (low) {
+    int piv = -1;
+    double best = 1e-13 * dmax;
+    for (int P = 0; P < np; ++P)
+      if (!used[P] && d[P] > best) best = d[P], piv = P;
+    if (piv < 0) break;
+    if (!(2.0 * (r + 1 + 2) < 0.9 * np)) low = false;  // no gain over the full form
+    used[piv] = 1;
+    const double s = std::sqrt(d[piv]);
+    std::vector<double> col(np);
+    for (int P = 0; P < np; ++P) {
+      double v = V[(size_t)P * np + piv];
+      for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + piv];
+      col[P] = v / s;
+    }
+    for (int P = 0; P < np; ++P) d[P] -= col[P] * col[P];
+    L.insert(L.end(), col.begin(), col.end());
+    ++r;
+  }
+  for (int P = 0; low && P < np; ++P)
+    for (int Q = 0; Q <= P; ++Q) {
+      double v = V[(size_t)P * np + Q];
+      for (int q = 0; q < r; ++q) v -= L[(size_t)q * np + P] * L[(size_t)q * np + Q];
+      if (!(std::fabs(v) <= 1e-12 * dmax)) {
+        low = false;
+        break;
+      }
+    }
+  if (!low) return 0;
+  const int rr = r + 2;
+  Ut.assign((size_t)rr * np, 0.0);
+  UL.assign((size_t)np * rr, 0.0);
+  for (int P = 0; P < np; ++P) {
+    for (int q = 0; q < r; ++q) {
+      Ut[(size_t)q * np + P] = L[(size_t)q * np + P];
+      UL[(size_t)P * rr + q] = 0.5 * L[(size_t)q * np + P];
+    }
+    Ut[(size_t)r * np + P] = kappa[P];
+    Ut[(size_t)(r + 1) * np + P] = delta[P];
+    UL[(size_t)P * rr + r] = delta[P] / (2.0 * N);
+    UL[(size_t)P * rr + r + 1] = kappa[P] / (2.0 * N);
+  }
+  return rr;
 }
 
 }  // namespace sbci

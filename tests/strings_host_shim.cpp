@@ -1,6 +1,6 @@
-// Host build of the library's string-table builder and small eigen-solver
-// (csrc/strings.cpp) for the CPU tests, with plain-array entry points for
-// ctypes.  Test infrastructure only.
+// Host build of the library's string-table builder, small eigen-solver and
+// density-fitted factor (csrc/strings.cpp) for the CPU tests, with plain-array
+// entry points for ctypes.  Test infrastructure only.
 #include <cstring>
 #include <string>
 
@@ -31,5 +31,18 @@ int host_build_strings(int norb, int nelec, uint32_t *masks, uint32_t *links) {
 }
 
 void host_jacobi_eigh(int n, const double *A, double *w, double *V) { sbci::jacobi_eigh(n, A, w, V); }
+
+// The density-fitted factor: returns r + 2 (0: full form kept) and copies
+// Ut [(r+2) np] and UL [np (r+2)] when they fit cap doubles each.
+int host_df_factor(int np, const double *V, const double *kappa, const double *delta, int N, double *Ut,
+                   double *UL, long long cap) {
+  std::vector<double> a, b;
+  const int rr = sbci::df_factor(np, V, kappa, delta, N, a, b);
+  if (rr > 0 && (long long)a.size() <= cap && (long long)b.size() <= cap) {
+    std::memcpy(Ut, a.data(), sizeof(double) * a.size());
+    std::memcpy(UL, b.data(), sizeof(double) * b.size());
+  }
+  return rr;
+}
 
 }  // extern "C"

@@ -8,7 +8,13 @@ tests/strings_host_shim.cpp, against the oracle and textbook results:
   SBCI2 subspace problems against LAPACK (numpy): eigenvalues within
   1e-13 max|lambda| (Jacobi is accurate to rounding in every eigenvalue),
   V orthonormal and A V = V Lambda to 1e-12 max|A|, including repeated
-  eigenvalues and already diagonal input.
+  eigenvalues and already diagonal input;
+* the density-fitted factor W = F M F^T of the packed operator (reading L1):
+  rank naux + 2 on density-fitted integrals and on stretched chains whose
+  distant pair densities vanish, F M F^T equal to W (the operator as the
+  context builds it, written out here from its definition) within 1e-12 of
+  max|W|, the full form kept for full-rank integrals (H12 at 1.2 A) and for
+  a pair matrix that is not positive semi-definite.
 """
 import ctypes
 import os
@@ -19,6 +25,7 @@ import numpy as np
 import pytest
 
 from oracle import strings as st
+from paper_2603_06101_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -45,6 +52,7 @@ def lib(tmp_path_factory):
     L.host_string_sizes.argtypes = [ctypes.c_int, ctypes.c_int, P]
     L.host_build_strings.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
     L.host_jacobi_eigh.argtypes = [ctypes.c_int, P, P, P]
+    L.host_df_factor.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, P, P, ctypes.c_longlong]
     return L
 
 
@@ -111,3 +119,62 @@ def test_jacobi_special_spectra(lib):
     X = rng.standard_normal((40, 5))
     X[:, 4] = X[:, 3] + 1e-7 * rng.standard_normal(40)
     _check(lib, X.T @ X)
+
+
+def _packed_operator(I):
+    """Pair matrix V = (ij|kl), kappa_ij = h_ij - 1/2 sum_m (im|mj), delta and
+    W = 1/2 V + (kappa delta^T + delta kappa^T) / (2N) over packed pairs i >= j."""
+    n = I.h1.shape[0]
+    eri = I.eri.reshape(n, n, n, n)
+    pairs = [(i, j) for i in range(n) for j in range(i + 1)]
+    V = np.array([[eri[i, j, k, l] for (k, l) in pairs] for (i, j) in pairs])
+    kmat = I.h1 - 0.5 * np.einsum("immj->ij", eri)
+    kap = np.array([kmat[i, j] for (i, j) in pairs])
+    dl = np.array([1.0 if i == j else 0.0 for (i, j) in pairs])
+    N = I.nalpha + I.nbeta
+    return V, kap, dl, N, 0.5 * V + (np.outer(kap, dl) + np.outer(dl, kap)) / (2 * N)
+
+
+def df_factor(lib, V, kap, dl, N):
+    npair = V.shape[0]
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    kap = np.ascontiguousarray(kap, dtype=np.float64)
+    dl = np.ascontiguousarray(dl, dtype=np.float64)
+    cap = npair * (npair + 2)
+    Ut = np.zeros(cap)
+    UL = np.zeros(cap)
+    rr = lib.host_df_factor(npair, V.ctypes.data, kap.ctypes.data, dl.ctypes.data, int(N), Ut.ctypes.data,
+                            UL.ctypes.data, cap)
+    if rr == 0:
+        return 0, None, None
+    return rr, Ut[:rr * npair].reshape(rr, npair), UL[:rr * npair].reshape(npair, rr)
+
+
+@pytest.mark.parametrize("make,rank", [(lambda: inputs.random_df(14, 7, 3, 2), 42 + 2),
+                                       (lambda: inputs.random_df(14, 3, 7, 7, naux=20), 20 + 2),
+                                       (lambda: inputs.h_chain(12, 2.959854009887736), None)])
+def test_df_factor_reproduces_the_operator(lib, make, rank):
+    I = make()
+    V, kap, dl, N, W = _packed_operator(I)
+    rr, Ut, UL = df_factor(lib, V, kap, dl, N)
+    assert rr > 0 and 2 * rr < 0.9 * V.shape[0]
+    if rank is not None:
+        assert rr == rank
+    assert np.abs(UL @ Ut - W).max() <= 1e-12 * np.abs(W).max()
+    # Ut rows: the Cholesky vectors, then kappa and delta
+    assert np.array_equal(Ut[-2], kap) and np.array_equal(Ut[-1], dl)
+
+
+def test_df_factor_keeps_the_full_form(lib):
+    # full-rank integrals: the factorisation stops once 2 (r + 2) reaches 0.9 npair
+    V, kap, dl, N, _ = _packed_operator(inputs.h_chain(12, 1.2))
+    assert df_factor(lib, V, kap, dl, N)[0] == 0
+    # a pair matrix with a negative direction: the remainder check rejects it
+    I = inputs.random_df(12, 5, 3, 3, naux=6)
+    V, kap, dl, N, _ = _packed_operator(I)
+    u = np.random.default_rng(1).standard_normal(V.shape[0])
+    Vbad = V - 0.5 * np.abs(V).max() * np.outer(u, u) / (u @ u)
+    assert np.linalg.eigvalsh(Vbad).min() < 0
+    assert df_factor(lib, Vbad, kap, dl, N)[0] == 0
+    # all-zero integrals: nothing to factor
+    assert df_factor(lib, np.zeros_like(V), kap, dl, N)[0] == 0
