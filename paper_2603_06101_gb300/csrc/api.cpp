@@ -119,7 +119,7 @@ struct sbci_ctx {
   void *d_Wos = nullptr;      // BF16 integer slices of W for the FP64 tensor-core contraction (nullptr: off)
   int *d_fexp = nullptr;      // their per-output-pair exponents
   int os_grid = 0;
-  // low-rank form W = U_r L_r U_r^T of the FP64 SIMT contraction (lowrank.h); 0: off
+  // factored form W = F M F^T of the FP64 SIMT contraction (lowrank.h, df_factor): its rank, 0: off
   int lr_rank = 0;
   void *d_lrUt64 = nullptr, *d_lrUL64 = nullptr;
   double *d_diag = nullptr;
