@@ -142,12 +142,18 @@ typedef struct {
 /* Fills *p with the defaults listed above.  Returns SBCI_ERR_INVALID on NULL. */
 sbci_status sbci_params_init(sbci_params *p);
 
-/* Creates a context on the current CUDA device for one active space.
+/* Creates a context on the current CUDA device for one active space: the
+ * Hamiltonian H whose lowest eigenpairs SBCI seeks (Eq. 1; the determinant
+ * representation is the host program's, not specified by the paper).
  * Builds the string tables (host), the packed two-electron operator W
  * (one-electron part absorbed), the diagonal of H, and uploads them.
  * h1: host [norb*norb]; eri: host [norb^4] (ij|kl); both FP64, read only.
  * cuda_stream: a cudaStream_t to run on, or NULL for a library-owned stream.
- * On success *out owns all device memory until sbci_destroy. */
+ * On success *out owns all device memory until sbci_destroy.  Errors:
+ * SBCI_ERR_INVALID for sizes outside the limits, h1 not symmetric or eri
+ * without the 8-fold symmetry of real orbitals (1e-10 of the largest entry),
+ * SBCI_ERR_NUMERIC for NaN/Inf inputs (both before any CUDA call),
+ * SBCI_ERR_NOMEM / SBCI_ERR_CUDA from the device set-up (nothing leaks). */
 sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
                                 const double *h1, const double *eri, double e_core,
                                 void *cuda_stream);
@@ -164,12 +170,19 @@ sbci_status sbci_dims(const sbci_ctx *ctx, long long *ndet, int *na, int *nb,
  * (max(k,l)+1)/2 + min(k,l). */
 sbci_status sbci_string_table(const sbci_ctx *ctx, int spin, int *out);
 
-/* D_I = <I|H|I> (electronic).  out: [Ndet] host (on_device = 0) or device. */
+/* D_I = <I|H|I> (electronic): the diagonal of the preconditioner
+ * (D - E^0)^-1 (Eqs. 6-7, S31).  out: [Ndet] host (on_device = 0) or device. */
 sbci_status sbci_diagonal(sbci_ctx *ctx, double *out, int on_device);
 
-/* sigma = H c for nvec vectors, each [Ndet] (electronic H, no e_core).
+/* sigma = H c for nvec vectors, each [Ndet] (electronic H, no e_core): the
+ * H-product of every SB step (Eqs. S9, S32).
  * c and sigma: host (on_device = 0) or device (on_device = 1) pointers to
- * nvec*Ndet doubles; they must not overlap.  prec: sbci_precision. */
+ * nvec*Ndet doubles; they must not overlap.  prec: sbci_precision.
+ * nvec = 0 does nothing.  Errors: SBCI_ERR_INVALID for NULL pointers,
+ * nvec < 0 or a precision the context cannot run; SBCI_ERR_NUMERIC for
+ * NaN/Inf in host input (device inputs are not scanned: non-finite values
+ * propagate to sigma); SBCI_ERR_TIMEOUT when a bounded device wait of the
+ * tensor-core kernels ran out (the context stays usable). */
 sbci_status sbci_sigma(sbci_ctx *ctx, const double *c, double *sigma, int nvec,
                        int prec, int on_device);
 
@@ -288,10 +301,13 @@ sbci_status sbci_solve_sbci2(sbci_ctx *ctx, int k, const sbci_params *params, in
 sbci_status sbci_davidson(sbci_ctx *ctx, int k, const sbci_params *params, int max_space,
                           double *energies, double *vecs, sbci_report *rep, long long *vector_bytes);
 
-/* Copies up to cap trace records of the last solve; *n = records available. */
+/* Copies up to cap trace records of the last solve; *n = records available.
+ * The records are the per-step quantities the paper plots (Fig. 3: E_t, b,
+ * c, k, |E_{t+1} - E_t|, |z'|) plus the events of the solve. */
 sbci_status sbci_trace(const sbci_ctx *ctx, sbci_trace_record *buf, int cap, int *n);
 
-/* Per-kernel statistics of the library's own launches on the context stream. */
+/* Per-kernel statistics of the library's own launches on the context stream
+ * (no counterpart in the paper). */
 typedef struct {
   char name[32];       /* kernel family, e.g. "sigma_gather_contract" */
   long long launches;  /* launches since the last sbci_profile call */
