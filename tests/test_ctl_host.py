@@ -286,3 +286,22 @@ def test_restart_causes_in_order(ctl):
     assert check(ctl, **{**args, "t": p.max_cycle - 2})[1][0] == 0
     # S62a before S62b
     assert check(ctl, **{**args, "k": 0.05}, alpha=2)[1][0] == 2
+
+
+def test_undefined_later_step_takes_the_first_step_path(ctl):
+    """Reading R15: x, y, z orthonormal with x decoupled (H_xy = H_xz = 0) and
+    the lowest Ritz vector inside span{y, z}: its x-component is exactly 0, so
+    k, b and c of Eqs. S53-S55 are undefined.  The step is taken on the
+    first-step path from x (y dropped): the 2x2 problem in (x, z) has its
+    lowest vector along x (E = H_xx, k = 1, c = 0) and the record's event is 8."""
+    Hxx, Hyy, Hyz, Hzz = -1.8, -2.0, 0.5, -1.5
+    #        NXX  NXY  NYY  HXX  HXY  HYY  ZPZP NXZ  NYZ  NZZ  HXZ  HYZ  HZZ
+    dots = [1.0, 0.0, 1.0, Hxx, 0.0, Hyy, 0.0, 0.0, 0.0, 1.0, 0.0, Hyz, Hzz]
+    assert np.linalg.eigvalsh([[Hyy, Hyz], [Hyz, Hzz]])[0] < Hxx
+    halt, o = solve(ctl, dots, first=0, sx=1.0)
+    assert halt == H_RUN and o[11] == 8
+    assert o[0] == Hxx and o[1] == 1.0 and o[2] == 0.0 and abs(o[3]) == 1.0
+    assert o[9] == 0.0  # y dropped
+    # the same problem posed as a first step gives the same parameters
+    halt1, o1 = solve(ctl, dots, first=1, sx=1.0)
+    assert halt1 == H_RUN and o1[11] == 0 and np.array_equal(o1[:4], o[:4])
