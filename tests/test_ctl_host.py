@@ -18,6 +18,8 @@ by g++ (tests/ctl_host_shim.cpp), against the oracle SBCI1.
 * Mixed-precision stages: the switch at the end of the low-precision stage,
   the re-sync windows and the FP64 fallback of the refinement stage, and the
   caps, on synthetic states.
+* Degenerate steps on constructed dot products: Gram-Schmidt breakdowns of y
+  and z (reading R7) and undefined later-step coefficients (reading R15).
 """
 import ctypes
 import os
@@ -81,12 +83,12 @@ def solve(lib, dots, first, sx, gs_tol=1e-14):
 
 def check(lib, *, E_prev, E_new, b=1.0, c=0.0, k=1.0, dz=1e-3, t=1, alpha=0, stage=1, prec=FP64,
           user_prec=FP64, n_sigma=10, n_stage1=0, n_sync=0, max_sigma=1000, refine_max_sigma=300,
-          p=osb.SBCIParams(), mixed_eps=1e-8, mixed_r=1e-4):
+          p=osb.SBCIParams(), mixed_eps=1e-8, mixed_r=1e-4, nxy=0.0):
     pr = np.array([p.eps0, p.r0, p.b_th, p.eps1, p.x_th1, p.x_th2, p.r1, mixed_eps, mixed_r, p.gs_tol,
                    E_prev, E_new, b, c, k], dtype=np.float64)
     ip = np.array([p.max_cycle, max_sigma, refine_max_sigma, user_prec, prec, stage, alpha, t, n_sigma,
                    n_stage1, n_sync], dtype=np.int32)
-    dots = np.array([1.0, 0.0, 1.0, dz * dz], dtype=np.float64)
+    dots = np.array([1.0, nxy, 1.0, dz * dz], dtype=np.float64)
     out = np.zeros(7, dtype=np.int32)
     halt = lib.host_ctl_check(_dptr(pr), _iptr(ip), _dptr(dots), _iptr(out))
     return halt, out
@@ -305,3 +307,26 @@ def test_undefined_later_step_takes_the_first_step_path(ctl):
     # the same problem posed as a first step gives the same parameters
     halt1, o1 = solve(ctl, dots, first=1, sx=1.0)
     assert halt1 == H_RUN and o1[11] == 0 and np.array_equal(o1[:4], o[:4])
+
+
+def test_gram_schmidt_breakdowns(ctl):
+    """Reading R7.  (1) After a step, y inside span{x} (N_xy^2 = N_xx N_yy):
+    the next step takes the first-step path (t = 0, first = 1) without a
+    restart record.  (2) A later step whose z lies in span{x, y}: c = 0 and
+    the 2x2 problem in (x, y).  (3) A first step whose z lies in span{x}: no
+    move (E = H_xx, c = 0, k = 1)."""
+    halt, out = check(ctl, E_prev=-2.0, E_new=-2.0 - 1e-6, dz=1e-3, t=4, nxy=1.0)
+    assert halt == H_RUN and out[0] == 0 and out[1] == 0 and out[2] == 1
+    halt, out = check(ctl, E_prev=-2.0, E_new=-2.0 - 1e-6, dz=1e-3, t=4, nxy=0.5)
+    assert halt == H_RUN and out[1] == 5 and out[2] == 0
+    Hxx, Hxy, Hyy = -1.0, 0.3, -0.5
+    #        NXX  NXY  NYY  HXX  HXY  HYY  ZPZP NXZ  NYZ  NZZ  HXZ  HYZ  HZZ
+    dots = [1.0, 0.0, 1.0, Hxx, Hxy, Hyy, 0.0, 1.0, 0.0, 1.0, Hxx, Hxy, Hxx]  # z = x
+    halt, o = solve(ctl, dots, first=0, sx=1.0)
+    w, U = np.linalg.eigh([[Hxx, Hxy], [Hxy, Hyy]])
+    assert halt == H_RUN and o[2] == 0.0 and abs(o[0] - w[0]) < 1e-14
+    assert abs(o[1] - U[1, 0] / U[0, 0]) < 1e-12  # b: y coefficient over x coefficient
+    assert abs(abs(o[3]) - 1.0 / abs(U[0, 0])) < 1e-12
+    dots = [4.0, 0.0, 0.0, 4.0 * Hxx, 0.0, 0.0, 0.0, 2.0, 0.0, 1.0, 2.0 * Hxx, 0.0, Hxx]  # |x| = 2, z = x/2
+    halt, o = solve(ctl, dots, first=1, sx=0.5)
+    assert halt == H_RUN and o[0] == Hxx and o[2] == 0.0 and o[3] == 1.0
