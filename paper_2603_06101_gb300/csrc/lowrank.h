@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "sbci_internal.h"
 
 namespace sbci {
@@ -25,5 +27,12 @@ namespace sbci {
 // precision of the contraction (prec 0: double, else float).
 cudaError_t launch_gather_contract_lr(const SigmaArgs &a, int prec, const void *Ut, const void *UL, int r,
                                       cudaStream_t s);
+
+// The factor on the host (strings.cpp): pivoted Cholesky of the pair matrix
+// V [np][np] plus the one-electron part (kappa, delta [np], N electrons).
+// Returns r + 2 with Ut = F^T [r+2][np] and UL = F M [np][r+2], or 0 when the
+// full form is kept.
+int df_factor(int np, const double *V, const double *kappa, const double *delta, int N,
+              std::vector<double> &Ut, std::vector<double> &UL);
 
 }  // namespace sbci

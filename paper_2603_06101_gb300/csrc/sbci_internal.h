@@ -231,12 +231,6 @@ cudaError_t launch_dav_precond(double *out, const double *in, const double *diag
 // Small dense symmetric eigen-solver (cyclic Jacobi), ascending eigenvalues,
 // eigenvectors in columns of V (row-major n x n), n <= kDavMaxSpace.
 void jacobi_eigh(int n, const double *A, double *w, double *V);
-// Density-fitted factor W = F M F^T of the packed operator (lowrank.h): the
-// pivoted Cholesky of the pair matrix V [np][np] plus the one-electron part
-// (kappa, delta [np], N electrons).  Returns r + 2 with Ut = F^T [r+2][np] and
-// UL = F M [np][r+2], or 0 when the full form is kept (strings.cpp).
-int df_factor(int np, const double *V, const double *kappa, const double *delta, int N,
-              std::vector<double> &Ut, std::vector<double> &UL);
 
 void set_error(const std::string &msg);
 

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <vector>
 
+#include "lowrank.h"
 #include "sbci_internal.h"
 
 namespace sbci {

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <string>
 
+#include "lowrank.h"
 #include "sbci_internal.h"
 
 namespace sbci {
