@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: batched mixed precision vs sequential FP64, p50/p99")
     ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the short serving stream in the default bench line")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-n14", action="store_true")
     ap.add_argument("--batch", type=int, default=16,
                     help="H10 solves per step, solved together by the batched persistent kernels "
                          "(1: one solve per step through its own graph loop)")
@@ -175,7 +179,8 @@ def oracle_solve_time(I, nstates, max_steps=None):
     t0 = time.perf_counter()
     done = True
     try:
-        run.solve(nstates)
+        res = run.solve(nstates)
+        oracle_solve_time.energies = [r.energy for r in res]
     except StopIteration:
         done = False
     return time.perf_counter() - t0, run.n_sigma, done
@@ -199,6 +204,31 @@ def whole_job_rate(world: int, units_per_rank: float, seconds_max: float) -> flo
     return world * units_per_rank / seconds_max
 
 
+GOLDEN_H10 = os.path.join(ROOT, "tests", "golden", "h10_sector_energies.json")
+
+
+def golden_energies():
+    """Exact H10 sector energies (total, hartree) written by the committed
+    oracle script tests/golden/make_sector_energies.py, or None."""
+    if not os.path.exists(GOLDEN_H10):
+        return None
+    with open(GOLDEN_H10) as f:
+        return np.array(json.load(f)["total"])
+
+
+def energy_errors(E, ref):
+    """Per-state |E - ref| of the sorted energies (None without a reference)."""
+    if ref is None:
+        return None
+    return [float(x) for x in np.abs(np.sort(np.asarray(E)) - np.sort(ref))]
+
+
+def percentiles(ms):
+    ms = np.asarray(ms, dtype=float)
+    return {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "samples": int(ms.size)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -208,26 +238,237 @@ def run_reference(args, rank, world):
     sample = 12  # H-products per bounded sample (initial guess + first SB steps)
     for _ in range(args.warmup):
         oracle_solve_time(I, NSTATES, max_steps=sample)
-    times = []
+    times, per = [], []
     for _ in range(args.steps):
         t, n, _ = oracle_solve_time(I, NSTATES, max_steps=sample)
-        times.append(t / n)
-    per_sigma = float(np.mean(times))
+        times.append(t)
+        per.append(t / n)
+    per_sigma = float(np.mean(per))
     value = 1.0 / (per_sigma * nsig_full)
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        # measured wall time of one timed step (one bounded sample), not 1/value
+        "ms_per_step": 1000.0 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "norb": 10, "ndet": 63504, "states": NSTATES, "sector": "c=c^T"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"each step: the first {sample} H-products of the oracle SBCI1 solve "
-                                   f"(time per H-product incl. its SB work), scaled by the "
-                                   f"{nsig_full} H-products of one full oracle solve ({t_full:.1f} s)"},
+                         "sample": f"each timed step: the first {sample} H-products of the oracle SBCI1 solve "
+                                   f"with their SB work ({1000.0 * float(np.mean(times)):.0f} ms); solves/s = 1 / "
+                                   f"(time per H-product x the {nsig_full} H-products of one full oracle "
+                                   f"solve, measured untimed before the steps: {t_full:.1f} s)"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+TF32_OF_BF16 = 0.5  # nominal dense TF32 / BF16 tensor rate (1.1 vs 2.25 PFLOP/s)
+SIGMA_FAMILIES = ("gather_contract_tc", "gather_contract_os", "gather_contract", "gather_contract_lr",
+                  "scatter", "symfinish", "fused_sigma")
+
+
+def family_of(name: str) -> str:
+    base = name[len("batch_"):] if name.startswith("batch_") else name
+    base = base[len("sigma_"):] if base.startswith("sigma_") else base
+    return {"update": "sb_update", "project": "sb_project"}.get(base, base)
+
+
+def roofline(name, launches, ms, dets_per_launch, npair, prec, pk, pk_kind, sm_mhz, alpha_avg=0.0):
+    """Roofline entry of one kernel family from its CUDA-event time.
+
+    Algorithmic counts of the measurement plan: one sigma moves 16 B per
+    determinant (c read, sigma written, FP64) and does 2 npair^2 flops per
+    determinant (packed pairs); one SB update sweep moves 96 B per determinant,
+    the projection 16 + 8 alpha.  The D/G scratch a kernel writes or reads is
+    not algorithmic: it is what the DRAM traffic figure shows on top."""
+    fam = family_of(name)
+    avg_s = ms / 1000.0 / max(launches, 1)
+    flops = 2.0 * npair * npair * dets_per_launch
+    hbm_peak = pk["hbm_gbs"]
+    if fam in SIGMA_FAMILIES:
+        bytes_alg = 16.0 * dets_per_launch
+        hbm = {"bound": "hbm", "achieved": bytes_alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "peak_kind": f"{pk_kind} copy bandwidth", "algorithmic_per_launch": bytes_alg,
+               "algorithmic_note": f"16 B per determinant per sigma (c read + sigma written, FP64) x "
+                                   f"{dets_per_launch} determinants"}
+        hbm["frac"] = hbm["achieved"] / hbm_peak
+        other = None
+        if fam in ("gather_contract_tc", "fused_sigma", "gather_contract_os"):
+            tpeak = pk.get("bf16_tflops", 1900.0) * (TF32_OF_BF16 if prec != "fp64" else 1.0)
+            note = ("TF32: measured bf16 x nominal TF32/BF16 ratio 0.5" if prec != "fp64"
+                    else "BF16 slices of the exact FP64 contraction: measured bf16")
+            other = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                     "peak_kind": f"{pk_kind} {note}", "algorithmic_per_launch": flops,
+                     "algorithmic_note": "2 npair^2 flops per determinant (the split precisions execute more)"}
+        elif fam in ("gather_contract", "gather_contract_lr"):
+            lanes = 2.0 if prec == "fp64" else 128.0
+            peak = 2.0 * lanes * 152 * sm_mhz * 1e6 / 1e12
+            other = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "peak_kind": f"{'FP64' if prec == 'fp64' else 'FP32'}: 152 SMs x {lanes:.0f} FMA/clk x 2 x "
+                                  f"median SM clock", "algorithmic_per_launch": flops}
+        if other:
+            other["frac"] = other["achieved"] / other["peak"]
+            hbm["other_ceiling"] = other
+        roof = hbm
+    else:
+        per_det = {"sb_update": 96.0, "sb_project": 16.0 + 8.0 * alpha_avg}.get(fam, 16.0)
+        bytes_alg = per_det * dets_per_launch
+        roof = {"bound": "hbm", "achieved": bytes_alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "peak_kind": f"{pk_kind} copy bandwidth", "algorithmic_per_launch": bytes_alg,
+                "algorithmic_note": f"{per_det:g} B per determinant x {dets_per_launch} determinants"}
+        roof["frac"] = roof["achieved"] / hbm_peak
+    roof["kernel"] = name
+    roof["avg_launch_us"] = avg_s * 1e6
+    roof["launches"] = int(launches)
+    roof["traffic"] = traffic_for(name)
+    return roof
+
+
+def serving_leg(n, slots, quiet=True):
+    """Serving stream over H6/H8/H10/H12 chains (1-4 states, spacing 0.7-3.0 A,
+    seed 4): (1) saturation run of the batched mixed-precision server (every
+    arrival at t = 0) -> capacity; (2) Poisson arrivals at 0.7 x capacity
+    through the server -> p50/p99 latency; (3) the same Poisson trace served by
+    plain FP64 SBCI1 one solve per launch, in arrival order -> p50/p99.
+    Latency = completion - arrival."""
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    base = inputs.serving_trace(n, seed=4, rate_per_s=float("inf"))
+    ints = [inputs.h_chain(r.natoms, r.spacing_angstrom) for r in base]
+    ks = [r.nstates for r in base]
+    # a seeded full-symmetry component in every start (start_noise): symmetric
+    # chains would otherwise let rounding decide which symmetry a state search
+    # explores, and the two precisions could meet different states
+    p_mixed = sbci.params(prec=sbci.SBCI_TF32X3, start_noise=1e-2, noise_seed=2603)
+    p_fp64 = sbci.params(prec=sbci.SBCI_FP64, start_noise=1e-2, noise_seed=2603)
+    budget = 64 << 30
+
+    def serve(arrivals, p):
+        server = sbci.Server(budget, slots)
+        t0 = time.perf_counter()
+        tickets, done, lat = {}, {}, {}
+        errors = {}
+        order = np.argsort(arrivals, kind="stable")
+        nxt = 0
+        while len(done) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[order[nxt]] <= now:
+                i = int(order[nxt])
+                tickets[i] = server.submit(ints[i], ks[i], p)
+                nxt += 1
+            server.progress()
+            for i, t in tickets.items():
+                if i in done:
+                    continue
+                r = server.poll(t)
+                if r is not None:
+                    done[i] = r
+                    if r[3] != 0:
+                        errors[i] = sbci.last_error()
+                    lat[i] = (time.perf_counter() - t0) - arrivals[i]
+        makespan = time.perf_counter() - t0
+        server.close()
+        return makespan, np.array([lat[i] for i in range(n)]), done, errors
+
+    # warm-up: one of each size through the server (graph builds, module loads)
+    warm = sbci.Server(budget, 4)
+    for sz in (6, 8, 10, 12):
+        t = warm.submit(inputs.h_chain(sz, 1.0), 1, p_mixed)
+        while warm.poll(t) is None:
+            warm.progress()
+    warm.close()
+    torch.cuda.synchronize()
+    sat_span, _, _, _ = serve(np.zeros(n), p_mixed)
+    capacity = n / sat_span
+    rate = 0.7 * capacity
+    gaps = np.random.default_rng(4).exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    span_m, lat_m, done_m, errors_m = serve(arrivals, p_mixed)
+    # plain FP64, one solve per launch, in arrival order
+    t0 = time.perf_counter()
+    lat_f = np.zeros(n)
+    E_f, st_f = {}, {}
+    for i in np.argsort(arrivals, kind="stable"):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        ctx = sbci.Context.from_integrals(ints[i])
+        E, _, _, st = ctx.solve(ks[i], p_fp64)
+        ctx.close()
+        E_f[int(i)] = E
+        st_f[int(i)] = int(st)
+        lat_f[i] = (time.perf_counter() - t0) - arrivals[i]
+    span_f = time.perf_counter() - t0
+    diff = [float(np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max()) for i in range(n)]
+    bad = [i for i in range(n) if diff[i] > 1e-6]
+    out = {
+        "requests": n, "trace": "H6/H8/H10/H12 STO-3G, spacing U(0.7, 3.0) A, 1-4 states, seed 4; "
+                                "Poisson arrivals at 0.7 x the saturation capacity",
+        "saturation_solves_per_s": capacity, "poisson_rate_per_s": rate,
+        "batched_tf32x3": {"solves_per_s": n / span_m, "p50_s": float(np.percentile(lat_m, 50)),
+                           "p99_s": float(np.percentile(lat_m, 99)), "slots": slots},
+        "fp64_one_solve_per_launch": {"solves_per_s": n / span_f, "p50_s": float(np.percentile(lat_f, 50)),
+                                      "p99_s": float(np.percentile(lat_f, 99))},
+        "max_energy_diff_mixed_vs_fp64_hartree": float(max(diff)),
+        "requests_differing_by_more_than_1e-6": len(bad),
+        "sizes": {str(sz): int(sum(1 for r in base if r.natoms == sz)) for sz in (6, 8, 10, 12)},
+    }
+    if not quiet:
+        out["differing"] = [{"request": i, "natoms": base[i].natoms, "spacing": base[i].spacing_angstrom,
+                             "k": ks[i], "E_mixed": [float(e) for e in done_m[i][0]],
+                             "status_mixed": int(done_m[i][3]), "E_fp64": [float(e) for e in E_f[i]],
+                             "status_fp64": st_f[i], "error_mixed": errors_m.get(i)} for i in bad]
+    return out
+
+
+def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
+    """Random density-fitted integrals, n = 14, 7 alpha / 7 beta (seed 14;
+    11,778,624 determinants): one TF32x3 sigma and one FP64 sigma timed per
+    kernel with CUDA events on the library stream (roofline of each), then the
+    2-state solve in mixed precision with FP64 refinement (solve time, FP64
+    residual per state)."""
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    I = inputs.random_df(14, 14)
+    ctx = sbci.Context.from_integrals(I)
+    c = torch.from_numpy(inputs.random_vector(ctx.na, ctx.nb, 1)).cuda()
+    out = torch.empty_like(c)
+    res = {"workload": "random density-fitted integrals n=14, 7a/7b, seed 14", "ndet": ctx.ndet,
+           "npair": ctx.npair}
+    for tag, prec, pname in (("tf32x3", sbci.SBCI_TF32X3, "tf32x3"), ("fp64", sbci.SBCI_FP64, "fp64")):
+        ctx.sigma(c, out, prec=prec)  # warm-up (scratch allocation)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        t0 = time.perf_counter()
+        for _ in range(reps if prec != sbci.SBCI_FP64 else 1):
+            ctx.sigma(c, out, prec=prec)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = ctx.profile_read()
+        ctx.profile(False)
+        st = {k: v for k, v in st.items() if v[0] and k.startswith("sigma_")}
+        nsig = reps if prec != sbci.SBCI_FP64 else 1
+        dom = max(st.items(), key=lambda kv: kv[1][1])
+        res[f"sigma_{tag}"] = {
+            "ms_per_sigma": sum(v[1] for v in st.values()) / nsig, "wall_ms_per_sigma": 1e3 * wall / nsig,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in st.items()},
+            "roofline": roofline(dom[0], dom[1][0], dom[1][1], ctx.ndet, ctx.npair, pname, pk, pk_kind, sm_mhz)}
+    p = sbci.params(prec=sbci.SBCI_TF32X3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, _, R, st = ctx.solve(2, p)
+    torch.cuda.synchronize()
+    res["solve_tf32x3_2_states"] = {
+        "seconds": time.perf_counter() - t0, "status": int(st), "energies": [float(e) for e in E],
+        "fp64_residual_per_state": [float(r.residual) for r in R],
+        "converged": [int(r.converged) for r in R], "sigma_per_state": [int(r.n_sigma) for r in R],
+        "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R]}
+    ctx.close()
+    return res
 
 
 def run_gb300(args, rank, world, local_rank):
@@ -248,6 +489,7 @@ def run_gb300(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     B = max(1, args.batch) if args.prec == "tf32x3" else 1
     batch_ctx = [ctx] + [sbci.Context.from_integrals(I, stream=stream.cuda_stream) for _ in range(B - 1)]
+    ref_E = golden_energies()
 
     def one_solve():
         if B == 1:
@@ -255,9 +497,26 @@ def run_gb300(args, rank, world, local_rank):
             return E, R, st
         E, R, st = sbci.solve_batch(batch_ctx, NSTATES, p)
         one_solve.launches += sbci.solve_batch.last_launches
+        one_solve.all_E = E
         return E[0], R[:NSTATES], st
 
     one_solve.launches = 0
+    one_solve.all_E = None
+
+    def timed_solves(fn, steps):
+        """CUDA-event time of each call on the library stream, L2 flushed before each."""
+        out = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)  # L2 flush: 256 MB > 129 MB L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out, r
 
     for _ in range(max(args.warmup, 3)):
         E, R, st = one_solve()
@@ -272,18 +531,9 @@ def run_gb300(args, rank, world, local_rank):
     torch.cuda.synchronize()
     sampler.start()
     one_solve.launches = 0
-    t_ms = 0.0
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)  # L2 flush: 256 MB > 129 MB L2
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        E, R, st = one_solve()
-        e1.record(stream)
-        e1.synchronize()
-        t_ms += e0.elapsed_time(e1)
+    step_ms, (E, R, st) = timed_solves(one_solve, args.steps)
+    t_ms = float(sum(step_ms))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if dist:
@@ -293,22 +543,28 @@ def run_gb300(args, rank, world, local_rank):
     launches = sum(v[0] for v in stats.values()) if B == 1 else one_solve.launches
     t_max = max_over_ranks(t_ms, dist)
     value = whole_job_rate(world, B * args.steps, t_max / 1000.0)
-    # ---------------- one solve alone (latency), same event timing
+    all_E = one_solve.all_E if B > 1 else np.asarray([E])
+    err_batch = None
+    if ref_E is not None:
+        err_batch = [max(energy_errors(Ei, ref_E)[s] for Ei in all_E) for s in range(NSTATES)]
+    # ---------------- one solve per launch: the same workload with the mixed
+    # sigma, and plain FP64 SBCI1 (latency per solve = its CUDA-event time)
     single = None
+    fp64_arm = None
     if B > 1:
-        ts = 0.0
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.solve(NSTATES, p)
-            e1.record(stream)
-            e1.synchronize()
-            ts += e0.elapsed_time(e1)
-        single = {"solves_per_s": args.steps / (ts / 1000.0), "ms_per_solve": ts / args.steps,
-                  "engine": "one graph loop per solve"}
+        ms1, (E1, _, R1, st1) = timed_solves(lambda: ctx.solve(NSTATES, p), args.steps)
+        single = {"solves_per_s": len(ms1) / (sum(ms1) / 1000.0), "ms_per_solve": float(np.mean(ms1)),
+                  "latency": percentiles(ms1), "engine": "one graph loop per solve", "sigma_precision": args.prec,
+                  "energy_err_vs_oracle": energy_errors(E1, ref_E)}
+    if args.prec != "fp64":
+        p64 = sbci.params(sector=1, prec=sbci.SBCI_FP64)
+        ctx.solve(NSTATES, p64)  # warm-up: the FP64 graph
+        k64 = min(args.steps, 10)
+        ms64, (E64, _, R64, st64) = timed_solves(lambda: ctx.solve(NSTATES, p64), k64)
+        fp64_arm = {"solves_per_s": len(ms64) / (sum(ms64) / 1000.0), "ms_per_solve": float(np.mean(ms64)),
+                    "latency": percentiles(ms64), "engine": "plain FP64 SBCI1, one graph loop per solve",
+                    "status": int(st64), "sigma_per_solve": int(sum(r.n_sigma for r in R64)),
+                    "energies": [float(e) for e in E64], "energy_err_vs_oracle": energy_errors(E64, ref_E)}
     # ---------------- kernel timing pass: the same solves with each step kernel
     # launched on its own and bracketed by CUDA events on the launching stream
     kt0 = torch.cuda.Event(enable_timing=True)
@@ -335,72 +591,16 @@ def run_gb300(args, rank, world, local_rank):
         units = B  # every batched launch serves the B solves (same Hamiltonian: they halt together)
     # ---------------- roofline of the dominant kernel
     pk, pk_kind = peaks()
-    dom = max(kstats.items(), key=lambda kv: kv[1][1])
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    kst = {k: v for k, v in kstats.items() if v[0]}
+    dom = max(kst.items(), key=lambda kv: kv[1][1])
     name, (nl, ms) = dom
     npair, ndet = ctx.npair, ctx.ndet
-    avg_s = ms / 1000.0 / max(nl, 1)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    flops = 2.0 * npair * npair * ndet * units
-    base = name[len("batch_"):] if name.startswith("batch_") else name
-    base = {"update": "sb_update", "project": "sb_project", "scatter": "sigma_scatter"}.get(base, base)
-    if base == "gather_contract_tc" or base == "sigma_gather_contract_tc":
-        # two ceilings: the contraction on the tensor pipe and the HBM traffic the
-        # kernel must move (G written, 4 B per pair, and the FP32 z read, 4 B, per
-        # determinant); the larger ideal time is the binding one
-        tpeak = pk.get("bf16_tflops", 1900.0) * 0.5  # TF32 dense = half the BF16 rate (1.1 vs 2.25 PF)
-        bytes_alg = float(4 * npair + 4) * ndet * units
-        t_tensor = flops / (tpeak * 1e12)
-        t_hbm = bytes_alg / (pk["hbm_gbs"] * 1e9)
-        tensor = {"achieved": flops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
-                  "frac": flops / avg_s / 1e12 / tpeak, "algorithmic_per_launch": flops,
-                  "peak_kind": f"{pk_kind} bf16 x nominal TF32/BF16 ratio 0.5; algorithmic 2 npair^2 flops "
-                               "per determinant (the 3-term split executes 3x)"}
-        hbm = {"achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-               "frac": bytes_alg / avg_s / 1e9 / pk["hbm_gbs"], "algorithmic_per_launch": bytes_alg,
-               "peak_kind": pk_kind, "algorithmic_note": f"{4 * npair + 4} B per determinant (G write + z read)"}
-        if t_hbm >= t_tensor:
-            roof = {"bound": "hbm", **hbm, "other_ceiling": {"bound": "tensor", **tensor}}
-        else:
-            roof = {"bound": "tensor", **tensor, "other_ceiling": {"bound": "hbm", **hbm}}
-    elif base == "sigma_gather_contract_os":
-        # FP64 contraction by exact BF16 slices: the HBM traffic it must move (G
-        # written in FP64, 8 B per pair, and c read, 8 B, per determinant) and the
-        # tensor work it executes (34 slice products of 2 Kp Np flops, Kp = Np = 64)
-        bytes_alg = float(8 * npair + 8) * ndet * units
-        xflops = 34.0 * 2 * 64 * 64 * ndet * units
-        tpeak = pk.get("bf16_tflops", 1900.0)
-        hbm = {"achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-               "frac": bytes_alg / avg_s / 1e9 / pk["hbm_gbs"], "algorithmic_per_launch": bytes_alg,
-               "peak_kind": pk_kind, "algorithmic_note": f"{8 * npair + 8} B per determinant (FP64 G write + c read)"}
-        tensor = {"achieved": xflops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
-                  "frac": xflops / avg_s / 1e12 / tpeak, "algorithmic_per_launch": xflops,
-                  "peak_kind": f"{pk_kind} bf16; executed slice products (34 of 2 x 64 x 64 flops per determinant)"}
-        if bytes_alg / (pk["hbm_gbs"] * 1e9) >= xflops / (tpeak * 1e12):
-            roof = {"bound": "hbm", **hbm, "other_ceiling": {"bound": "tensor", **tensor}}
-        else:
-            roof = {"bound": "tensor", **tensor, "other_ceiling": {"bound": "hbm", **hbm}}
-    elif base == "sigma_gather_contract" and args.prec == "fp64":
-        peak = 4.0 * 152 * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA per clock per SM (1.25 TF/s at 2.07 GHz)
-        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_kind": "FP64: 152 SMs x 2 FMA/clk x 2 flop x median SM clock (the 1.25 TFLOP/s nominal)",
-                "algorithmic_per_launch": flops}
-    elif base == "sigma_gather_contract":
-        peak = 2.0 * 152 * 128 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_kind": "FP32: 152 SMs x 128 lanes x 2 flop x median SM clock",
-                "algorithmic_per_launch": flops}
-    else:
-        gsz = 8 if args.prec == "fp64" else 4
-        per_det = {"sigma_scatter": npair * gsz + 8, "sb_update": 12 * 8, "sb_project": 4 * 8}.get(base, 16)
-        bytes_alg = float(per_det) * ndet * units
-        roof = {"bound": "hbm", "achieved": bytes_alg / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "peak_kind": pk_kind, "algorithmic_per_launch": bytes_alg,
-                "algorithmic_note": f"{per_det} B per determinant x {units} solves"}
-    roof["kernel"] = name
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_for(name)
-    roof["avg_launch_us"] = avg_s * 1e6
+    alpha_avg = (NSTATES - 1) / 2.0
+    roof = roofline(name, nl, ms, ndet * units, npair, args.prec, pk, pk_kind, sm_mhz, alpha_avg)
     roof["share_of_timing_pass"] = ms / max(kpass_ms, 1e-9)
+    kernel_rooflines = {k: roofline(k, v[0], v[1], ndet * units, npair, args.prec, pk, pk_kind, sm_mhz, alpha_avg)
+                        for k, v in kst.items() if family_of(k) not in ("end", "reduce", "dots", "lincomb")}
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -425,13 +625,23 @@ def run_gb300(args, rank, world, local_rank):
         e2e = {"value": whole_job_rate(world, B * args.steps, te), "unit": "solves/s",
                "h2d_bytes_per_step": int(B * (h1.nbytes + eri.nbytes)),
                "d2h_bytes_per_step": int(d2h)}
+    # ---------------- further workloads of the measurement plan (rank 0, N = 1)
+    serving = None
+    n14 = None
+    if rank == 0 and world == 1:
+        if not args.no_serving:
+            serving = serving_leg(args.serving_requests, args.slots)
+        if not args.no_n14:
+            n14 = random_df_leg(pk, pk_kind, sm_mhz)
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
+    oracle_same_run = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_full, nsig_o, _ = oracle_solve_time(I, NSTATES)
         cpu = {"value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one full oracle SBCI1 solve of the same workload ({nsig_o} H-products, "
                          f"{t_full:.1f} s, numpy/OpenBLAS on all host cores)"}
+        oracle_same_run = energy_errors(E, np.asarray(oracle_solve_time.energies) + I.e_core)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -447,8 +657,15 @@ def run_gb300(args, rank, world, local_rank):
                        "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R],
                        "controller_us_per_step": sum(r.ctl_cycles for r in R) / max(nsig, 1) / (clocks.get("sm_mhz") or 2070.0),
                        "energies": [float(e) for e in E]},
+            "latency": percentiles(step_ms),
+            "energy_err_vs_oracle": err_batch,
+            "energy_err_vs_oracle_note": "per state, max over the step's solves, |E - E_exact| against the "
+                                         "oracle's exact sector energies (tests/golden/h10_sector_energies.json)",
+            "energy_err_vs_oracle_sbci1_same_run": oracle_same_run,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "single_solve": single,
+            "single_solve": single, "fp64_one_solve_per_launch": fp64_arm,
+            "serving": serving, "random_df_n14": n14,
+            "kernel_rooflines": kernel_rooflines,
             "autotuner": sbci.batch_classes() if B > 1 else None,
             "launches_timed": {k: v[0] for k, v in stats.items() if v[0]},
             "kernels_timing_pass": {k: {"launches": v[0], "ms": v[1]} for k, v in kstats.items() if v[0]},
@@ -569,107 +786,10 @@ def run_davidson(args):
 
 
 def run_serving(args):
-    """Serving stream over H6/H8/H10/H12 chains (1-4 states, spacing 0.7-3.0 A).
-
-    1. saturation run of the batched mixed-precision server (all arrivals at
-       t = 0) -> capacity;  2. Poisson arrivals at 0.7 x capacity through the
-    server -> p50/p99 latency;  3. the same Poisson trace served by plain FP64
-    one solve at a time (each solve alone, in arrival order) -> p50/p99 and
-    solves/s.  Latency = completion - arrival.
-    """
-    import torch
-
-    from paper_2603_06101_gb300 import inputs, sbci
-
-    n = args.requests
-    base = inputs.serving_trace(n, seed=4, rate_per_s=float("inf"))
-    ints = [inputs.h_chain(r.natoms, r.spacing_angstrom) for r in base]
-    ks = [r.nstates for r in base]
-    # a seeded full-symmetry component in every start (start_noise): symmetric
-    # chains would otherwise let rounding decide which symmetry a state search
-    # explores, and the two precisions could meet different states
-    p_mixed = sbci.params(prec=sbci.SBCI_TF32X3, start_noise=1e-2, noise_seed=2603)
-    p_fp64 = sbci.params(prec=sbci.SBCI_FP64, start_noise=1e-2, noise_seed=2603)
-    budget = 64 << 30
-
-    def serve(arrivals, p, slots):
-        server = sbci.Server(budget, slots)
-        t0 = time.perf_counter()
-        tickets, done, lat = {}, {}, {}
-        serve.errors = {}
-        order = np.argsort(arrivals, kind="stable")
-        nxt = 0
-        while len(done) < n:
-            now = time.perf_counter() - t0
-            while nxt < n and arrivals[order[nxt]] <= now:
-                i = int(order[nxt])
-                tickets[i] = server.submit(ints[i], ks[i], p)
-                nxt += 1
-            server.progress()
-            for i, t in tickets.items():
-                if i in done:
-                    continue
-                r = server.poll(t)
-                if r is not None:
-                    done[i] = r
-                    if r[3] != 0:
-                        serve.errors[i] = sbci.last_error()
-                    lat[i] = (time.perf_counter() - t0) - arrivals[i]
-        makespan = time.perf_counter() - t0
-        server.close()
-        return makespan, np.array([lat[i] for i in range(n)]), done
-
-    # warm-up: one of each size through the server (graph builds, module loads)
-    warm = sbci.Server(budget, 4)
-    for sz in (6, 8, 10, 12):
-        t = warm.submit(inputs.h_chain(sz, 1.0), 1, p_mixed)
-        while warm.poll(t) is None:
-            warm.progress()
-    warm.close()
-    torch.cuda.synchronize()
-    sat_span, sat_lat, _ = serve(np.zeros(n), p_mixed, args.slots)
-    capacity = n / sat_span
-    rate = 0.7 * capacity
-    gaps = np.random.default_rng(4).exponential(1.0 / rate, size=n)
-    arrivals = np.cumsum(gaps) - gaps[0]
-    span_m, lat_m, done_m = serve(arrivals, p_mixed, args.slots)
-    errors_m = dict(serve.errors)
-    # plain FP64, one solve per launch, in arrival order
-    t0 = time.perf_counter()
-    lat_f = np.zeros(n)
-    E_f, st_f = {}, {}
-    for i in np.argsort(arrivals, kind="stable"):
-        while time.perf_counter() - t0 < arrivals[i]:
-            pass
-        ctx = sbci.Context.from_integrals(ints[i])
-        E, _, _, st = ctx.solve(ks[i], p_fp64)
-        ctx.close()
-        E_f[int(i)] = E
-        st_f[int(i)] = int(st)
-        lat_f[i] = (time.perf_counter() - t0) - arrivals[i]
-    span_f = time.perf_counter() - t0
-    err = max(float(np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max()) for i in range(n))
-    err0 = max(float(abs(done_m[i][0][0] - E_f[i][0])) for i in range(n))
-    bad = [i for i in range(n) if np.abs(np.sort(done_m[i][0]) - np.sort(E_f[i])).max() > 1e-6]
-    nbad = len(bad)
-    details = [{"request": i, "natoms": base[i].natoms, "spacing": base[i].spacing_angstrom, "k": ks[i],
-                "E_mixed": [float(e) for e in done_m[i][0]], "status_mixed": int(done_m[i][3]),
-                "converged_mixed": [int(r.converged) for r in done_m[i][1]],
-                "n_sigma_mixed": [int(r.n_sigma) for r in done_m[i][1]],
-                "E_fp64": [float(e) for e in E_f[i]], "status_fp64": st_f[i],
-                "error_mixed": errors_m.get(i)} for i in bad]
-    line = {
-        "serving": f"{n} requests, H6/H8/H10/H12 STO-3G, spacing U(0.7, 3.0) A, 1-4 states (seed 4)",
-        "saturation_solves_per_s": capacity, "poisson_rate_per_s": rate,
-        "batched_tf32x3": {"solves_per_s": n / span_m, "p50_s": float(np.percentile(lat_m, 50)),
-                           "p99_s": float(np.percentile(lat_m, 99)), "slots": args.slots},
-        "sequential_fp64": {"solves_per_s": n / span_f, "p50_s": float(np.percentile(lat_f, 50)),
-                            "p99_s": float(np.percentile(lat_f, 99))},
-        "max_energy_diff_mixed_vs_fp64_hartree": err, "max_ground_state_diff_hartree": err0,
-        "requests_differing_by_more_than_1e-6": nbad, "differing": details,
-        "sizes": {str(sz): int(sum(1 for r in base if r.natoms == sz)) for sz in (6, 8, 10, 12)},
-    }
-    print(json.dumps(line), flush=True)
+    """The serving stream alone (``--serving``): ``--requests`` requests through
+    the batched mixed-precision server against plain FP64 one solve per launch
+    (see serving_leg), with the differing requests listed."""
+    print(json.dumps({"serving": serving_leg(args.requests, args.slots, quiet=False)}), flush=True)
 
 
 def main():

@@ -208,9 +208,12 @@ sbci_status sbci_sigma(sbci_ctx *ctx, const double *c, double *sigma, int nvec,
  * array: calls that overlap on the GPU (other streams, other threads, other
  * contexts) race and give wrong results; serialise them.  The array keeps
  * the last call's contents; every call overwrites all of the part it reads.
- * Errors: SBCI_ERR_INVALID for NULL arguments or a space whose scratch
- * (npair * Ndet * 8 bytes) exceeds the array; SBCI_ERR_CUDA on a launch
- * error.  Never calls cudaMalloc, cudaFree or an allocating library routine. */
+ * The context's device must be the current CUDA device (the array's address
+ * is per device).
+ * Errors: SBCI_ERR_INVALID for NULL arguments, a space whose scratch
+ * (npair * Ndet * 8 bytes) exceeds the array, or a current device other than
+ * the context's; SBCI_ERR_CUDA on a launch error.  Never calls cudaMalloc,
+ * cudaFree or an allocating library routine. */
 sbci_status sbci_sigma_noalloc(const sbci_ctx *ctx, const double *c, double *sigma,
                                void *cuda_stream);
 

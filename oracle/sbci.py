@@ -15,8 +15,8 @@ Follows Algorithm 1 (SBCI1 for state alpha) with Sections S1.1-S1.5:
 * residual z' (Eq. S29 / Eq. S60) and convergence (Eq. S30 / Eq. S61);
 * norm-triggered restart (Eqs. S62a-c and max_cycle).
 
-Readings where the paper is silent or ambiguous (each is listed with its
-reason in the design notes of the repository):
+Readings where the paper is silent or ambiguous, each with the reason it is
+taken:
 
 R1  z' = (X - E x)/k (Eqs. S29/S60); |z'| is then the residual norm of the
     unit vector x/|x| because |k| = |x| (Eq. S62b).
@@ -123,6 +123,23 @@ def _guarded(d: np.ndarray, guard: float) -> np.ndarray:
 def _sym(v: np.ndarray, shape) -> np.ndarray:
     m = v.reshape(shape)
     return (0.5 * (m + m.T)).reshape(-1)
+
+
+def restart_cause(p, alpha, b, k, dE, dz, t):
+    """Restart test of Section S1.5 after a step that did not converge, in the
+    order the paper lists it: Eq. S62a (alpha > 0, |b| < b_th and the energy
+    change below eps1), Eq. S62b (|k| = |x_{t+1}| outside [x_th1, x_th2]),
+    Eq. S62c (|z'| > r1 on a later step, t > 0), then the max_cycle period
+    (reading R5: t + 1 reaches max_cycle).  Returns "a", "b", "c", "max" or ""."""
+    if alpha > 0 and abs(b) < p.b_th and dE < p.eps1:
+        return "a"
+    if abs(k) < p.x_th1 or abs(k) > p.x_th2:
+        return "b"
+    if dz > p.r1 and t > 0:
+        return "c"
+    if t + 1 >= p.max_cycle:
+        return "max"
+    return ""
 
 
 class SBCI1:
@@ -245,15 +262,7 @@ class SBCI1:
                 self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz, "converged"))
                 return StateResult(E_new, x / np.linalg.norm(x), True, self.n_sigma - sigma0,
                                    nstep, restarts), second
-            cause = ""
-            if alpha > 0 and abs(b) < p.b_th and dE < p.eps1:
-                cause = "a"
-            elif abs(k) < p.x_th1 or abs(k) > p.x_th2:
-                cause = "b"
-            elif dz > p.r1 and t > 0:
-                cause = "c"
-            elif t + 1 >= p.max_cycle:
-                cause = "max"
+            cause = restart_cause(p, alpha, b, k, dE, dz, t)
             self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz,
                                          f"restart:{cause}" if cause else ("undef" if undefined else "")))
             E = E_new

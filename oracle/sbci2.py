@@ -20,8 +20,8 @@ lowest upward while the pair (alpha, alpha+1) is updated together
   (Eqs. S98-S100, S126-S128);
 * restarts S130a-c and max_cycle = 10 (Section S2.5).
 
-Readings where the paper is silent or ambiguous (each also listed in the
-design notes of the repository):
+Readings where the paper is silent or ambiguous, each with the reason it is
+taken:
 
 Q1  Start vectors: determinants by ascending (D_I, I), symmetrised when
     sector = 1 and Gram-Schmidt orthonormalised (dropped below gs_tol), until

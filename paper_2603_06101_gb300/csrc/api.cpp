@@ -129,6 +129,7 @@ struct sbci_ctx {
   double *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
   int *d_status = nullptr, *h_status = nullptr;  // device error word (bounded waits)
   int nsm = 1;
+  int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
   size_t tmp_elems = 0;
@@ -1900,6 +1901,7 @@ int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_grid(c->ndet, c->nsm)
 int sbci::ctx_scatter_blocks(const sbci_ctx *c) { return scatter_grid(c->ndet, c->nsm); }
 int sbci::ctx_symfin_blocks(const sbci_ctx *c) { return use_symfin(c) ? symfin_grid(c->Na, c->nsm) : 0; }
 long long sbci::ctx_ndet(const sbci_ctx *c) { return c->ndet; }
+int sbci::ctx_device(const sbci_ctx *c) { return c->device; }
 
 long long sbci::ctx_launch_count(const sbci_ctx *c) {
   long long n = 0;
@@ -2075,6 +2077,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
   TRY(cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"));
   c->nsm = std::max(nsm, 1);
+  c->device = dev;
   c->grid = 8 * c->nsm;  // upper bound of every kernel's block count that writes partials
   TRY(cuda_ok(prepare_sigma_kernels(), "kernel attributes"));
   // packed operator W[P][Q], P = (i>=j), Q = (k>=l):

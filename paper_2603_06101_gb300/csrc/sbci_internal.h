@@ -253,6 +253,7 @@ int ctx_step_blocks(const sbci_ctx *c);
 int ctx_scatter_blocks(const sbci_ctx *c);
 int ctx_symfin_blocks(const sbci_ctx *c);  // 0 unless the solve uses the singlet-sector split
 long long ctx_ndet(const sbci_ctx *c);
+int ctx_device(const sbci_ctx *c);  // CUDA device the context was created on
 long long ctx_launch_count(const sbci_ctx *c);
 size_t ctx_device_bytes(int norb, int nalpha, int nbeta, int k);
 

@@ -65,6 +65,15 @@ extern "C" sbci_status sbci_sigma_noalloc(const sbci_ctx *ctx, const double *c, 
               std::to_string((size_t)SBCI_NOALLOC_SCRATCH_BYTES) + "; use sbci_sigma");
     return SBCI_ERR_INVALID;
   }
+  // the kernels run on the context's device, and the scratch address below is
+  // the array on the current device: the two must be the same GPU
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx_device(ctx)) {
+    set_error("sbci_sigma_noalloc: the current CUDA device (" + std::to_string(cur) +
+              ") is not the context's device (" + std::to_string(ctx_device(ctx)) +
+              "); make the context's device current first");
+    return SBCI_ERR_INVALID;
+  }
   if (cuda_stream) s = (cudaStream_t)cuda_stream;
   void *G = nullptr;
   cudaError_t e = scratch_address(&G);

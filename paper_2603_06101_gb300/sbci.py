@@ -151,6 +151,12 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _torch_float64():
+    import torch
+
+    return torch.float64
+
+
 def params(**kw) -> sbci_params:
     lib = load()
     p = sbci_params()
@@ -227,12 +233,31 @@ class Context:
         return out
 
     def sigma_noalloc(self, c, out, stream=None):
-        """FP64 sigma of one device vector into ``out`` (device), allocation-free,
-        asynchronous on ``stream`` (a cudaStream_t handle) or the context stream."""
-        pc, dev = _ptr(c)
-        po, dev2 = _ptr(out)
-        assert dev and dev2, "sigma_noalloc takes device tensors"
-        _check(self._lib.sbci_sigma_noalloc(self._h, pc, po, C.c_void_p(stream) if stream else None))
+        """FP64 sigma of one device vector into ``out`` without any allocation.
+
+        ``c`` and ``out``: contiguous float64 CUDA tensors of exactly ``ndet``
+        elements on the context's device.  The call is queued on ``stream`` (a
+        cudaStream_t handle) or, by default, on torch's current stream of that
+        device, so torch work issued later on the same stream sees ``out``."""
+        for name, t in (("c", c), ("out", out)):
+            if not hasattr(t, "data_ptr"):
+                raise TypeError(f"sigma_noalloc: {name} must be a torch tensor")
+            if t.dtype != _torch_float64():
+                raise TypeError(f"sigma_noalloc: {name} must be float64, got {t.dtype}")
+            if t.numel() != self.ndet:
+                raise ValueError(f"sigma_noalloc: {name} must hold ndet = {self.ndet} elements, got {t.numel()}")
+            if not t.is_contiguous():
+                raise ValueError(f"sigma_noalloc: {name} must be contiguous")
+        if c.device != out.device:
+            raise ValueError("sigma_noalloc: c and out must be on the same device")
+        if not c.is_cuda:
+            raise ValueError("sigma_noalloc: c and out must be CUDA tensors")
+        if stream is None:
+            import torch
+
+            stream = torch.cuda.current_stream(c.device).cuda_stream
+        _check(self._lib.sbci_sigma_noalloc(self._h, C.c_void_p(c.data_ptr()), C.c_void_p(out.data_ptr()),
+                                            C.c_void_p(stream) if stream else None))
         return out
 
     def begin(self, k, p: sbci_params | None = None, c0=None):

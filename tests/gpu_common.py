@@ -49,3 +49,28 @@ def rel_err(a, b):
     a = np.asarray(a).reshape(-1)
     b = np.asarray(b).reshape(-1)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_sector_energies(key, k):
+    """Lowest k electronic energies of H in the c = c^T sector (n_alpha =
+    n_beta): Lanczos (oracle.eigen.lowest_lanczos) on S H S, S the
+    symmetriser c -> (c + c^T)/2.  The antisymmetric complement maps to 0, so
+    for the negative electronic energies of these systems the k lowest
+    eigenvalues of S H S are the sector's."""
+    from oracle import eigen
+
+    ora = oracle_sigma(key)
+    na, nb = ora.Na, ora.Nb
+    assert na == nb
+
+    def apply(v):
+        m = v.reshape(na, nb)
+        h = ora.apply(0.5 * (m + m.T))
+        return 0.5 * (h + h.T)
+
+    v0 = np.random.default_rng(7).standard_normal(na * nb).reshape(na, nb)
+    v0 = (v0 + v0.T).reshape(-1)
+    w, _ = eigen.lowest_lanczos(apply, na * nb, k, v0=v0)
+    assert w.max() < -1e-3, "sector energies must be negative for the projection to isolate them"
+    return w

@@ -158,3 +158,38 @@ def test_binding_prototypes_match_the_header(lib_path):
         assert [_kind_ctypes(t) for t in fn.argtypes] == [_kind_c(a) for a in args], name
         want_ret = {"sbci_status": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p}[ret]
         assert fn.restype is want_ret, (name, ret)
+
+
+def test_sigma_noalloc_wrapper_rejects_bad_tensors_before_the_library():
+    """The binding checks dtype, size, contiguity and device of c and out
+    before any call into the library (a wrong tensor would let the kernels read
+    or write past the caller's buffer)."""
+    torch = pytest.importorskip("torch")
+    from paper_2603_06101_gb300 import sbci
+
+    class FakeLib:
+        calls = 0
+
+        def sbci_sigma_noalloc(self, *a):
+            FakeLib.calls += 1
+            return 0
+
+    ctx = object.__new__(sbci.Context)
+    ctx._lib = FakeLib()
+    ctx._h = None
+    ctx.ndet = 16
+    good = torch.zeros(16, dtype=torch.float64)
+    cases = [
+        (torch.zeros(16, dtype=torch.float32), good, TypeError),   # wrong dtype of c
+        (good, torch.zeros(16, dtype=torch.float32), TypeError),   # wrong dtype of out
+        (torch.zeros(15, dtype=torch.float64), good, ValueError),  # short c
+        (good, torch.zeros(17, dtype=torch.float64), ValueError),  # long out
+        (torch.zeros(32, dtype=torch.float64)[::2], good, ValueError),  # not contiguous
+        (good, good.clone(), ValueError),                          # host tensors
+        (good.numpy(), good, TypeError),                           # not a tensor
+    ]
+    for c, out, exc in cases:
+        with pytest.raises(exc):
+            ctx.sigma_noalloc(c, out)
+    assert FakeLib.calls == 0
+    ctx._h = None

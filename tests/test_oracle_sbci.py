@@ -239,3 +239,39 @@ def test_r15_later_step_undefined_and_first_step_fallback():
     assert np.all(np.isfinite([E1, b1, c1, k1]))
     B = np.linalg.qr(np.stack([xn, z], axis=1))[0]
     assert abs(E1 - np.linalg.eigvalsh(B.T @ Hm @ B)[0]) < 1e-12
+
+
+def test_restart_cause_on_constructed_scalars():
+    """Section S1.5, Eqs. S62a-c with the paper's thresholds (b_th = 1e-2,
+    eps1 = 1e-7, x_th1 = 0.1, x_th2 = 1.2, r1 = 1, max_cycle = 20), each
+    condition switched on alone from a base step that triggers none, plus the
+    edges the inequalities fix (strict bounds, alpha > 0 in S62a, t > 0 in
+    S62c, the max_cycle period of reading R5)."""
+    p = sbci.SBCIParams()
+    base = dict(alpha=1, b=0.5, k=1.0, dE=1e-3, dz=0.5, t=3)
+
+    def cause(**kw):
+        a = dict(base, **kw)
+        return sbci.restart_cause(p, a["alpha"], a["b"], a["k"], a["dE"], a["dz"], a["t"])
+
+    assert cause() == ""
+    # S62a: needs alpha > 0, |b| < b_th and dE < eps1 together
+    assert cause(b=-5e-3, dE=5e-8) == "a"
+    assert cause(alpha=0, b=5e-3, dE=5e-8) == ""  # the ground state never restarts by S62a
+    assert cause(b=1e-2, dE=5e-8) == ""  # |b| = b_th is not below it
+    assert cause(b=5e-3, dE=1e-7) == ""  # dE = eps1 is not below it
+    assert cause(b=5e-3) == ""  # large dE
+    # S62b: |k| outside [x_th1, x_th2], either sign of k
+    assert cause(k=0.05) == "b" and cause(k=-0.05) == "b"
+    assert cause(k=1.3) == "b" and cause(k=-1.3) == "b"
+    assert cause(k=0.1) == "" and cause(k=1.2) == ""  # the bounds themselves are inside
+    # S62c: |z'| > r1 on a later step only
+    assert cause(dz=1.5) == "c"
+    assert cause(dz=1.5, t=0) == ""
+    assert cause(dz=1.0) == ""
+    # the max_cycle period: t + 1 reaches max_cycle
+    assert cause(t=19) == "max" and cause(t=18) == ""
+    # order of the tests when several hold: S62a, then S62b, S62c, max_cycle
+    assert cause(b=5e-3, dE=5e-8, k=2.0, dz=2.0, t=19) == "a"
+    assert cause(k=2.0, dz=2.0, t=19) == "b"
+    assert cause(dz=2.0, t=19) == "c"
