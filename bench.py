@@ -265,7 +265,7 @@ def run_reference(args, rank, world):
 
 TF32_OF_BF16 = 0.5  # nominal dense TF32 / BF16 tensor rate (1.1 vs 2.25 PFLOP/s)
 SIGMA_FAMILIES = ("gather_contract_tc", "gather_contract_os", "gather_contract", "gather_contract_lr",
-                  "scatter", "symfinish", "fused_sigma")
+                  "scatter", "symfinish", "fused_column")
 
 
 def family_of(name: str) -> str:
@@ -294,7 +294,7 @@ def roofline(name, launches, ms, dets_per_launch, npair, prec, pk, pk_kind, sm_m
                                    f"{dets_per_launch} determinants"}
         hbm["frac"] = hbm["achieved"] / hbm_peak
         other = None
-        if fam in ("gather_contract_tc", "fused_sigma", "gather_contract_os"):
+        if fam in ("gather_contract_tc", "fused_column", "gather_contract_os"):
             tpeak = pk.get("bf16_tflops", 1900.0) * (TF32_OF_BF16 if prec != "fp64" else 1.0)
             note = ("TF32: measured bf16 x nominal TF32/BF16 ratio 0.5" if prec != "fp64"
                     else "BF16 slices of the exact FP64 contraction: measured bf16")

@@ -243,9 +243,12 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
  * batched persistent kernels over a device job table (see sbci_server_*);
  * others are solved one after the other.  params as in sbci_solve (init must
  * be 0).  energies: host [n][k] totals; rep: host [n][k] or NULL; launches
- * (nullable): kernels this call launched (six per batched loop body plus the
- * host-driven ones).  Each context afterwards holds its finished solve
- * (sbci_finish, sbci_trace). */
+ * (nullable): kernels this call launched (per batched loop body: update,
+ * projection, the sigma kernels its solves need -- tensor-core tile kernel and
+ * scatter, or the column-fused kernel of singlet-sector solves with at most
+ * 256 strings per spin -- the symmetric finish of sector solves, and the end
+ * kernel; plus the host-driven ones).  Each context afterwards holds its
+ * finished solve (sbci_finish, sbci_trace). */
 sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
                              sbci_report *rep, long long *launches);
 
@@ -328,25 +331,33 @@ sbci_status sbci_profile_read(sbci_ctx *ctx, sbci_kernel_stat *out, int cap, int
 
 /* Kernel timing of the batch engine that sbci_solve_batch uses on the current
  * device (no counterpart in the paper).  Resets its statistics; enable = 1
- * makes later sbci_solve_batch calls on this device launch the six kernels of
+ * makes later sbci_solve_batch calls on this device launch the kernels of
  * every batched loop body one by one, each bracketed by CUDA events on the
  * engine's stream, instead of through the graph loop (same arithmetic). */
 sbci_status sbci_batch_profile(int enable);
 
 /* Waits for the recorded events and copies up to cap entries (families
  * "batch_update", "batch_project", "batch_gather_contract_tc",
- * "batch_scatter", "batch_symfinish", "batch_end"); *n = 6. */
+ * "batch_fused_column", "batch_scatter", "batch_symfinish", "batch_end");
+ * *n = 7.  A family that a class does not launch stays at zero. */
 sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n);
 
 /* Launch shapes of the batch engine on the current device, one record per
- * operand class met so far (no counterpart in the paper).  The autotuner
- * fills ctas[] once it has timed every candidate (tuned = 1). */
+ * class of job tables met so far (no counterpart in the paper): the operand
+ * sizes of its tile-kernel and column-kernel jobs and the kernels its loop
+ * body launches.  The autotuner fills ctas[] once it has timed every
+ * candidate (tuned = 1). */
 typedef struct {
-  int Kp, Np;            /* tensor-core operand class (padded pair counts) */
-  int smem_bytes;        /* dynamic shared memory of a tensor-core CTA */
-  int tc_per_sm_max;     /* tensor-core CTAs that fit one SM */
+  int Kp, Np;            /* tile-kernel operand class (padded pair counts) */
+  int smem_bytes;        /* dynamic shared memory of a tile-kernel CTA */
+  int tc_per_sm_max;     /* tile-kernel CTAs that fit one SM */
   int tuned;             /* 1 once the autotuner has chosen */
-  int ctas[6];           /* update, projection, tensor core, scatter, symmetric finish, end */
+  int ctas[7];           /* update, projection, tensor-core tile, fused column, scatter,
+                            symmetric finish, end */
+  int fKp, fNp;          /* column-kernel operand class (the singlet-sector solves
+                            with at most 256 strings per spin) */
+  int fused_smem_bytes;  /* dynamic shared memory of a column-kernel CTA */
+  int kernels;           /* bit k set: kernel k of ctas[] is launched in each loop body */
 } sbci_batch_class;
 
 /* Copies up to cap records; *n = classes. */

@@ -60,12 +60,13 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
                                        "davidson_dots", "davidson_combine", "davidson_precond",
-                                       "sigma_gather_contract_os", "sigma_gather_contract_lr"};
+                                       "sigma_gather_contract_os", "sigma_gather_contract_lr",
+                                       "sigma_fused_column"};
 
 struct Prof {
   bool on = false;
@@ -131,6 +132,7 @@ struct sbci_ctx {
   int nsm = 1;
   int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
+  int fc_grid = 0;  // CTAs of the column-fused sector kernel (0: unsupported shape or turned off)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
   size_t tmp_elems = 0;
   std::vector<double> W_host;
@@ -398,7 +400,27 @@ SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
   return a;
 }
 
-// One step body: update -> projection -> sigma (gather+contract, scatter).
+// The sector sigma of a TF32x3 step runs as the column-fused kernel (gather,
+// contraction and alpha-only scatter in one launch, G never in global memory)
+// where the shape allows it.
+bool use_fused(const sbci_ctx *c, int prec) { return prec == SBCI_TF32X3 && use_symfin(c) && c->fc_grid > 0; }
+
+// Counts the kernels of `bodies` step bodies run by a graph.
+void count_bodies(sbci_ctx *c, int prec, long long bodies) {
+  Prof &pf = c->prof;
+  pf.launches[K_UPD] += bodies;
+  pf.launches[K_PROJ] += bodies;
+  if (use_fused(c, prec)) {
+    pf.launches[K_FC] += bodies;
+  } else {
+    pf.launches[gc_kid(c, prec)] += bodies;
+    pf.launches[K_SC] += bodies;
+  }
+  if (use_symfin(c)) pf.launches[K_SF] += bodies;
+}
+
+// One step body: update -> projection -> sigma (gather+contract, scatter, or
+// the column-fused kernel) -> symmetric finish (singlet sector).
 // timing = 1: each launch is counted and bracketed with events (not in capture).
 sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool timing) {
   const StepArgs st = step_args(c, cond);
@@ -412,8 +434,12 @@ sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool tim
   };
   RET(L(K_UPD, [&] { return launch_update_ctl(st, g, c->stream); }));
   RET(L(K_PROJ, [&] { return launch_project_ctl(st, g, c->stream); }));
-  RET(L(gc_kid(c, prec), [&] { return launch_gc(c, sa, prec); }));
-  RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
+  if (use_fused(c, prec)) {
+    RET(L(K_FC, [&] { return launch_fused_column(sa, c->d_status, c->fc_grid, c->stream); }));
+  } else {
+    RET(L(gc_kid(c, prec), [&] { return launch_gc(c, sa, prec); }));
+    RET(L(K_SC, [&] { return launch_scatter(sa, p32, c->stream); }));
+  }
   if (sa.symA) RET(L(K_SF, [&] { return launch_symfin(sa, p32, c->stream); }));
   return SBCI_OK;
 }
@@ -458,14 +484,8 @@ sbci_status run_until_halt(sbci_ctx *c) {
     if (!s.gexec[prec]) RET(build_graph(c, prec));
     CK(cudaGraphLaunch(s.gexec[prec], c->stream));
     RET(ctl_read(c));
-    // kernels the graph ran: four per body
-    const long long bodies = s.h_ctl->iters;
-    Prof &pf = c->prof;
-    pf.launches[K_UPD] += bodies;
-    pf.launches[K_PROJ] += bodies;
-    pf.launches[gc_kid(c, prec)] += bodies;
-    pf.launches[K_SC] += bodies;
-    if (use_symfin(c)) pf.launches[K_SF] += bodies;
+    // kernels the graph ran
+    count_bodies(c, prec, s.h_ctl->iters);
     s.h_ctl->iters = 0;
     CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
     return SBCI_OK;
@@ -1868,13 +1888,7 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
   RET(ctl_read(c));
   const long long bodies = s.h_ctl->iters;
   const int prec = s.h_ctl->prec;
-  if (own_graph) {  // the solve's own graph ran four kernels per body
-    c->prof.launches[K_UPD] += bodies;
-    c->prof.launches[K_PROJ] += bodies;
-    c->prof.launches[gc_kid(c, prec)] += bodies;
-    c->prof.launches[K_SC] += bodies;
-    if (use_symfin(c)) c->prof.launches[K_SF] += bodies;
-  }
+  if (own_graph) count_bodies(c, prec, bodies);  // the kernels the solve's own graph ran
   s.h_ctl->iters = 0;
   CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
   const sbci_status st = handle_halt(c);
@@ -1894,6 +1908,7 @@ bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
   if (!tc_dims(c->npair, &j->Kp, &j->Np, &cols, &smem)) return false;
   j->step = step_args(c, 0);
   j->sig = sigma_ctl_args(c, SBCI_TF32X3, 0);
+  j->fused = use_fused(c, SBCI_TF32X3) ? 1 : 0;
   return true;
 }
 
@@ -2154,6 +2169,10 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
+  {  // SBCI_FUSED=0 keeps the tile kernel + scatter for singlet-sector TF32x3 steps
+    const char *e = std::getenv("SBCI_FUSED");
+    c->fc_grid = (e && e[0] == '0') ? 0 : fc_grid(c->npair, c->Na, c->Nb, c->sb.nlink, c->nsm);
+  }
   {
     int Kp, Np;
     uint32_t cols;

@@ -18,6 +18,7 @@ struct BatchJob {
   StepArgs step;  // update / projection arguments (cond = 0)
   SigmaArgs sig;  // sigma arguments (ctl set, cond = 0)
   int Kp, Np;     // tensor-core operand sizes of this solve
+  int fused;      // 1: its sigma is the column-fused sector kernel (no tile kernel, no scatter)
 };
 
 struct BatchTable {
@@ -26,6 +27,7 @@ struct BatchTable {
   int off_sc[kMaxBatch + 1];    // prefix sums of the scatter virtual blocks
   int off_tc[kMaxBatch + 1];    // prefix sums of the 128-determinant tensor-core tiles
   int off_sf[kMaxBatch + 1];    // prefix sums of the symmetric-finish virtual blocks (0 if none)
+  int off_fc[kMaxBatch + 1];    // prefix sums of the column-fused sigma's columns (0 unless fused)
   unsigned int tc_next;         // work-queue head of the tensor-core kernel
   unsigned long long bodies;    // loop bodies run (BK_COUNT kernels each)
   int stop;                     // the last body ended with a halted solve
@@ -38,9 +40,12 @@ struct BatchTable {
 constexpr int kBatchMaxPair = 105;
 
 
-// The kernels of one batched loop body, in launch order (the symmetric finish
-// serves the singlet-sector solves; the others finish in the scatter).
-enum BatchKernel { BK_UPDATE = 0, BK_PROJECT, BK_TC, BK_SCATTER, BK_SYMFIN, BK_END, BK_COUNT };
+// The kernels of one batched loop body, in launch order: the tile kernel and
+// the scatter serve the solves whose sigma is not column-fused, the column
+// kernel the singlet-sector solves with at most 256 strings per spin, the
+// symmetric finish every singlet-sector solve (the others finish in the
+// scatter).  A class's graph launches only the kernels its tables use.
+enum BatchKernel { BK_UPDATE = 0, BK_PROJECT, BK_TC, BK_FUSED, BK_SCATTER, BK_SYMFIN, BK_END, BK_COUNT };
 
 // Launch shapes of the batched kernels on a device with num_sms SMs for one
 // operand class: the tensor-core buffers are sized for the largest Kp x Np of
@@ -50,10 +55,23 @@ struct BatchConfig {
   uint32_t cols;       // TMEM columns per tensor-core CTA
   size_t smem;         // dynamic shared memory of the tensor-core kernel
   int tc_per_sm_max;   // tensor-core CTAs that fit one SM (shared memory, TMEM)
+  int fKp, fNp;        // operand buffers of the column kernel (largest of the fused jobs)
+  uint32_t fcols;      // TMEM columns per column CTA (two accumulators)
+  size_t fsmem;        // dynamic shared memory of the column kernel
+  int fc_per_sm_max;   // column CTAs that fit one SM
+  unsigned mask;       // bit k set: kernel k is launched (it has work in this class)
   int ctas[BK_COUNT];  // CTAs of each kernel of the body (the autotuner's choice)
 };
 
-cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg);
+// Kernels a table needs (bits of BatchConfig::mask) and its operand class:
+// the largest Kp / Np of the tile-kernel jobs and of the column-kernel jobs.
+struct BatchClass {
+  int Kp, Np, fKp, fNp;
+  unsigned mask;
+};
+BatchClass table_class(const BatchTable &t);
+
+cudaError_t batch_config(int num_sms, const BatchClass &k, BatchConfig *cfg);
 
 // One kernel of the body; cond = 0 outside a graph (the end kernel then only
 // records the stop flag).

@@ -44,6 +44,7 @@
 
 #include "batch.h"
 #include "ctl.h"
+#include "fused_body.cuh"
 #include "sbci_internal.h"
 #include "sigma_body.cuh"
 #include "step_body.cuh"
@@ -317,6 +318,107 @@ cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- column-fused sector sigma
+
+// TMEM allocation, mbarrier set-up and operand B of a column CTA (uniform:
+// every thread calls it).
+__device__ __forceinline__ void fc_begin(const FcSmem &sm, uint32_t tmem_cols) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(fc_tmem_slot(sm))),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm.sbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+}
+
+// Error path and TMEM release at the end of a column CTA.
+__device__ __forceinline__ void fc_end(const FcSmem &sm, bool ok, int pending, uint32_t phase, uint32_t tmem,
+                                       uint32_t tmem_cols, int *status) {
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, 1);
+    if (pending) mbar_wait(sm.sbar, phase, kWaitIters);  // let the outstanding MMAs drain (bounded)
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kFcThreads, 2)
+    k_fused_column(SigmaArgs a, int Kp, int Np, uint32_t tmem_cols, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const FcSmem sm = fc_carve(smem, Kp, Np);
+  if (!a.ctl || a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
+  const float *zf = a.ctl->zf;
+  if (!zf || !a.symA) {  // the column kernel needs the FP32 z and the A^T buffer: refuse
+    if (threadIdx.x == 0) atomicOr(status, 4);
+    return;
+  }
+  if ((int)blockIdx.x >= a.nb) return;
+  fc_begin(sm, tmem_cols);
+  fc_load_B(a, Kp, Np, sm);  // (ends with a barrier)
+  const uint32_t tmem = *fc_tmem_slot(sm);
+  uint32_t phase = 0;
+  int pending = 0;
+  bool ok = true;
+  for (int b = blockIdx.x; b < a.nb && ok; b += gridDim.x) ok = fc_column(a, zf, b, Kp, Np, sm, tmem, phase, &pending);
+  fc_end(sm, ok, pending, phase, tmem, tmem_cols, status);
+}
+
+bool fc_dims(int npair, int na, int nb, int nlink_b, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
+  uint32_t tc_cols;
+  size_t tc_smem;
+  if (na != nb || na < 1 || na > kFcMaxStr || nlink_b > kFcMaxLink ||
+      !tc_dims(npair, Kp, Np, &tc_cols, &tc_smem))
+    return false;
+  const uint32_t c = 2u * (uint32_t)fc_acc_stride(*Np);
+  *cols = c;
+  *smem = fc_smem_bytes(*Kp, *Np);
+  return c <= 512 && *smem <= 227 * 1024;
+}
+
+// Sets the opt-in shared-memory limit of a column kernel and returns its
+// resident CTAs per SM for a launch with smem bytes and cols TMEM columns.
+static int fc_prepare(const void *f, size_t smem, uint32_t cols) {
+  int optin = 0;
+  if (max_dynamic_smem(f, &optin) != cudaSuccess || (int)smem > optin ||
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+          cudaSuccess)
+    return 0;
+  int per_sm = resident_ctas(f, kFcThreads, smem);
+  if ((uint32_t)per_sm * cols > 512) per_sm = (int)(512 / cols);
+  return per_sm;
+}
+
+int fc_grid(int npair, int na, int nb, int nlink_b, int num_sms) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!fc_dims(npair, na, nb, nlink_b, &Kp, &Np, &cols, &smem)) return 0;
+  const int per_sm = fc_prepare((const void *)k_fused_column, smem, cols);
+  if (per_sm < 1) return 0;
+  long long grid = (long long)num_sms * per_sm;
+  if (grid > nb) grid = nb;
+  return (int)grid;
+}
+
+cudaError_t launch_fused_column(const SigmaArgs &a, int *status, int grid, cudaStream_t s) {
+  int Kp, Np;
+  uint32_t cols;
+  size_t smem;
+  if (!fc_dims(a.npair, a.na, a.nb, a.nlink_b, &Kp, &Np, &cols, &smem) || grid < 1) return cudaErrorInvalidValue;
+  k_fused_column<<<grid, kFcThreads, smem, s>>>(a, Kp, Np, cols, status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- batched
 
 __device__ __forceinline__ int find_job(const int *off, int njobs, int item) {
@@ -456,6 +558,60 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                  : "memory");
 }
 
+// Column-fused sector sigma over the table's fused jobs: (job, column) items
+// in contiguous chunks per CTA (a CTA meets one or two jobs and loads
+// operand B once or twice).
+__global__ void __launch_bounds__(kFcThreads, 2)
+    k_fused_batch(BatchTable *bt, int Kpmax, int Npmax, uint32_t tmem_cols, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const FcSmem sm = fc_carve(smem, Kpmax, Npmax);
+  __shared__ int s_off[kMaxBatch + 1];
+  __shared__ int s_halt[kMaxBatch];
+  __shared__ const float *s_zf[kMaxBatch];
+  __shared__ __align__(16) SigmaArgs s_args;  // the current job's arguments
+  const int tid = threadIdx.x;
+  const int nj = bt->njobs;
+  const int total = bt->off_fc[nj];
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int first = blockIdx.x * chunk, last = min(total, first + chunk);
+  if (first >= last) return;  // uniform: before any TMEM allocation or barrier
+  fc_begin(sm, tmem_cols);
+  for (int i = tid; i <= nj; i += blockDim.x) s_off[i] = bt->off_fc[i];
+  for (int i = tid; i < nj; i += blockDim.x) {
+    const CtlState *c = bt->job[i].step.ctl;
+    s_halt[i] = c->halt;
+    s_zf[i] = c->zf;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *fc_tmem_slot(sm);
+  uint32_t phase = 0;
+  int pending = 0;
+  bool ok = true;
+  int cur = -1, Kp = 0, Np = 0;
+  for (int item = first; item < last && ok; ++item) {
+    const int j = find_job(s_off, nj, item);
+    if (s_halt[j]) continue;  // block-uniform
+    if (!s_zf[j] || !bt->job[j].sig.symA) {  // a fused job always has both; refuse otherwise
+      if (tid == 0) atomicOr(status, 4);
+      continue;
+    }
+    if (j != cur) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(&bt->job[j].sig);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+      for (int i = tid; i < (int)(sizeof(SigmaArgs) / 4); i += blockDim.x) dst[i] = src[i];
+      Kp = bt->job[j].Kp;
+      Np = bt->job[j].Np;
+      __syncthreads();
+      fc_load_B(s_args, Kp, Np, sm);  // (ends with a barrier)
+      cur = j;
+    }
+    ok = fc_column(s_args, s_zf[j], item - s_off[j], Kp, Np, sm, tmem, phase, &pending);
+  }
+  fc_end(sm, ok, pending, phase, tmem, tmem_cols, status);
+}
+
 // Ends a batched loop body (kMaxBatch threads, one per job): resets the tile
 // queue, counts the body, and ends the while-loop when a solve halted (or the
 // table is empty), so the host can act on it.
@@ -475,10 +631,12 @@ __global__ void __launch_bounds__(kMaxBatch) k_batch_end(BatchTable *bt, unsigne
   }
 }
 
-cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
+cudaError_t batch_config(int num_sms, const BatchClass &k, BatchConfig *cfg) {
+  const int Kp = k.Kp, Np = k.Np;
   if (Kp < 8 || Np < 16 || Kp % 8 || Np % 16 || Np > 256) return cudaErrorInvalidValue;
   cfg->Kp = Kp;
   cfg->Np = Np;
+  cfg->mask = k.mask | (1u << BK_UPDATE) | (1u << BK_PROJECT) | (1u << BK_END);
   cfg->cols = 32;
   while (cfg->cols < (uint32_t)Np) cfg->cols <<= 1;
   cfg->smem = (size_t)(2 * kTcM * Kp + 2 * Np * Kp) * 4 + 16;
@@ -499,10 +657,22 @@ cudaError_t batch_config(int num_sms, int Kp, int Np, BatchConfig *cfg) {
   int per_sm = resident_ctas((const void *)k_tc_batch, kTcThreads, cfg->smem);
   if ((uint32_t)per_sm * cfg->cols > 512) per_sm = (int)(512 / cfg->cols);
   cfg->tc_per_sm_max = per_sm;
+  // the column kernel (sized for the largest fused job)
+  cfg->fKp = k.fKp;
+  cfg->fNp = k.fNp;
+  cfg->fcols = 2u * (uint32_t)fc_acc_stride(k.fNp);
+  cfg->fsmem = fc_smem_bytes(k.fKp, k.fNp);
+  cfg->fc_per_sm_max = 1;
+  if (cfg->mask & (1u << BK_FUSED)) {
+    if (k.fKp < 8 || k.fNp < 16 || cfg->fcols > 512 || cfg->fsmem > 227 * 1024) return cudaErrorInvalidValue;
+    cfg->fc_per_sm_max = fc_prepare((const void *)k_fused_batch, cfg->fsmem, cfg->fcols);
+    if (cfg->fc_per_sm_max < 1) return cudaErrorInvalidValue;
+  }
   // defaults until the autotuner has measured this class
   cfg->ctas[BK_UPDATE] = 2 * num_sms;
   cfg->ctas[BK_PROJECT] = 4 * num_sms;
   cfg->ctas[BK_TC] = num_sms * per_sm;
+  cfg->ctas[BK_FUSED] = num_sms * cfg->fc_per_sm_max;
   cfg->ctas[BK_SCATTER] = 3 * num_sms;
   cfg->ctas[BK_SYMFIN] = 2 * num_sms;
   cfg->ctas[BK_END] = 1;
@@ -516,6 +686,9 @@ cudaError_t launch_batch_kernel(int which, const BatchConfig &cfg, BatchTable *d
     case BK_PROJECT: k_project_batch<<<cfg.ctas[BK_PROJECT], kStepThreads, 0, s>>>(d_table); break;
     case BK_TC:
       k_tc_batch<<<cfg.ctas[BK_TC], kTcThreads, cfg.smem, s>>>(d_table, cfg.Kp, cfg.Np, cfg.cols, status);
+      break;
+    case BK_FUSED:
+      k_fused_batch<<<cfg.ctas[BK_FUSED], kFcThreads, cfg.fsmem, s>>>(d_table, cfg.fKp, cfg.fNp, cfg.fcols, status);
       break;
     case BK_SCATTER: k_scatter_batch<<<cfg.ctas[BK_SCATTER], kScTile, 0, s>>>(d_table); break;
     case BK_SYMFIN: k_symfin_batch<<<cfg.ctas[BK_SYMFIN], kScTile, 0, s>>>(d_table); break;
@@ -543,7 +716,8 @@ cudaError_t build_batch_graph(const BatchConfig &cfg, BatchTable *d_table, int *
   if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
       cudaSuccess)
     return e;
-  for (int k = 0; k < BK_COUNT; ++k) launch_batch_kernel(k, cfg, d_table, status, (unsigned long long)h, s);
+  for (int k = 0; k < BK_COUNT; ++k)
+    if (cfg.mask & (1u << k)) launch_batch_kernel(k, cfg, d_table, status, (unsigned long long)h, s);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(s, &captured);
   if (e != cudaSuccess) return e;

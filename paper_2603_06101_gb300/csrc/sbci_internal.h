@@ -174,6 +174,14 @@ int tc_grid(int npair, long long ndet, int num_sms);
 // Writes W (FP64 [npair_pad][npair]) as TF32 hi/lo operand B, [2][Np*Kp].
 cudaError_t launch_split_W(const double *W, int npair, int Kp, int Np, uint32_t *out, cudaStream_t s);
 cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
+// Column-fused TF32x3 sigma of the singlet sector (kernels_loop.cu,
+// fused_body.cuh): gather, contraction and alpha-only scatter of one column
+// of A per CTA step, G kept in shared memory; device-controlled mode only
+// (input z from the controller's FP32 copy, A^T written to a.symA).
+// Supported for n_alpha = n_beta strings per spin <= 256.
+bool fc_dims(int npair, int na, int nb, int nlink_b, int *Kp, int *Np, uint32_t *cols, size_t *smem);
+int fc_grid(int npair, int na, int nb, int nlink_b, int num_sms);  // 0: unsupported shape
+cudaError_t launch_fused_column(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
 // Helper kernels (kernels_vec.cu)

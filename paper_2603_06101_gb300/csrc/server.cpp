@@ -87,21 +87,29 @@ void tune_init(ClassGraph &g, int nsm) {
   g.cand[BK_UPDATE] = {nsm, 2 * nsm, 4 * nsm};
   g.cand[BK_PROJECT] = {nsm, 2 * nsm, 4 * nsm, 8 * nsm};
   for (int k = 1; k <= g.cfg.tc_per_sm_max; ++k) g.cand[BK_TC].push_back(k * nsm);
+  for (int k = 1; k <= g.cfg.fc_per_sm_max; ++k) g.cand[BK_FUSED].push_back(k * nsm);
   g.cand[BK_SCATTER] = {nsm, 2 * nsm, 3 * nsm, 6 * nsm};
   g.cand[BK_SYMFIN] = {nsm, 2 * nsm, 4 * nsm};
   g.cand[BK_END] = {1};
-  for (int k = 0; k < BK_COUNT; ++k) g.ms[k].assign(g.cand[k].size(), std::vector<float>());
+  for (int k = 0; k < BK_COUNT; ++k) {
+    if (!(g.cfg.mask & (1u << k))) g.cand[k] = {g.cfg.ctas[k]};  // not launched in this class
+    g.ms[k].assign(g.cand[k].size(), std::vector<float>());
+  }
 }
+
+bool launched(const ClassGraph &g, int k) { return (g.cfg.mask & (1u << k)) != 0; }
 
 bool tune_complete(const ClassGraph &g) {
   for (int k = 0; k < BK_COUNT; ++k)
-    for (const auto &v : g.ms[k])
-      if ((int)v.size() < kTuneSamples) return false;
+    if (launched(g, k))
+      for (const auto &v : g.ms[k])
+        if ((int)v.size() < kTuneSamples) return false;
   return true;
 }
 
 void tune_choose(ClassGraph &g) {
   for (int k = 0; k < BK_COUNT; ++k) {
+    if (!launched(g, k)) continue;
     int best = 0;
     float best_t = 0.f;
     for (size_t c = 0; c < g.cand[k].size(); ++c) {
@@ -118,6 +126,13 @@ void tune_choose(ClassGraph &g) {
   g.tuned = true;
 }
 
+// Kernels per loop body of a class.
+int body_kernels(const ClassGraph &g) {
+  int n = 0;
+  for (int k = 0; k < BK_COUNT; ++k) n += launched(g, k) ? 1 : 0;
+  return n;
+}
+
 // Event timing of single launches (kernel timing and tuning).
 struct KernelStats {
   bool on = false;
@@ -126,15 +141,15 @@ struct KernelStats {
 };
 
 struct GraphCache {
-  std::map<int, ClassGraph> m;
+  std::map<std::vector<int>, ClassGraph> m;
   cudaEvent_t ev[2 * BK_COUNT] = {};
   int *h_stop = nullptr;  // pinned
-  ClassGraph *get(int Kp, int Np, int nsm) {
-    const int key = Np * 4096 + Kp;
+  ClassGraph *get(const BatchClass &k, int nsm) {
+    const std::vector<int> key = {k.Kp, k.Np, k.fKp, k.fNp, (int)k.mask};
     auto it = m.find(key);
     if (it != m.end()) return &it->second;
     ClassGraph g;
-    if (batch_config(nsm, Kp, Np, &g.cfg) != cudaSuccess) return nullptr;
+    if (batch_config(nsm, k, &g.cfg) != cudaSuccess) return nullptr;
     tune_init(g, nsm);
     return &(m[key] = g);
   }
@@ -175,6 +190,7 @@ cudaError_t run_round(GraphCache &gc, ClassGraph &cg, BatchTable *d_table, int *
       if (ci[k] >= 0) cfg.ctas[k] = cg.cand[k][ci[k]];
     }
     for (int k = 0; k < BK_COUNT; ++k) {
+      if (!launched(cg, k)) continue;
       if ((e = cudaEventRecord(gc.ev[2 * k], s)) != cudaSuccess) return e;
       if ((e = launch_batch_kernel(k, cfg, d_table, d_status, 0ull, s)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(gc.ev[2 * k + 1], s)) != cudaSuccess) return e;
@@ -183,6 +199,7 @@ cudaError_t run_round(GraphCache &gc, ClassGraph &cg, BatchTable *d_table, int *
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return e;
     for (int k = 0; k < BK_COUNT; ++k) {
+      if (!launched(cg, k)) continue;
       float t = 0.f;
       if ((e = cudaEventElapsedTime(&t, gc.ev[2 * k], gc.ev[2 * k + 1])) != cudaSuccess) return e;
       if (ci[k] >= 0) cg.ms[k][ci[k]].push_back(t);
@@ -199,15 +216,29 @@ cudaError_t run_round(GraphCache &gc, ClassGraph &cg, BatchTable *d_table, int *
   }
 }
 
-// Operand class of a table: the largest Kp and Np of its jobs.
-void table_class(const BatchTable &t, int *Kp, int *Np) {
-  *Kp = 8;
-  *Np = 16;
+}  // namespace
+
+// Operand class of a table: the largest Kp and Np of its tile-kernel jobs and
+// of its column-kernel jobs, and the kernels its jobs need.
+BatchClass sbci::table_class(const BatchTable &t) {
+  BatchClass k{8, 16, 8, 16, 0u};
   for (int j = 0; j < t.njobs; ++j) {
-    if (t.job[j].Kp > *Kp) *Kp = t.job[j].Kp;
-    if (t.job[j].Np > *Np) *Np = t.job[j].Np;
+    const BatchJob &b = t.job[j];
+    if (b.fused) {
+      k.mask |= 1u << BK_FUSED;
+      k.fKp = std::max(k.fKp, b.Kp);
+      k.fNp = std::max(k.fNp, b.Np);
+    } else {
+      k.mask |= (1u << BK_TC) | (1u << BK_SCATTER);
+      k.Kp = std::max(k.Kp, b.Kp);
+      k.Np = std::max(k.Np, b.Np);
+    }
+    if (b.sig.symA) k.mask |= 1u << BK_SYMFIN;
   }
+  return k;
 }
+
+namespace {
 
 struct Result {
   int done = 0;
@@ -322,12 +353,23 @@ sbci_status admit(sbci_server *sv) {
 
 namespace {
 
+// Work-item offsets of job nj (just filled by ctx_batch_job) in every kernel
+// of the body: a column-fused job has columns and no tiles or scatter blocks.
+void table_offsets(BatchTable &t, int nj, const sbci_ctx *c) {
+  const BatchJob &b = t.job[nj];
+  t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(c);
+  t.off_sc[nj + 1] = t.off_sc[nj] + (b.fused ? 0 : ctx_scatter_blocks(c));
+  t.off_tc[nj + 1] = t.off_tc[nj] + (b.fused ? 0 : (int)((ctx_ndet(c) + 127) / 128));
+  t.off_fc[nj + 1] = t.off_fc[nj] + (b.fused ? b.sig.nb : 0);
+  t.off_sf[nj + 1] = t.off_sf[nj] + ctx_symfin_blocks(c);
+}
+
 // Rebuilds the job table from the batched slots and launches one round.
 sbci_status launch_batch_round(sbci_server *sv) {
   BatchTable &t = *sv->h_table;
   sv->batch_slots.clear();
   int nj = 0;
-  t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
+  t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = t.off_fc[0] = 0;
   for (int i = 0; i < (int)sv->slots.size(); ++i) {
     SolveSlot &sl = sv->slots[i];
     if (!sl.used || !sl.batched || sl.host_pending || nj >= kMaxBatch) continue;
@@ -338,10 +380,7 @@ sbci_status launch_batch_round(sbci_server *sv) {
       if (st != SBCI_OK) retire(sv, sl, st);
       continue;
     }
-    t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(sl.ctx);
-    t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(sl.ctx);
-    t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(sl.ctx) + 127) / 128);
-    t.off_sf[nj + 1] = t.off_sf[nj] + ctx_symfin_blocks(sl.ctx);
+    table_offsets(t, nj, sl.ctx);
     t.halted[nj] = 0;
     sv->batch_slots.push_back(i);
     ++nj;
@@ -349,9 +388,7 @@ sbci_status launch_batch_round(sbci_server *sv) {
   t.njobs = nj;
   t.tc_next = 0;
   if (nj == 0) return SBCI_OK;
-  int Kp, Np;
-  table_class(t, &Kp, &Np);
-  ClassGraph *cg = sv->graphs.get(Kp, Np, sv->nsm);
+  ClassGraph *cg = sv->graphs.get(table_class(t), sv->nsm);
   if (!cg) {
     set_error("server: no batch configuration for this operand class");
     return SBCI_ERR_CUDA;
@@ -434,7 +471,8 @@ struct Engine {
 constexpr int kMaxDevices = 64;
 Engine g_engines[kMaxDevices];
 const char *const kBatchKernelName[BK_COUNT] = {"batch_update", "batch_project", "batch_gather_contract_tc",
-                                                "batch_scatter", "batch_symfinish", "batch_end"};
+                                                "batch_fused_column", "batch_scatter", "batch_symfinish",
+                                                "batch_end"};
 
 cudaError_t engine_setup(Engine &eng, int dev) {
   if (eng.ready) return cudaSuccess;
@@ -448,11 +486,10 @@ cudaError_t engine_setup(Engine &eng, int dev) {
   return e;
 }
 
-cudaError_t engine_round(Engine &eng) {
-  int Kp, Np;
-  table_class(*eng.h_table, &Kp, &Np);
-  ClassGraph *cg = eng.graphs.get(Kp, Np, eng.nsm);
+cudaError_t engine_round(Engine &eng, int *kernels_per_body) {
+  ClassGraph *cg = eng.graphs.get(table_class(*eng.h_table), eng.nsm);
   if (!cg) return cudaErrorInvalidValue;
+  *kernels_per_body = body_kernels(*cg);
   return run_round(eng.graphs, *cg, eng.d_table, eng.d_status, eng.stream, &eng.prof);
 }
 
@@ -500,7 +537,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     set_error("sbci_solve_batch: CUDA set-up failed");
     return SBCI_ERR_CUDA;
   }
-  unsigned long long bodies = 0;
+  unsigned long long bodies = 0;  // kernels the batch rounds launched (bodies x kernels per body)
   sbci_status worst = SBCI_OK;
   // a solve that halted sits out the next round: that round is launched first
   // and the solve's host work (FP64 re-syncs, verification, next state) runs on
@@ -511,7 +548,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     BatchTable &t = *eng.h_table;
     std::vector<int> row;
     int nj = 0;
-    t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = 0;
+    t.off_step[0] = t.off_sc[0] = t.off_tc[0] = t.off_sf[0] = t.off_fc[0] = 0;
     for (int i = 0; i < n; ++i) {
       if (done[i] || is_pending[i]) continue;
       if (!ctx_batch_job(ctx[i], &t.job[nj])) {  // not batchable: solve it on its own
@@ -527,10 +564,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
         if (st != SBCI_OK) worst = st;
         continue;
       }
-      t.off_step[nj + 1] = t.off_step[nj] + ctx_step_blocks(ctx[i]);
-      t.off_sc[nj + 1] = t.off_sc[nj] + ctx_scatter_blocks(ctx[i]);
-      t.off_tc[nj + 1] = t.off_tc[nj] + (int)((ctx_ndet(ctx[i]) + 127) / 128);
-      t.off_sf[nj + 1] = t.off_sf[nj] + ctx_symfin_blocks(ctx[i]);
+      table_offsets(t, nj, ctx[i]);
       t.halted[nj] = 0;
       row.push_back(i);
       ++nj;
@@ -541,10 +575,11 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     t.bodies = 0;
     int status = 0;
     unsigned long long round_bodies = 0;
+    int per_body = 0;
     if (nj > 0 &&
         (cudaMemcpyAsync(eng.d_table, eng.h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, eng.stream) !=
              cudaSuccess ||
-         engine_round(eng) != cudaSuccess ||
+         engine_round(eng, &per_body) != cudaSuccess ||
          cudaMemcpyAsync(t.halted, eng.d_table->halted, sizeof(int) * kMaxBatch, cudaMemcpyDeviceToHost,
                          eng.stream) != cudaSuccess ||
          cudaMemcpyAsync(&status, eng.d_status, sizeof(int), cudaMemcpyDeviceToHost, eng.stream) != cudaSuccess ||
@@ -574,7 +609,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       return SBCI_ERR_CUDA;
     }
     if (host_st != SBCI_OK) return host_st;
-    bodies += round_bodies;
+    bodies += round_bodies * (unsigned long long)per_body;
     if (status) {
       set_error("a bounded device wait ran out (batched tensor-core kernel)");
       return SBCI_ERR_TIMEOUT;
@@ -588,7 +623,7 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
   if (launches) {
     long long host_launches1 = 0;
     for (int i = 0; i < n; ++i) host_launches1 += ctx_launch_count(ctx[i]);
-    *launches = (long long)(BK_COUNT * bodies) + (host_launches1 - host_launches0);
+    *launches = (long long)bodies + (host_launches1 - host_launches0);
   }
   return worst;
 }
@@ -644,6 +679,10 @@ sbci_status sbci_batch_classes(sbci_batch_class *out, int cap, int *n) {
       r.Np = g.cfg.Np;
       r.smem_bytes = (int)g.cfg.smem;
       r.tc_per_sm_max = g.cfg.tc_per_sm_max;
+      r.fKp = g.cfg.fKp;
+      r.fNp = g.cfg.fNp;
+      r.fused_smem_bytes = (int)g.cfg.fsmem;
+      r.kernels = (int)g.cfg.mask;
       r.tuned = g.tuned ? 1 : 0;
       for (int k = 0; k < BK_COUNT; ++k) r.ctas[k] = g.cfg.ctas[k];
     }
@@ -682,7 +721,13 @@ sbci_status sbci_server_create(sbci_server **out, size_t mem_budget_bytes, int m
     int Kp, Np;
     uint32_t cols;
     size_t smem;
-    sv->batch_ok = tc_dims(kBatchMaxPair, &Kp, &Np, &cols, &smem) && sv->graphs.get(Kp, Np, sv->nsm) != nullptr;
+    sv->batch_ok = tc_dims(kBatchMaxPair, &Kp, &Np, &cols, &smem) &&
+                   sv->graphs.get(BatchClass{Kp, Np, 8, 16, (1u << BK_TC) | (1u << BK_SCATTER)}, sv->nsm) != nullptr;
+    // and the largest column-fused class (10 orbitals, 252 strings per spin)
+    int fKp, fNp;
+    if (sv->batch_ok && fc_dims(55, 252, 252, 30, &fKp, &fNp, &cols, &smem))
+      sv->batch_ok = sv->graphs.get(BatchClass{8, 16, fKp, fNp, (1u << BK_FUSED) | (1u << BK_SYMFIN)}, sv->nsm) !=
+                     nullptr;
   }
   if (!sv->batch_ok) {
     set_error("sbci_server_create: building the batch graph failed");

@@ -67,7 +67,8 @@ class sbci_kernel_stat(C.Structure):
 
 class sbci_batch_class(C.Structure):
     _fields_ = [("Kp", C.c_int), ("Np", C.c_int), ("smem_bytes", C.c_int), ("tc_per_sm_max", C.c_int),
-                ("tuned", C.c_int), ("ctas", C.c_int * 6)]
+                ("tuned", C.c_int), ("ctas", C.c_int * 7), ("fKp", C.c_int), ("fNp", C.c_int),
+                ("fused_smem_bytes", C.c_int), ("kernels", C.c_int)]
 
 
 _lib = None
@@ -386,9 +387,10 @@ def batch_classes() -> list:
     buf = (sbci_batch_class * 16)()
     n = C.c_int()
     _check(load().sbci_batch_classes(buf, 16, C.byref(n)))
+    names = ["update", "project", "tensor_core", "fused_column", "scatter", "symfinish", "end"]
     return [{"Kp": b.Kp, "Np": b.Np, "smem_bytes": b.smem_bytes, "tc_per_sm_max": b.tc_per_sm_max,
-             "tuned": bool(b.tuned), "ctas": {"update": b.ctas[0], "project": b.ctas[1], "tensor_core": b.ctas[2],
-                                              "scatter": b.ctas[3], "symfinish": b.ctas[4], "end": b.ctas[5]}}
+             "fKp": b.fKp, "fNp": b.fNp, "fused_smem_bytes": b.fused_smem_bytes, "tuned": bool(b.tuned),
+             "ctas": {nm: b.ctas[i] for i, nm in enumerate(names) if b.kernels & (1 << i)}}
             for b in list(buf)[: min(n.value, 16)]]
 
 

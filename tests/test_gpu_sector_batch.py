@@ -107,3 +107,29 @@ def test_sector_server_same_alone_and_in_mix():
         assert st == sbci.SBCI_OK and all(r.converged for r in R)
         assert np.array_equal(E, Ea), np.abs(E - Ea).max()
     server.close()
+
+
+def test_sector_batch_runs_the_column_kernel():
+    """The batched sector H10 loop body is update, projection, column-fused
+    sigma, symmetric finish and end: no tile kernel, no scatter, G never in
+    global memory.  Same energies under kernel timing as through the graph."""
+    sbci = require_lib()
+    I = make_integrals(("chain", 10, 1.2))
+    p = sbci.params(sector=1, prec=sbci.SBCI_TF32X3)
+    ctxs = [sbci.Context.from_integrals(I) for _ in range(4)]
+    E0, _, st = sbci.solve_batch(ctxs, 2, p)
+    assert st == sbci.SBCI_OK
+    sbci.batch_profile(True)
+    E1, _, st = sbci.solve_batch(ctxs, 2, p)
+    stats = sbci.batch_profile_read()
+    sbci.batch_profile(False)
+    assert st == sbci.SBCI_OK and np.array_equal(E0, E1)
+    bodies = stats["batch_end"][0]
+    assert bodies > 0
+    for k in ("batch_update", "batch_project", "batch_fused_column", "batch_symfinish"):
+        assert stats[k][0] == bodies and stats[k][1] > 0.0, k
+    assert stats["batch_gather_contract_tc"][0] == 0 and stats["batch_scatter"][0] == 0
+    cls = [c for c in sbci.batch_classes() if "fused_column" in c["ctas"]]
+    assert cls and all("tensor_core" not in c["ctas"] for c in cls)
+    for c in ctxs:
+        c.close()
