@@ -63,9 +63,17 @@ typedef enum {
                       W = F M F^T, F = [L | kappa | delta], 2 (r + 2) npair
                       instead of npair^2 multiply-adds; SBCI_LOWRANK=0, read
                       when a context is created, turns it off. */
-  SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation */
-  SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores: reserved, not built;
-                      every call with it returns SBCI_ERR_INVALID */
+  SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation
+                      (about 2^-21 relative per product), n <= 14; singlet-sector
+                      steps of spaces with at most 256 strings per spin run the
+                      column-fused kernel (gather, contraction and scatter of one
+                      column of the alpha part per CTA, no scratch in global
+                      memory; SBCI_FUSED=0, read when a context is created,
+                      keeps the tile kernel and scatter) */
+  SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores (D_hi W_hi + D_hi W_lo +
+                      D_lo W_hi, FP32 accumulation; about 2^-17 relative per
+                      product), every orbital count up to 16: the tensor-core
+                      mode of n = 15-16, where TF32 operands exceed shared memory */
   SBCI_FP32 = 3    /* FP32 SIMT contraction (reference for the split modes) */
 } sbci_precision;
 

@@ -60,13 +60,13 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_GCBF, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
                                        "davidson_dots", "davidson_combine", "davidson_precond",
                                        "sigma_gather_contract_os", "sigma_gather_contract_lr",
-                                       "sigma_fused_column"};
+                                       "sigma_fused_column", "sigma_gather_contract_bf16"};
 
 struct Prof {
   bool on = false;
@@ -117,6 +117,8 @@ struct sbci_ctx {
   float *d_Wf = nullptr;
   float *d_cf = nullptr;      // FP32 copy of a plain sigma's input (tensor-core mode)
   uint32_t *d_Wtc = nullptr;  // TF32 hi/lo operand B of the tensor-core sigma (nullptr: unsupported)
+  uint16_t *d_Wbf = nullptr;  // BF16 hi/lo operand B of the BF16x3 sigma (nullptr: unsupported)
+  int bf_grid = 0;            // CTAs of the BF16x3 kernel (0: unsupported shape)
   void *d_Wos = nullptr;      // BF16 integer slices of W for the FP64 tensor-core contraction (nullptr: off)
   int *d_fexp = nullptr;      // their per-output-pair exponents
   int os_grid = 0;
@@ -207,7 +209,7 @@ sbci_status timed(sbci_ctx *c, int kid, F &&launch) {
 }
 
 // SBCI_ERR_INVALID for a precision this context cannot run (TF32x3 beyond
-// n = 14, the reserved BF16x3).
+// n = 14, BF16x3 beyond n = 16).
 sbci_status check_prec(const sbci_ctx *c, int prec) {
   if (prec == SBCI_FP64 || prec == SBCI_FP32) return SBCI_OK;
   if (prec == SBCI_TF32X3) {
@@ -215,16 +217,22 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
     uint32_t cols;
     size_t smem;
     if (tc_dims(c->npair, &Kp, &Np, &cols, &smem) && c->tc_grid > 0) return SBCI_OK;
-    set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14); use SBCI_FP32");
+    set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14); use SBCI_BF16X3 or SBCI_FP32");
     return SBCI_ERR_INVALID;
   }
-  set_error("precision mode not available in this build");
+  if (prec == SBCI_BF16X3) {
+    if (c->d_Wbf && c->bf_grid > 0) return SBCI_OK;
+    set_error("SBCI_BF16X3: not available for this space");
+    return SBCI_ERR_INVALID;
+  }
+  set_error("unknown precision mode");
   return SBCI_ERR_INVALID;
 }
 
 // The gather + contract kernel family of a sigma precision, and its launch.
 int gc_kid(const sbci_ctx *c, int prec) {
   if (prec == SBCI_TF32X3) return K_GCTC;
+  if (prec == SBCI_BF16X3) return K_GCBF;
   if (prec == SBCI_FP64 && c->d_Wos) return K_GCOS;
   if (prec == SBCI_FP64 && c->lr_rank > 0) return K_GCLR;
   return K_GC;
@@ -234,6 +242,8 @@ cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
   switch (gc_kid(c, prec)) {
     case K_GCTC:
       return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream);
+    case K_GCBF:
+      return launch_gather_contract_bf(a, c->d_Wbf, c->d_status, c->bf_grid, c->stream);
     case K_GCOS:
       return launch_gather_contract_os(a, c->d_Wos, c->d_fexp, c->d_status, c->os_grid, c->stream);
     case K_GCLR:
@@ -267,7 +277,7 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   a.partials = c->d_partials;  // (no dots: dot_u all null)
   a.grid = scatter_grid(c->ndet, c->nsm);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
-  if (prec == SBCI_TF32X3) {
+  if (prec == SBCI_TF32X3 || prec == SBCI_BF16X3) {  // the tensor-core gathers read an FP32 copy
     if (!c->d_cf) RET(dmalloc(&c->d_cf, (size_t)c->ndet));
     CK(launch_to_float(in, c->d_cf, c->ndet, c->stream));
     a.cf = c->d_cf;
@@ -1996,7 +2006,7 @@ void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wos, c->d_fexp, c->d_cf,
+  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wbf, c->d_Wos, c->d_fexp, c->d_cf,
                   c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
                   c->d_tmp_out, c->d_lrUt64, c->d_lrUL64};
   for (void *p : ptrs)
@@ -2181,6 +2191,11 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
     }
+  }
+  if (bf_W_elems(c->npair) > 0) {  // BF16x3 operand B and the kernel's launch shape
+    TRY(cuda_ok(cudaMalloc((void **)&c->d_Wbf, sizeof(uint16_t) * bf_W_elems(c->npair)), "cudaMalloc"));
+    TRY(cuda_ok(launch_split_W_bf(c->d_W, c->npair, c->d_Wbf, c->stream), "split kernel"));
+    c->bf_grid = bf_grid(c->npair, c->ndet, c->nsm);
   }
   // low-rank form of W for the FP64 SIMT contraction (lowrank.h, df_factor)
   const char *lr_mode = std::getenv("SBCI_LOWRANK");  // "0": keep the full contraction

@@ -182,6 +182,15 @@ cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid,
 bool fc_dims(int npair, int na, int nb, int nlink_b, int *Kp, int *Np, uint32_t *cols, size_t *smem);
 int fc_grid(int npair, int na, int nb, int nlink_b, int num_sms);  // 0: unsupported shape
 cudaError_t launch_fused_column(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
+// tcgen05 BF16x3 gather + contract (kernels_bf.cu) for npair <= 136; writes
+// FP32 G like prec 1.  W as BF16 hi / lo operand B: bf_W_elems(npair) uint16,
+// made once per context by launch_split_W_bf.
+bool bf_dims(int npair, int *Kp, int *Np, uint32_t *cols, size_t *smem);
+int bf_grid(int npair, long long ndet, int num_sms);  // 0: unsupported shape
+size_t bf_W_elems(int npair);
+cudaError_t launch_split_W_bf(const double *W, int npair, uint16_t *out, cudaStream_t s);
+cudaError_t launch_gather_contract_bf(const SigmaArgs &a, const uint16_t *Wbf, int *status, int grid,
+                                      cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
 // Helper kernels (kernels_vec.cu)

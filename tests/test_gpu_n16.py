@@ -70,3 +70,23 @@ def test_mixed_ground_state_n16(ctx16):
     hx = sc.sampled_sigma_rows(I.h1, I.eri, 8, 8, x, rows)
     e_el = E[0] - I.e_core
     assert np.abs(hx - e_el * x[rows]).max() < p.r0
+
+
+def test_sigma_bf16x3_n16_sampled_rows(ctx16):
+    """The tensor-core contraction at n = 16 (Kp = Np = 144, BF16 operands):
+    sampled rows against the oracle within the BF16x3 bound of 2e-4 of
+    max|sigma| (see test_gpu_bf16), through the tcgen05 kernel."""
+    import torch
+
+    sbci, I, ctx = ctx16
+    c = torch.from_numpy(inputs.random_vector(12870, 12870, 162)).cuda()
+    ctx.profile(False)
+    s = ctx.sigma(c, prec=sbci.SBCI_BF16X3)
+    assert ctx.profile_read()["sigma_gather_contract_bf16"][0] == 1
+    rows = np.random.default_rng(18).choice(ctx.ndet, 12, replace=False)
+    ref = sc.sampled_sigma_rows(I.h1, I.eri, 8, 8, c.cpu().numpy(), rows)
+    got = s.reshape(-1)[torch.from_numpy(rows).cuda()].cpu().numpy()
+    scale = float(s.abs().max())
+    assert np.abs(got - ref).max() < 2e-4 * scale
+    del c, s
+    torch.cuda.empty_cache()
