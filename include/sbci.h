@@ -128,6 +128,14 @@ typedef struct {
   int n_restart[4];   /* restarts by cause: S62a, S62b, S62c, max_cycle */
   long long ctl_cycles; /* SM clock cycles the device controller (convergence and
                            restart tests, subspace solve) spent on this state */
+  double s136_ratio;  /* energy-conservation health of the state (Section S4,
+                         Eq. S136): geometric mean of |Delta E / ((2/c) Delta T)|
+                         over its later steps with |Delta E| > 1e-6 hartree
+                         (Delta E = E_t - E_{t+1}, the trace's s136 as the
+                         denominator); near 1 when the classical energy of
+                         Eq. 1 is conserved across updates; 0 if no step
+                         qualified */
+  int s136_steps;     /* steps in s136_ratio */
 } sbci_report;
 
 typedef struct {
@@ -145,6 +153,11 @@ typedef struct {
                            in Eqs. S53-S55): the step was taken on the
                            first-step path from x */
   int prec;           /* sbci_precision of the sigma used in the step */
+  double s136;        /* right-hand side of Eq. S136 for the update of this step,
+                         (2/c_{t-1}) Delta T = (b_{t-1}/c_{t-1}) (y_{t+1}^T M y_{t+1}
+                         - y_t^T M y_t) with the mass M = D - E_{t+1} (Section S4,
+                         Eqs. S134-S136, indices of the update y_t -> y_{t+1});
+                         NaN on first steps; 0 in host records */
 } sbci_trace_record;
 
 /* Fills *p with the defaults listed above.  Returns SBCI_ERR_INVALID on NULL. */

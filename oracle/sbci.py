@@ -86,6 +86,11 @@ class StepRecord:
     dE: float
     dz: float
     event: str  # "", "converged", "restart:a", "restart:b", "restart:c", "restart:max"
+    # right-hand side of Eq. S136 for this step's update, (2/c_{t-1}) Delta T
+    # (Eqs. S134-S136 with the indices shifted to the update of step t, which
+    # takes y_t to y_{t+1}): (b_{t-1}/c_{t-1}) (y_{t+1}^T M y_{t+1} - y_t^T M y_t),
+    # M = D - E_{t+1}; NaN on first steps and where c_{t-1} = 0
+    s136: float = float("nan")
 
 
 @dataclass
@@ -208,6 +213,7 @@ class SBCI1:
         nstep = 0
         restarts = {"a": 0, "b": 0, "c": 0, "max": 0}
         second = None
+        bc_prev = None  # (b, c) of the previous step, for the Eq. S136 diagnostic
         while True:
             if self.n_sigma - sigma0 >= p.max_sigma:
                 return StateResult(E, x / np.linalg.norm(x), False, self.n_sigma - sigma0,
@@ -250,6 +256,13 @@ class SBCI1:
                 Y_new = Y - c * Z  # S57
                 x_new = x + b * y_new  # S58
                 X_new = X + b * Y_new  # S59
+            s136 = float("nan")
+            if t > 0 and bc_prev is not None and bc_prev[1] != 0.0:
+                # Section S4: the kinetic-energy change of the update with the
+                # mass M = D - E_{t+1} (the preconditioner's matrix), scaled by 2/c
+                M = self.diag - E_new
+                s136 = (bc_prev[0] / bc_prev[1]) * (y_new @ (M * y_new) - y @ (M * y))
+            bc_prev = (b, c)
             # second Ritz vector in terms of the pre-update vectors (S1.4)
             cx, cy, cz, E2 = sec
             second = (cx * x + cy * y + cz * z, cx * X + cy * Y + cz * Z, E2)
@@ -259,12 +272,13 @@ class SBCI1:
             nstep += 1
             x, X, y, Y, zp = x_new, X_new, y_new, Y_new, zp_new
             if dE < p.eps0 and dz < p.r0:  # S61
-                self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz, "converged"))
+                self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz, "converged", s136))
                 return StateResult(E_new, x / np.linalg.norm(x), True, self.n_sigma - sigma0,
                                    nstep, restarts), second
             cause = restart_cause(p, alpha, b, k, dE, dz, t)
             self.trace.append(StepRecord(alpha, t, E_new, b, c, k, dE, dz,
-                                         f"restart:{cause}" if cause else ("undef" if undefined else "")))
+                                         f"restart:{cause}" if cause else ("undef" if undefined else ""),
+                                         s136))
             E = E_new
             if cause:  # restart of Algorithm 1 with R4
                 restarts[cause] += 1

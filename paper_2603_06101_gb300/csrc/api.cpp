@@ -605,6 +605,20 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residua
   r.n_step = h.n_step;
   for (int i = 0; i < 4; ++i) r.n_restart[i] = h.n_restart[i];
   r.ctl_cycles = h.ctl_cycles;
+  {  // Eq. S136 health of the state from its trace (consecutive later steps)
+    double lsum = 0.0;
+    int n = 0;
+    for (size_t i = 1; i < s.trace.size(); ++i) {
+      const sbci_trace_record &p = s.trace[i - 1], &q = s.trace[i];
+      if (q.state != alpha || p.state != alpha || q.t <= 0 || !std::isfinite(q.s136) || q.s136 == 0.0) continue;
+      const double dE = p.energy - q.energy;
+      if (std::fabs(dE) <= 1e-6) continue;
+      lsum += std::log(std::fabs(dE / q.s136));
+      ++n;
+    }
+    r.s136_ratio = n ? std::exp(lsum / n) : 0.0;
+    r.s136_steps = n;
+  }
   if (!converged) s.any_unconverged = 1;
   if (alpha + 1 >= s.k) {
     s.done = true;

@@ -65,6 +65,9 @@ struct CtlHead {
   sbci_trace_record pending;
   int ntrace;  // records committed since the host last drained them
   double dots[S_COUNT];
+  // y_t . (D y_t), y_t . y_t after the previous update and (b, c) of the
+  // previous step: the Eq. S136 diagnostic of the next step
+  double s136_yDy, s136_Nyy, s136_b, s136_c;
   sbci_trace_record *trace_ptr;  // the ring of the device state (CtlState::trace)
 };
 
@@ -405,6 +408,19 @@ __host__ __device__ inline void ctl_check(CtlHead &s) {
   const double dE = fabs(s.E_solve - s.E);
   r.dE = dE;
   r.dz = dz;
+  // Section S4, Eq. S136 (indices of the update of step t, y_t -> y_{t+1}):
+  // (2/c_{t-1}) Delta T = (b_{t-1}/c_{t-1}) (y_{t+1}^T M y_{t+1} - y_t^T M y_t),
+  // M = D - E_{t+1}; defined on later steps (y_t is the previous update's y)
+  r.s136 = (double)NAN;
+  if (r.t > 0 && s.s136_c != 0.0) {
+    const double Et1 = s.E_solve;
+    const double dT = fma(-Et1, d[S_NYY], d[S_YDY]) - fma(-Et1, s.s136_Nyy, s.s136_yDy);
+    r.s136 = s.s136_b * f_recip(s.s136_c) * dT;
+  }
+  s.s136_yDy = d[S_YDY];
+  s.s136_Nyy = d[S_NYY];
+  s.s136_b = r.b;
+  s.s136_c = r.c;
   s.E = s.E_solve;
   const bool low_stage = (s.stage == 0 && r.prec != SBCI_FP64);
   if (!isfinite(dz) || !isfinite(d[S_NXX])) {
@@ -503,6 +519,7 @@ __host__ __device__ inline void ctl_solve(CtlHead &s) {
   r.dz = 0.0;
   r.event = event;
   r.prec = s.prec;
+  r.s136 = 0.0;
   s.pending = r;
   s.E_solve = o.E;
   s.second[0] = o.r[0];

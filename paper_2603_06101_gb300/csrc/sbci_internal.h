@@ -123,7 +123,8 @@ enum Slot : int {
   S_HXZ, S_HYZ, S_HZZ,                                   // sigma epilogue
   S_XCW0,                                                // x_c^i . w, i < kMaxStates
   S_GEN0 = S_XCW0 + kMaxStates,                          // general-purpose dots
-  S_COUNT = S_GEN0 + 16
+  S_YDY = S_GEN0 + 16,                                   // y . (D y) of the update (Eq. S136 diagnostic)
+  S_COUNT
 };
 
 // Arguments of the sigma kernels for one vector.

@@ -52,7 +52,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
   float *zf = proj ? nullptr : s->zf;
   const double guard = s->p.guard;
   const double *pinv = s->pinv_ready ? a.pinv : nullptr;
-  constexpr int NV = 10 + kMaxStates;
+  constexpr int NV = 11 + kMaxStates;  // 10 step dots, x_c . w, y . (D y)
   double acc[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) acc[j] = 0.0;
@@ -90,6 +90,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
 #pragma unroll
       for (int j = 0; j < kMaxStates; ++j)
         if (j < nxc) acc[10 + j] = fma(a.xc[(size_t)j * a.n + i], w, acc[10 + j]);
+      acc[NV - 1] = fma(y * a.diag[i], y, acc[NV - 1]);  // kinetic term of Section S4 (M = D - E)
     }
   };
   if (u.sx == 1.0 && u.sy == 1.0) sweep(std::true_type{});
@@ -101,6 +102,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
   for (int j = 7; j < 10; ++j) slots[j] = proj ? -1 : (S_NXZ + j - 7);
 #pragma unroll
   for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < nxc) ? S_XCW0 + j : -1;
+  slots[NV - 1] = S_YDY;
   block_partials<NV, kStepThreads>(acc, slots, a.partials, nvb, vb);
   if (!last_block(a.counter + 0, nvb)) return false;
   int act[NV];

@@ -52,13 +52,14 @@ class sbci_params(C.Structure):
 class sbci_report(C.Structure):
     _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("converged", C.c_int),
                 ("n_sigma", C.c_int), ("n_sigma_fp64", C.c_int), ("n_step", C.c_int),
-                ("n_restart", C.c_int * 4), ("ctl_cycles", C.c_longlong)]
+                ("n_restart", C.c_int * 4), ("ctl_cycles", C.c_longlong), ("s136_ratio", C.c_double),
+                ("s136_steps", C.c_int)]
 
 
 class sbci_trace_record(C.Structure):
     _fields_ = [("state", C.c_int), ("t", C.c_int), ("energy", C.c_double), ("b", C.c_double),
                 ("c", C.c_double), ("k", C.c_double), ("dE", C.c_double), ("dz", C.c_double),
-                ("event", C.c_int), ("prec", C.c_int)]
+                ("event", C.c_int), ("prec", C.c_int), ("s136", C.c_double)]
 
 
 class sbci_kernel_stat(C.Structure):

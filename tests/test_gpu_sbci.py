@@ -46,6 +46,8 @@ def test_h6_random_start_trajectory_parity():
         assert abs(abs(g.k) - abs(o.k)) < 1e-8
         ev = {0: "", 1: "converged", 2: "restart:a", 3: "restart:b", 4: "restart:c", 5: "restart:max"}[g.event]
         assert ev == o.event
+        # the Eq. S136 right-hand side of the update: defined on the same steps
+        assert np.isfinite(g.s136) == np.isfinite(o.s136)
     v = V[0]
     assert np.linalg.norm(H @ v - (E[0] - I.e_core) * v) < 2e-5
 
@@ -156,3 +158,41 @@ def test_start_noise_matches_oracle(key, k, kw):
         H = sc.dense_hamiltonian(I.h1, I.eri, I.nalpha, I.nbeta)
         w = np.linalg.eigvalsh(H)[:k] + I.e_core
         assert np.abs(np.sort(E) - w).max() < 1e-8
+
+
+@pytest.mark.parametrize("key,c0seed", [(("chain", 6, 1.0), 0), (("chain", 10, 1.2), 0)])
+def test_energy_conservation_diagnostic_matches_oracle(key, c0seed):
+    """Section S4 (Eq. S136) at run time: the device controller's per-step
+    (2/c) Delta T equals the oracle's on the same FP64 trajectory (1e-8 of
+    its scale, while the two runs still agree step by step: the first 40
+    records), and the report's geometric-mean ratio |Delta E / ((2/c) Delta T)|
+    is the oracle's own, computed the same way from its trace."""
+    sbci = require_lib()
+    I = make_integrals(key)
+    ctx = sbci.Context.from_integrals(I)
+    c0 = inputs.random_vector(ctx.na, ctx.nb, c0seed) if c0seed is not None else None
+    kw = {"init": 1} if c0 is not None else {}
+    E, _, R, st = ctx.solve(1, sbci.params(**kw), c0=c0)
+    assert st == sbci.SBCI_OK
+    run, _ = _oracle_run(key, 1, c0=c0)
+    tr = ctx.trace()
+    n = min(40, len(tr), len(run.trace))
+    checked = 0
+    for g, o in list(zip(tr, run.trace))[:n]:
+        assert abs(g.energy - o.energy) < 1e-10  # still the same trajectory
+        assert np.isfinite(g.s136) == np.isfinite(o.s136)
+        if np.isfinite(o.s136):
+            assert abs(g.s136 - o.s136) <= 1e-8 * max(abs(o.s136), 1e-6), (g.s136, o.s136)
+            checked += 1
+    assert checked >= 5
+    # the report's summary against the same summary of the oracle's trace
+    lsum, cnt = 0.0, 0
+    for p_, q in zip(run.trace, run.trace[1:]):
+        if q.t > 0 and np.isfinite(q.s136) and q.s136 != 0.0 and abs(p_.energy - q.energy) > 1e-6:
+            lsum += np.log(abs((p_.energy - q.energy) / q.s136))
+            cnt += 1
+    assert R[0].s136_steps > 0
+    if len(tr) == len(run.trace):
+        assert R[0].s136_steps == cnt
+        assert abs(R[0].s136_ratio - np.exp(lsum / cnt)) < 1e-6 * np.exp(lsum / cnt)
+    assert 0.1 < R[0].s136_ratio < 10.0

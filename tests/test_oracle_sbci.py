@@ -275,3 +275,32 @@ def test_restart_cause_on_constructed_scalars():
     assert cause(b=5e-3, dE=5e-8, k=2.0, dz=2.0, t=19) == "a"
     assert cause(k=2.0, dz=2.0, t=19) == "b"
     assert cause(dz=2.0, t=19) == "c"
+
+
+def test_energy_conservation_in_the_trace():
+    """The trace's per-step Eq. S136 right-hand side (2/c) Delta T against the
+    Rayleigh-quotient drop Delta E of the same update (Eq. S134), on H8: the
+    paper's Section S4 finds the two close at every step (Fig. S10); here the
+    median of |Delta E / ((2/c) Delta T)| over the later steps that still move
+    the energy (|Delta E| > 1e-5) lies within a factor 3 of one (the band of
+    the diagnostic test above; the sign follows the z' convention of reading
+    R1), and first steps carry no value."""
+    I = inputs.h_chain(8, 1.0)
+    sig = sg.StringSigma(I.h1, I.eri, 4, 4)
+    D = sc.diagonal_by_occupation(I.h1, I.eri, 4, 4)
+    run = sbci.SBCI1(sig.apply, D, (70, 70))
+    run.solve(2)
+    tr = run.trace
+    ratios = []
+    for prev, cur in zip(tr, tr[1:]):
+        if cur.t == 0:
+            assert np.isnan(cur.s136)
+            continue
+        if prev.state != cur.state or not np.isfinite(cur.s136):
+            continue
+        dE = prev.energy - cur.energy
+        if abs(dE) > 1e-5:
+            ratios.append(dE / cur.s136)
+    assert len(ratios) >= 10
+    med = float(np.median(np.abs(ratios)))
+    assert 0.3 < med < 3.0, med
