@@ -410,6 +410,15 @@ SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
   return a;
 }
 
+// Virtual blocks of the update and projection sweeps: a singlet-sector solve
+// sweeps pairs of 16 x 16 tiles (one tile pair per block where the partials
+// buffer allows), every other solve ~4 elements per thread.
+int step_blocks(const sbci_ctx *c) {
+  if (!use_symfin(c)) return step_grid(c->ndet, c->nsm);
+  const long long T = (c->Na + 15) / 16, units = T * (T + 1) / 2;
+  return (int)std::max(1LL, std::min(units, (long long)c->grid));
+}
+
 // The sector sigma of a TF32x3 step runs as the column-fused kernel (gather,
 // contraction and alpha-only scatter in one launch, G never in global memory)
 // where the shape allows it.
@@ -435,7 +444,7 @@ void count_bodies(sbci_ctx *c, int prec, long long bodies) {
 sbci_status launch_body(sbci_ctx *c, int prec, unsigned long long cond, bool timing) {
   const StepArgs st = step_args(c, cond);
   const SigmaArgs sa = sigma_ctl_args(c, prec, cond);
-  const int g = step_grid(c->ndet, c->nsm);
+  const int g = step_blocks(c);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   auto L = [&](int kid, auto &&f) -> sbci_status {
     if (timing) return timed(c, kid, f);
@@ -1936,7 +1945,7 @@ bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
   return true;
 }
 
-int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_grid(c->ndet, c->nsm); }
+int sbci::ctx_step_blocks(const sbci_ctx *c) { return step_blocks(c); }
 int sbci::ctx_scatter_blocks(const sbci_ctx *c) { return scatter_grid(c->ndet, c->nsm); }
 int sbci::ctx_symfin_blocks(const sbci_ctx *c) { return use_symfin(c) ? symfin_grid(c->Na, c->nsm) : 0; }
 long long sbci::ctx_ndet(const sbci_ctx *c) { return c->ndet; }

@@ -11,11 +11,11 @@ namespace sbci {
 
 // Block partials of NV values per thread -> partials[slot * grid + block]
 // (slots[j] < 0: value j unused).  NT = threads per block; block is the
-// (virtual) block index within its grid of size grid.
+// (virtual) block index within its grid of size grid; buf: shared memory of
+// [NT / 32][NV][33] doubles.
 template <int NV, int NT>
-__device__ __forceinline__ void block_partials(const double (&v)[NV], const int (&slots)[NV],
-                                               double *partials, int grid, int block) {
-  __shared__ double buf[NT / 32][NV][33];
+__device__ __forceinline__ void block_partials_in(const double (&v)[NV], const int (&slots)[NV],
+                                                  double *partials, int grid, int block, double (*buf)[NV][33]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();  // a persistent block may come back with the buffer still in use
 #pragma unroll
@@ -33,6 +33,20 @@ __device__ __forceinline__ void block_partials(const double (&v)[NV], const int 
     for (int w = 0; w < NT / 32; ++w) s += buf[w][j][32];
     if (slots[j] >= 0) partials[(size_t)slots[j] * grid + block] = s;
   }
+}
+
+// The same with the block's own shared buffer.
+template <int NV, int NT>
+__device__ __forceinline__ void block_partials(const double (&v)[NV], const int (&slots)[NV],
+                                               double *partials, int grid, int block) {
+  __shared__ double buf[NT / 32][NV][33];
+  block_partials_in<NV, NT>(v, slots, partials, grid, block, buf);
+}
+
+// Bytes of the caller-provided buffer of block_partials_in.
+template <int NV, int NT>
+constexpr size_t block_partials_bytes() {
+  return sizeof(double) * (NT / 32) * NV * 33;
 }
 
 // Returns true in exactly one of nblocks (virtual) blocks: the last one to

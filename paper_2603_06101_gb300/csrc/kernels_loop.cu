@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(kStepThreads) k_update_ctl(StepArgs a) {
     halt_loop(a.cond);
     return;
   }
-  const bool halted = update_body(a, blockIdx.x, gridDim.x);
+  __shared__ __align__(16) unsigned char s_upd[kUpdSmemBytes];
+  const bool halted = a.sector ? update_body_sym(a, blockIdx.x, gridDim.x, s_upd)
+                               : update_body(a, blockIdx.x, gridDim.x, s_upd);
   if (halted && a.cond && threadIdx.x == 0)
     cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
 }
@@ -432,12 +434,15 @@ __device__ __forceinline__ int find_job(const int *off, int njobs, int item) {
 }
 
 __global__ void __launch_bounds__(kStepThreads) k_update_batch(BatchTable *bt) {
+  __shared__ __align__(16) unsigned char s_upd[kUpdSmemBytes];
   const int nj = bt->njobs;
   const int total = bt->off_step[nj];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int j = find_job(bt->off_step, nj, item);
     const int vb = item - bt->off_step[j], nvb = bt->off_step[j + 1] - bt->off_step[j];
-    if (update_body(bt->job[j].step, vb, nvb) && threadIdx.x == 0) bt->halted[j] = 1;
+    const StepArgs &sa = bt->job[j].step;
+    const bool halted = sa.sector ? update_body_sym(sa, vb, nvb, s_upd) : update_body(sa, vb, nvb, s_upd);
+    if (halted && threadIdx.x == 0) bt->halted[j] = 1;
   }
 }
 

@@ -37,6 +37,17 @@ __device__ __forceinline__ void split_det(long long I, int nb, int &ia, int &ib)
   ib = (int)(u - q * (unsigned)nb);
 }
 
+// Unit u of the T (T + 1) / 2 pairs of 32 x 32 tiles (ti, tj), ti >= tj, of
+// a square matrix (row-major over ti): the work units of the kernels that
+// read a tile and its transpose together.
+__device__ __forceinline__ void tri_unit(int u, int *ti, int *tj) {
+  int t = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while (t * (t + 1) / 2 > u) --t;
+  while ((t + 1) * (t + 2) / 2 <= u) ++t;
+  *ti = t;
+  *tj = u - t * (t + 1) / 2;
+}
+
 // Visits the links of one string U at a time: the U list entries, then the U
 // gathered values (independent loads, all in flight), then the U updates.
 // Entry e of the list is lst[e * stride] (stride 1: a row of a [N][nlink]

@@ -79,13 +79,6 @@ __device__ __forceinline__ bool scatter_body(const SigmaArgs &a, int vb, int nvb
 // of sigma against x, y and z, and the last block runs the subspace solve.
 constexpr int kSfT = 32;
 
-__device__ __forceinline__ void sf_tile_of(int u, int *ti, int *tj) {
-  int t = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-  while (t * (t + 1) / 2 > u) --t;
-  while ((t + 1) * (t + 2) / 2 <= u) ++t;
-  *ti = t;
-  *tj = u - t * (t + 1) / 2;
-}
 
 template <typename AccT>
 __device__ __forceinline__ bool symfin_body(const SigmaArgs &a, int vb, int nvb) {
@@ -100,7 +93,7 @@ __device__ __forceinline__ bool symfin_body(const SigmaArgs &a, int vb, int nvb)
   double dots[3] = {0.0, 0.0, 0.0};
   for (int u = vb; u < units; u += nvb) {
     int ti, tj;
-    sf_tile_of(u, &ti, &tj);
+    tri_unit(u, &ti, &tj);
     __syncthreads();  // the previous unit's readers are done
     for (int k = tid; k < kSfT * kSfT; k += blockDim.x) {
       const int r = k / kSfT, c = k - r * kSfT;

@@ -40,7 +40,9 @@ __device__ __forceinline__ double recip(double d) {
 // Symplectic-Euler update sweep (Eqs. 10-11, S56-S59), residual (Eq. S60) and
 // preconditioner (Eqs. 6-7); the last block runs the convergence / restart
 // test of the controller (Eq. S61, S62).
-__device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) {
+constexpr int kUpdNV = 11 + kMaxStates;  // 10 step dots, x_c . w, y . (D y)
+
+__device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb, unsigned char *smem) {
   CtlState *s = a.ctl;
   if (s->halt) return false;
   const UpdParams u = s->up;
@@ -52,7 +54,7 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
   float *zf = proj ? nullptr : s->zf;
   const double guard = s->p.guard;
   const double *pinv = s->pinv_ready ? a.pinv : nullptr;
-  constexpr int NV = 11 + kMaxStates;  // 10 step dots, x_c . w, y . (D y)
+  constexpr int NV = kUpdNV;
   double acc[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) acc[j] = 0.0;
@@ -103,7 +105,8 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
 #pragma unroll
   for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < nxc) ? S_XCW0 + j : -1;
   slots[NV - 1] = S_YDY;
-  block_partials<NV, kStepThreads>(acc, slots, a.partials, nvb, vb);
+  block_partials_in<NV, kStepThreads>(acc, slots, a.partials, nvb, vb,
+                                      reinterpret_cast<double (*)[NV][33]>(smem));
   if (!last_block(a.counter + 0, nvb)) return false;
   int act[NV];
   int na = 0;
@@ -117,13 +120,163 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb) 
          }) != 0;
 }
 
-// Projection against the stored states (Eq. S31) with the c = c^T
-// symmetrisation of the singlet sector; dots x.z, y.z, z.z.
+// The update sweep of a singlet-sector solve (c = c^T, n_alpha = n_beta):
+// every vector of the step is symmetric as a matrix, so the sweep takes each
+// symmetric pair of elements (i, j), (j, i) once.  Work unit: a pair of 16 x 16
+// tiles, (ti, tj) read coalesced and its transpose (tj, ti) written through
+// shared memory (on a diagonal tile the elements with row >= column).  Per
+// pair: the recurrences and the residual once; the preconditioner at both
+// diagonal elements D_ij and D_ji, and the symmetrised w = (w_ij + w_ji) / 2
+// of reading R10 (formerly the projection's first step); the dot products
+// weighted by the pair's two elements.  For the ground state (no stored
+// state to project against) it writes z itself, with its FP32 copy and the
+// dots x.z, y.z, z.z, and the projection pass has nothing left to do.
+constexpr int kSymT = 16;  // 256 threads: one element of the tile each
+struct SymSmem {
+  double v[5][kSymT][kSymT + 1];  // y, Y, x, X, w of tile (ti, tj), stored transposed
+  float f[kSymT][kSymT + 1];      // FP32 copy of z, transposed
+  double dT[kSymT][kSymT + 1];    // D of tile (tj, ti)
+  double pT[kSymT][kSymT + 1];    // 1 / guarded(D - E_c^0) of tile (tj, ti) (excited states)
+};
+// Shared memory of an update kernel: the tile buffers of the symmetric sweep
+// or the block reduction's buffer (used one after the other).
+constexpr size_t kUpdSmemBytes = sizeof(SymSmem) > block_partials_bytes<kUpdNV, kStepThreads>()
+                                     ? sizeof(SymSmem)
+                                     : block_partials_bytes<kUpdNV, kStepThreads>();
+
+__device__ __forceinline__ bool update_body_sym(const StepArgs &a, int vb, int nvb, unsigned char *smem) {
+  SymSmem &sm = *reinterpret_cast<SymSmem *>(smem);
+  CtlState *s = a.ctl;
+  if (s->halt) return false;
+  const UpdParams u = s->up;
+  const int alpha = s->alpha;
+  const bool direct = (alpha == 0);  // z itself, no projection pass
+  const int nxc = alpha;
+  const double *z = s->zc, *Z = s->Zc;
+  double *wout = direct ? s->zn : a.w;
+  float *zf = direct ? s->zf : nullptr;
+  const double guard = s->p.guard;
+  const double *pinv = s->pinv_ready ? a.pinv : nullptr;
+  const bool unit = (u.sx == 1.0 && u.sy == 1.0);
+  constexpr int NV = kUpdNV;
+  // half-weighted sums: a pair of elements adds its value once, a diagonal
+  // element half of it; the sums are doubled (exactly) at the end
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+  const int n = a.na;
+  const int T = (n + kSymT - 1) / kSymT, units = T * (T + 1) / 2;
+  const int tid = threadIdx.x, c = tid & (kSymT - 1), r0 = tid / kSymT;
+  constexpr int kRows = kStepThreads / kSymT;  // rows of a tile per pass
+  for (int un = vb; un < units; un += nvb) {
+    int ti, tj;
+    tri_unit(un, &ti, &tj);
+    __syncthreads();  // the previous unit's readers of the shared buffers are done
+    for (int r = r0; r < kSymT; r += kRows) {  // D (and the excited-state preconditioner) of tile (tj, ti)
+      const int i2 = tj * kSymT + r, j2 = ti * kSymT + c;
+      const bool in = i2 < n && j2 < n;
+      sm.dT[r][c] = in ? a.diag[(size_t)i2 * n + j2] : 0.0;
+      if (pinv) sm.pT[r][c] = in ? pinv[(size_t)i2 * n + j2] : 0.0;
+    }
+    __syncthreads();
+    for (int r = r0; r < kSymT; r += kRows) {
+      const int i = ti * kSymT + r, j = tj * kSymT + c;
+      if (i >= n || j >= n || (ti == tj && r < c)) continue;
+      const bool on_diag = (i == j);
+      const size_t I = (size_t)i * n + j;
+      const double y = fma(-u.c, z[I], unit ? a.y[I] : u.sy * a.y[I]);
+      const double Y = fma(-u.c, Z[I], unit ? a.Y[I] : u.sy * a.Y[I]);
+      const double x = fma(u.b, y, unit ? a.x[I] : u.sx * a.x[I]);
+      const double X = fma(u.b, Y, unit ? a.X[I] : u.sx * a.X[I]);
+      const double zp = fma(-u.E, x, X) * u.kinv;
+      const double dA = a.diag[I], dB = sm.dT[c][r];
+      const double pa = pinv ? pinv[I] : recip(guarded(dA - u.Epre, guard));
+      const double pb = on_diag ? pa : (pinv ? sm.pT[c][r] : recip(guarded(dB - u.Epre, guard)));
+      const double w = 0.5 * (zp * pa + zp * pb);
+      a.y[I] = y;
+      a.Y[I] = Y;
+      a.x[I] = x;
+      a.X[I] = X;
+      wout[I] = w;
+      if (zf) zf[I] = (float)w;
+      sm.v[0][c][r] = y;
+      sm.v[1][c][r] = Y;
+      sm.v[2][c][r] = x;
+      sm.v[3][c][r] = X;
+      sm.v[4][c][r] = w;
+      if (zf) sm.f[c][r] = (float)w;
+      // the dots in half weight: the first factor halved on the diagonal
+      auto dots = [&](auto diag_tag) {
+        constexpr bool Dg = decltype(diag_tag)::value;
+        const double xh = Dg ? 0.5 * x : x, yh = Dg ? 0.5 * y : y;
+        const double zh = Dg ? 0.5 * zp : zp, wh = Dg ? 0.5 * w : w;
+        acc[0] = fma(xh, x, acc[0]);
+        acc[1] = fma(xh, y, acc[1]);
+        acc[2] = fma(yh, y, acc[2]);
+        acc[3] = fma(xh, X, acc[3]);
+        acc[4] = fma(xh, Y, acc[4]);
+        acc[5] = fma(yh, Y, acc[5]);
+        acc[6] = fma(zh, zp, acc[6]);
+        if (direct) {
+          acc[7] = fma(xh, w, acc[7]);
+          acc[8] = fma(yh, w, acc[8]);
+          acc[9] = fma(wh, w, acc[9]);
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxStates; ++q)
+          if (q < nxc) acc[10 + q] = fma(a.xc[(size_t)q * a.n + I], wh, acc[10 + q]);
+        // y^T D y in full weight: y^2 (D_ij + D_ji) for a pair, y^2 D_ii on the diagonal
+        acc[NV - 1] = fma(yh * y, dA + dB, acc[NV - 1]);
+      };
+      if (on_diag) dots(std::true_type{});
+      else dots(std::false_type{});
+    }
+    __syncthreads();
+    // tile (tj, ti): element (r, c) is the transpose of (c, r) of tile (ti, tj)
+    for (int r = r0; r < kSymT; r += kRows) {
+      const int i2 = tj * kSymT + r, j2 = ti * kSymT + c;
+      if (i2 >= n || j2 >= n || (ti == tj && r >= c)) continue;
+      const size_t I2 = (size_t)i2 * n + j2;
+      a.y[I2] = sm.v[0][r][c];
+      a.Y[I2] = sm.v[1][r][c];
+      a.x[I2] = sm.v[2][r][c];
+      a.X[I2] = sm.v[3][r][c];
+      wout[I2] = sm.v[4][r][c];
+      if (zf) zf[I2] = sm.f[r][c];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NV - 1; ++j) acc[j] = 2.0 * acc[j];  // (the y^T D y sum is in full weight)
+  __syncthreads();  // the tile buffers become the reduction's
+  int slots[NV];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) slots[j] = S_NXX + j;
+#pragma unroll
+  for (int j = 7; j < 10; ++j) slots[j] = direct ? (S_NXZ + j - 7) : -1;
+#pragma unroll
+  for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < nxc) ? S_XCW0 + j : -1;
+  slots[NV - 1] = S_YDY;
+  block_partials_in<NV, kStepThreads>(acc, slots, a.partials, nvb, vb,
+                                      reinterpret_cast<double (*)[NV][33]>(smem));
+  if (!last_block(a.counter + 0, nvb)) return false;
+  int act[NV];
+  int na = 0;
+  for (int j = 0; j < NV; ++j)
+    if (slots[j] >= 0) act[na++] = slots[j];
+  finish_slots(a.partials, nvb, act, na, s->dots, a.counter + 0);
+  return ctl_run_shadowed(s, [](CtlHead &h) {
+           h.iters += 1;
+           if (h.iters > h.iter_cap) h.halt = H_CAP;
+           ctl_check(h);
+         }) != 0;
+}
+
+// Projection against the stored states (Eq. S31); dots x.z, y.z, z.z.
 __device__ __forceinline__ void project_body(const StepArgs &a, int vb, int nvb) {
   CtlState *s = a.ctl;
   if (s->halt) return;
   const int alpha = s->alpha;
-  if (!(alpha > 0 || a.sector)) return;  // the update wrote z directly
+  if (alpha == 0) return;  // the update wrote z directly (symmetrised in the sector)
   double coef[kMaxStates];
 #pragma unroll
   for (int j = 0; j < kMaxStates; ++j) coef[j] = (j < alpha) ? s->dots[S_XCW0 + j] : 0.0;
@@ -132,12 +285,7 @@ __device__ __forceinline__ void project_body(const StepArgs &a, int vb, int nvb)
   double acc[3] = {0.0, 0.0, 0.0};
   const long long stride = (long long)nvb * blockDim.x;
   for (long long i = (long long)vb * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    double v = a.w[i];
-    if (a.sector) {
-      int ia, ib;
-      split_det(i, a.nb, ia, ib);
-      v = 0.5 * (v + a.w[(size_t)ib * a.nb + ia]);
-    }
+    double v = a.w[i];  // (symmetric in the sector: the update symmetrised it)
 #pragma unroll
     for (int j = 0; j < kMaxStates; ++j)
       if (j < alpha) v = fma(-coef[j], a.xc[(size_t)j * a.n + i], v);
