@@ -157,7 +157,9 @@ typedef struct {
                          (2/c_{t-1}) Delta T = (b_{t-1}/c_{t-1}) (y_{t+1}^T M y_{t+1}
                          - y_t^T M y_t) with the mass M = D - E_{t+1} (Section S4,
                          Eqs. S134-S136, indices of the update y_t -> y_{t+1});
-                         NaN on first steps; 0 in host records */
+                         its sign is that of c, which the sign of the subspace
+                         eigenvector decides; NaN on first steps; 0 in host
+                         records */
 } sbci_trace_record;
 
 /* Fills *p with the defaults listed above.  Returns SBCI_ERR_INVALID on NULL. */

@@ -411,12 +411,14 @@ SigmaArgs sigma_ctl_args(sbci_ctx *c, int prec, unsigned long long cond) {
 }
 
 // Virtual blocks of the update and projection sweeps: a singlet-sector solve
-// sweeps pairs of 16 x 16 tiles (one tile pair per block where the partials
-// buffer allows), every other solve ~4 elements per thread.
+// sweeps pairs of 16 x 16 tiles, four tile pairs per virtual block (each
+// block ends with an FP64 reduction of its 19 dot products, which costs as
+// many FP64 instructions as about one tile pair of the sweep itself); every
+// other solve ~4 elements per thread.
 int step_blocks(const sbci_ctx *c) {
   if (!use_symfin(c)) return step_grid(c->ndet, c->nsm);
   const long long T = (c->Na + 15) / 16, units = T * (T + 1) / 2;
-  return (int)std::max(1LL, std::min(units, (long long)c->grid));
+  return (int)std::max(1LL, std::min((units + 3) / 4, (long long)c->grid));
 }
 
 // The sector sigma of a TF32x3 step runs as the column-fused kernel (gather,

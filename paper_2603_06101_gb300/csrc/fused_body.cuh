@@ -21,7 +21,8 @@
 //      forms sigma = A^T + A, which is the same matrix.
 // D, the split, the MMAs and the scatter's summation order are those of the
 // tile kernel (tc_tile) and of the alpha-only scatter (scatter_body), so the
-// column kernel gives bitwise the same A.
+// column kernel gives the same A (up to the sign of zero: the gathers store
+// each pair's single term where the tile kernel adds it to zero).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,7 +42,8 @@ struct FcSmem {
   float *A, *Alo;       // operand D (alpha part / hi, beta part / lo); G column after the MMAs
   uint32_t *Bhi, *Blo;  // W split into TF32 hi / lo (operand B)
   float *zrow;          // row b of z, kFcMaxStr floats
-  uint32_t *lb;         // link words of string b
+  uint32_t *lb;         // links of string b, decoded: [kFcMaxLink] row offsets J * nb, then
+                        // [kFcMaxLink] operand column offsets | sign << 31
   uint32_t sA, sAlo, sBhi, sBlo, sbar;
 };
 
@@ -54,7 +56,7 @@ __host__ __device__ constexpr int fc_acc_stride(int Np) {
 
 // Dynamic shared memory of a column CTA with Kp x Np operands.
 __host__ __device__ constexpr size_t fc_smem_bytes(int Kp, int Np) {
-  return (size_t)(2 * kTcM * Kp + 2 * Np * Kp + kFcMaxStr + kFcMaxLink) * 4 + 16;
+  return (size_t)(2 * kTcM * Kp + 2 * Np * Kp + kFcMaxStr + 2 * kFcMaxLink) * 4 + 16;
 }
 
 __device__ __forceinline__ FcSmem fc_carve(unsigned char *smem, int Kp, int Np) {
@@ -69,12 +71,16 @@ __device__ __forceinline__ FcSmem fc_carve(unsigned char *smem, int Kp, int Np) 
   sm.sAlo = smem_u32(sm.Alo);
   sm.sBhi = smem_u32(sm.Bhi);
   sm.sBlo = smem_u32(sm.Blo);
-  sm.sbar = smem_u32(sm.lb + kFcMaxLink);  // 8-byte aligned: every buffer above is a multiple of 8 bytes
+  sm.sbar = smem_u32(sm.lb + 2 * kFcMaxLink);  // 8-byte aligned: every buffer above is a multiple of 8 bytes
   return sm;
 }
 
 // The TMEM address slot, after the mbarrier.
-__device__ __forceinline__ uint32_t *fc_tmem_slot(const FcSmem &sm) { return sm.lb + kFcMaxLink + 2; }
+__device__ __forceinline__ uint32_t *fc_tmem_slot(const FcSmem &sm) { return sm.lb + 2 * kFcMaxLink + 2; }
+
+// Offset of column q within a row of the K-major no-swizzle TF32 operand (the
+// row's own part is (r / 8) * Kp * 8 + (r % 8) * 4, see opnd_off).
+__device__ __forceinline__ int fc_qoff(int q) { return (q >> 2) * 32 + (q & 3); }
 
 // The tile kernel's operand B loader, on the column CTA's buffers.
 __device__ __forceinline__ void fc_load_B(const SigmaArgs &a, int Kp, int Np, const FcSmem &fm) {
@@ -117,11 +123,16 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   // 0. row b of z (z[b][j] = z[j][b]) and the link words of b; the previous
   //    column's readers of these buffers finished at its last barrier
   for (int j = tid; j < na; j += blockDim.x) sm.zrow[j] = __ldg(zf + (size_t)b * nb + j);
-  for (int e = tid; e < a.nlink_b; e += blockDim.x) sm.lb[e] = __ldg(a.link_b + (size_t)b * a.nlink_b + e);
+  for (int e = tid; e < a.nlink_b; e += blockDim.x) {
+    const uint32_t v = __ldg(a.link_b + (size_t)b * a.nlink_b + e);
+    sm.lb[e] = (uint32_t)link_J(v) * (uint32_t)nb;
+    sm.lb[kFcMaxLink + e] = (uint32_t)fc_qoff(link_pair(v)) | (v & kSignBit);
+  }
   __syncthreads();
   const int r = tid & (kTcM - 1);
   const int half = tid >> 7;  // 0: alpha links of row r, 1: beta links of b at column r
   const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
+  const int rbase = (r >> 3) * (Kp * 8) + (r & 7) * 4;  // row r's part of an operand offset
   for (int t = 0; t < ntile; ++t) {
     if (t > 0) {  // the previous tile's MMAs read A / Alo: wait before overwriting them
       *pending = 1;
@@ -132,28 +143,30 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
     float *mine = half ? sm.Alo : sm.A;
     for (int q = 0; q < Kp; q += 4)
       *reinterpret_cast<float4 *>(mine + opnd_off(r, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    // each pair receives at most one term per spin (a string's links have
+    // distinct pairs), so the gathers store into the zeroed rows
     if (ia < na) {
       if (half == 0) {
         const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
         const float *zr = sm.zrow;
-        for_links_pipelined<8, float>(
+        for_links_pipelined<16, float>(
             la, a.nlink_a, 1, [&](uint32_t v) { return zr[link_J(v)]; },
-            [&](uint32_t v, float f) { mine[opnd_off(r, link_pair(v), Kp)] += link_neg(v) ? -f : f; });
+            [&](uint32_t v, float f) { mine[rbase + fc_qoff(link_pair(v))] = link_neg(v) ? -f : f; });
       } else {
         const float *zc = zf + ia;
-        const uint32_t *lb = sm.lb;
+        const uint32_t *lJ = sm.lb, *lQ = sm.lb + kFcMaxLink;
         const int nl = a.nlink_b;
-        // the link words are shared-memory reads; the z loads of 8 links are in flight together
-        for (int e = 0; e < nl; e += 8) {
-          float f[8];
+        // decoded links from shared memory; the z loads of 16 links are in flight together
+        for (int e = 0; e < nl; e += 16) {
+          float f[16];
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (e + j < nl) f[j] = __ldg(zc + (size_t)link_J(lb[e + j]) * nb);
+          for (int j = 0; j < 16; ++j)
+            if (e + j < nl) f[j] = __ldg(zc + lJ[e + j]);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
+          for (int j = 0; j < 16; ++j)
             if (e + j < nl) {
-              const uint32_t v = lb[e + j];
-              mine[opnd_off(r, link_pair(v), Kp)] += link_neg(v) ? -f[j] : f[j];
+              const uint32_t q = lQ[e + j];
+              mine[rbase + (int)(q & ~kSignBit)] = (q & kSignBit) ? -f[j] : f[j];
             }
         }
       }

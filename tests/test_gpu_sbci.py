@@ -163,9 +163,10 @@ def test_start_noise_matches_oracle(key, k, kw):
 @pytest.mark.parametrize("key,c0seed", [(("chain", 6, 1.0), 0), (("chain", 10, 1.2), 0)])
 def test_energy_conservation_diagnostic_matches_oracle(key, c0seed):
     """Section S4 (Eq. S136) at run time: the device controller's per-step
-    (2/c) Delta T equals the oracle's on the same FP64 trajectory (1e-8 of
-    its scale, while the two runs still agree step by step: the first 40
-    records), and the report's geometric-mean ratio |Delta E / ((2/c) Delta T)|
+    (2/c) Delta T equals the oracle's in magnitude on the same FP64 trajectory
+    (1e-8 of its scale, while the two runs still agree step by step: the
+    first 40 records; its sign follows that of c, which the eigenvector sign
+    decides), and the report's geometric-mean ratio |Delta E / ((2/c) Delta T)|
     is the oracle's own, computed the same way from its trace."""
     sbci = require_lib()
     I = make_integrals(key)
@@ -182,7 +183,9 @@ def test_energy_conservation_diagnostic_matches_oracle(key, c0seed):
         assert abs(g.energy - o.energy) < 1e-10  # still the same trajectory
         assert np.isfinite(g.s136) == np.isfinite(o.s136)
         if np.isfinite(o.s136):
-            assert abs(g.s136 - o.s136) <= 1e-8 * max(abs(o.s136), 1e-6), (g.s136, o.s136)
+            # c (and with it 2/c) takes the sign of the Ritz vector, which either
+            # eigen-solver may flip (reading C-11): compare magnitudes
+            assert abs(abs(g.s136) - abs(o.s136)) <= 1e-8 * max(abs(o.s136), 1e-6), (g.s136, o.s136)
             checked += 1
     assert checked >= 5
     # the report's summary against the same summary of the oracle's trace
