@@ -135,6 +135,7 @@ struct sbci_ctx {
   int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
   int fc_grid = 0;  // CTAs of the column-fused sector kernel (0: unsupported shape or turned off)
+  uint16_t *d_fc_link_a = nullptr;  // its 16-bit alpha links (J | pair << 8 | sign << 15)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
   size_t tmp_elems = 0;
   std::vector<double> W_host;
@@ -1982,6 +1983,7 @@ bool sbci::ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream)
   a->W = c->d_W;
   a->Wf = c->d_Wf;
   a->Wtc = c->d_Wtc;
+  a->fc_link_a = c->d_fc_link_a;
   a->na = c->Na;
   a->nb = c->Nb;
   a->nlink_a = c->sa.nlink;
@@ -2031,7 +2033,7 @@ void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wbf, c->d_Wos, c->d_fexp, c->d_cf,
+  void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wbf, c->d_fc_link_a, c->d_Wos, c->d_fexp, c->d_cf,
                   c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
                   c->d_tmp_out, c->d_lrUt64, c->d_lrUL64};
   for (void *p : ptrs)
@@ -2207,6 +2209,14 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   {  // SBCI_FUSED=0 keeps the tile kernel + scatter for singlet-sector TF32x3 steps
     const char *e = std::getenv("SBCI_FUSED");
     c->fc_grid = (e && e[0] == '0') ? 0 : fc_grid(c->npair, c->Na, c->Nb, c->sb.nlink, c->nsm);
+    if (c->fc_grid > 0) {  // (fc_dims holds J <= 255 and pair <= 127 for these spaces)
+      std::vector<uint16_t> w(c->sa.links.size());
+      for (size_t i = 0; i < w.size(); ++i) {
+        const uint32_t v = c->sa.links[i];
+        w[i] = (uint16_t)((uint32_t)link_J(v) | (uint32_t)link_pair(v) << 8 | (link_neg(v) ? 0x8000u : 0u));
+      }
+      TRY(up((void **)&c->d_fc_link_a, w.data(), w.size() * sizeof(uint16_t)));
+    }
   }
   {
     int Kp, Np;

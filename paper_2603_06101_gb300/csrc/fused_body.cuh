@@ -36,14 +36,15 @@ namespace sbci {
 constexpr int kFcThreads = 256;  // two threads per string of a 128-string tile
 constexpr int kFcMaxStr = 256;   // strings per spin (two tiles of the MMA's M = 128)
 constexpr int kFcMaxLink = 64;   // link words of string b staged in shared memory
+constexpr int kFcLinkMax = 8192; // 16-bit alpha link words of a space held in shared memory (na * nlink_a)
 
 // Shared-memory buffers of one column CTA.
 struct FcSmem {
   float *A, *Alo;       // operand D (alpha part / hi, beta part / lo); G column after the MMAs
   uint32_t *Bhi, *Blo;  // W split into TF32 hi / lo (operand B)
   float *zrow;          // row b of z, kFcMaxStr floats
-  uint32_t *lb;         // links of string b, decoded: [kFcMaxLink] row offsets J * nb, then
-                        // [kFcMaxLink] operand column offsets | sign << 31
+  uint32_t *lb;         // links of string b, decoded: J * nb | operand column offset << 16 | sign << 31
+  uint16_t *la;         // the space's alpha links, J | pair << 8 | sign << 15 (kFcLinkMax)
   uint32_t sA, sAlo, sBhi, sBlo, sbar;
 };
 
@@ -56,7 +57,7 @@ __host__ __device__ constexpr int fc_acc_stride(int Np) {
 
 // Dynamic shared memory of a column CTA with Kp x Np operands.
 __host__ __device__ constexpr size_t fc_smem_bytes(int Kp, int Np) {
-  return (size_t)(2 * kTcM * Kp + 2 * Np * Kp + kFcMaxStr + 2 * kFcMaxLink) * 4 + 16;
+  return (size_t)(2 * kTcM * Kp + 2 * Np * Kp + kFcMaxStr + kFcMaxLink) * 4 + (size_t)kFcLinkMax * 2 + 16;
 }
 
 __device__ __forceinline__ FcSmem fc_carve(unsigned char *smem, int Kp, int Np) {
@@ -71,12 +72,29 @@ __device__ __forceinline__ FcSmem fc_carve(unsigned char *smem, int Kp, int Np) 
   sm.sAlo = smem_u32(sm.Alo);
   sm.sBhi = smem_u32(sm.Bhi);
   sm.sBlo = smem_u32(sm.Blo);
-  sm.sbar = smem_u32(sm.lb + 2 * kFcMaxLink);  // 8-byte aligned: every buffer above is a multiple of 8 bytes
+  sm.la = reinterpret_cast<uint16_t *>(sm.lb + kFcMaxLink);
+  sm.sbar = smem_u32(sm.la + kFcLinkMax);  // 8-byte aligned: every buffer above is a multiple of 8 bytes
   return sm;
 }
 
 // The TMEM address slot, after the mbarrier.
-__device__ __forceinline__ uint32_t *fc_tmem_slot(const FcSmem &sm) { return sm.lb + 2 * kFcMaxLink + 2; }
+__device__ __forceinline__ uint32_t *fc_tmem_slot(const FcSmem &sm) {
+  return reinterpret_cast<uint32_t *>(sm.la + kFcLinkMax) + 2;
+}
+
+// The space's alpha links into shared memory (16-byte copies; when a CTA
+// starts a solve).  Ends with a barrier.
+__device__ __forceinline__ void fc_load_links(const SigmaArgs &a, const FcSmem &sm) {
+  const int nw = a.na * a.nlink_a;  // 16-bit words, <= kFcLinkMax
+  const uint16_t *src = a.fc_link_a;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) sm.la[i] = __ldg(src + i);
+  __syncthreads();
+}
+
+// x with the sign flipped where bit 15 of the link word w is set.
+__device__ __forceinline__ float fc_sign(float x, uint32_t w) {
+  return __uint_as_float(__float_as_uint(x) ^ ((w & 0x8000u) << 16));
+}
 
 // Offset of column q within a row of the K-major no-swizzle TF32 operand (the
 // row's own part is (r / 8) * Kp * 8 + (r % 8) * 4, see opnd_off).
@@ -123,10 +141,9 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   // 0. row b of z (z[b][j] = z[j][b]) and the link words of b; the previous
   //    column's readers of these buffers finished at its last barrier
   for (int j = tid; j < na; j += blockDim.x) sm.zrow[j] = __ldg(zf + (size_t)b * nb + j);
-  for (int e = tid; e < a.nlink_b; e += blockDim.x) {
+  for (int e = tid; e < a.nlink_b; e += blockDim.x) {  // J * nb < 2^16 for nb <= 256
     const uint32_t v = __ldg(a.link_b + (size_t)b * a.nlink_b + e);
-    sm.lb[e] = (uint32_t)link_J(v) * (uint32_t)nb;
-    sm.lb[kFcMaxLink + e] = (uint32_t)fc_qoff(link_pair(v)) | (v & kSignBit);
+    sm.lb[e] = (uint32_t)link_J(v) * (uint32_t)nb | (uint32_t)fc_qoff(link_pair(v)) << 16 | (v & kSignBit);
   }
   __syncthreads();
   const int r = tid & (kTcM - 1);
@@ -146,27 +163,29 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
     // each pair receives at most one term per spin (a string's links have
     // distinct pairs), so the gathers store into the zeroed rows
     if (ia < na) {
-      if (half == 0) {
-        const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+      if (half == 0) {  // all operands in shared memory
+        const uint16_t *lr = sm.la + ia * a.nlink_a;
         const float *zr = sm.zrow;
-        for_links_pipelined<16, float>(
-            la, a.nlink_a, 1, [&](uint32_t v) { return zr[link_J(v)]; },
-            [&](uint32_t v, float f) { mine[rbase + fc_qoff(link_pair(v))] = link_neg(v) ? -f : f; });
-      } else {
+        const int nl = a.nlink_a;
+#pragma unroll 4
+        for (int e = 0; e < nl; ++e) {
+          const uint32_t w = lr[e];
+          mine[rbase + fc_qoff((int)((w >> 8) & 0x7Fu))] = fc_sign(zr[w & 0xFFu], w);
+        }
+      } else {  // z rows of the column's beta links: coalesced loads, 8 in flight
         const float *zc = zf + ia;
-        const uint32_t *lJ = sm.lb, *lQ = sm.lb + kFcMaxLink;
+        const uint32_t *lw = sm.lb;
         const int nl = a.nlink_b;
-        // decoded links from shared memory; the z loads of 16 links are in flight together
-        for (int e = 0; e < nl; e += 16) {
-          float f[16];
+        for (int e = 0; e < nl; e += 8) {
+          float f[8];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (e + j < nl) f[j] = __ldg(zc + lJ[e + j]);
+          for (int j = 0; j < 8; ++j)
+            if (e + j < nl) f[j] = __ldg(zc + (lw[e + j] & 0xFFFFu));
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
+          for (int j = 0; j < 8; ++j)
             if (e + j < nl) {
-              const uint32_t q = lQ[e + j];
-              mine[rbase + (int)(q & ~kSignBit)] = (q & kSignBit) ? -f[j] : f[j];
+              const uint32_t w = lw[e + j];
+              mine[rbase + (int)((w >> 16) & 0x7FFFu)] = __uint_as_float(__float_as_uint(f[j]) ^ (w & kSignBit));
             }
         }
       }
@@ -239,11 +258,13 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   // 4. alpha-only scatter of the column: A[Ia, b] -> A^T[b][Ia]
   float *At = reinterpret_cast<float *>(a.symA) + (size_t)b * nb;
   for (int ia = tid; ia < na; ia += blockDim.x) {
+    const uint16_t *lr = sm.la + ia * a.nlink_a;
     float acc = 0.f;
-    for_links<8, float>(
-        a.link_a + (size_t)ia * a.nlink_a, a.nlink_a, 1,
-        [&](uint32_t v) { return Gs[link_pair(v) * kFcMaxStr + link_J(v)]; },
-        [&](uint32_t v, float g) { acc += link_neg(v) ? -g : g; });
+#pragma unroll 4
+    for (int e = 0; e < a.nlink_a; ++e) {  // in link order, as the scatter kernel sums
+      const uint32_t w = lr[e];
+      acc += fc_sign(Gs[((w >> 8) & 0x7Fu) * kFcMaxStr + (w & 0xFFu)], w);
+    }
     At[ia] = acc;
   }
   __syncthreads();  // G readers are done before the next column's writers

@@ -359,12 +359,13 @@ __global__ void __launch_bounds__(kFcThreads, 2)
   const FcSmem sm = fc_carve(smem, Kp, Np);
   if (!a.ctl || a.ctl->halt) return;  // uniform: before any TMEM allocation or barrier
   const float *zf = a.ctl->zf;
-  if (!zf || !a.symA) {  // the column kernel needs the FP32 z and the A^T buffer: refuse
+  if (!zf || !a.symA || !a.fc_link_a) {  // the column kernel needs these: refuse
     if (threadIdx.x == 0) atomicOr(status, 4);
     return;
   }
   if ((int)blockIdx.x >= a.nb) return;
   fc_begin(sm, tmem_cols);
+  fc_load_links(a, sm);
   fc_load_B(a, Kp, Np, sm);  // (ends with a barrier)
   const uint32_t tmem = *fc_tmem_slot(sm);
   uint32_t phase = 0;
@@ -377,8 +378,8 @@ __global__ void __launch_bounds__(kFcThreads, 2)
 bool fc_dims(int npair, int na, int nb, int nlink_b, int *Kp, int *Np, uint32_t *cols, size_t *smem) {
   uint32_t tc_cols;
   size_t tc_smem;
-  if (na != nb || na < 1 || na > kFcMaxStr || nlink_b > kFcMaxLink ||
-      !tc_dims(npair, Kp, Np, &tc_cols, &tc_smem))
+  if (na != nb || na < 1 || na > kFcMaxStr || nlink_b > kFcMaxLink || npair > 128 ||
+      (long long)na * nlink_b > kFcLinkMax || !tc_dims(npair, Kp, Np, &tc_cols, &tc_smem))
     return false;
   const uint32_t c = 2u * (uint32_t)fc_acc_stride(*Np);
   *cols = c;
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(kFcThreads, 2)
   for (int item = first; item < last && ok; ++item) {
     const int j = find_job(s_off, nj, item);
     if (s_halt[j]) continue;  // block-uniform
-    if (!s_zf[j] || !bt->job[j].sig.symA) {  // a fused job always has both; refuse otherwise
+    if (!s_zf[j] || !bt->job[j].sig.symA || !bt->job[j].sig.fc_link_a) {  // a fused job has all three
       if (tid == 0) atomicOr(status, 4);
       continue;
     }
@@ -609,6 +610,7 @@ __global__ void __launch_bounds__(kFcThreads, 2)
       Kp = bt->job[j].Kp;
       Np = bt->job[j].Np;
       __syncthreads();
+      fc_load_links(s_args, sm);
       fc_load_B(s_args, Kp, Np, sm);  // (ends with a barrier)
       cur = j;
     }

@@ -150,6 +150,8 @@ struct SigmaArgs {
   const float *Wf;       // FP32 copy (same layout), SBCI_FP32 mode
   const uint32_t *Wtc;   // TF32 hi then lo of W in the tensor-core operand layout
                          // ([2][Np*Kp], see tc_body.cuh), or nullptr
+  const uint16_t *fc_link_a;  // alpha links for the column-fused kernel, [na][nlink_a] of
+                              // J | pair << 8 | (sign < 0) << 15, or nullptr
   int na, nb, nlink_a, nlink_b, npair, npair_pad;
   long long ndet;
   // epilogue dots of sigma against up to three vectors (nullptr = unused)
