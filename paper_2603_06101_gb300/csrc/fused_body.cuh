@@ -150,19 +150,30 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   const int half = tid >> 7;  // 0: alpha links of row r, 1: beta links of b at column r
   const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
   const int rbase = (r >> 3) * (Kp * 8) + (r & 7) * 4;  // row r's part of an operand offset
+  constexpr int kPre = 16;  // beta-link values loaded before the previous tile's MMAs are waited for
   for (int t = 0; t < ntile; ++t) {
+    const int ia = t * kTcM + r;
+    const bool row_ok = ia < na;
+    const float *zc = zf + ia;
+    const uint32_t *lw = sm.lb;
+    const int nlb = a.nlink_b;
+    float pre[kPre];
+    if (half == 1 && row_ok) {  // their z loads overlap the wait below
+#pragma unroll
+      for (int j = 0; j < kPre; ++j)
+        if (j < nlb) pre[j] = __ldg(zc + (lw[j] & 0xFFFFu));
+    }
     if (t > 0) {  // the previous tile's MMAs read A / Alo: wait before overwriting them
       *pending = 1;
       if (!fc_wait(sm, phase)) return false;
       *pending = 0;
     }
-    const int ia = t * kTcM + r;
     float *mine = half ? sm.Alo : sm.A;
     for (int q = 0; q < Kp; q += 4)
       *reinterpret_cast<float4 *>(mine + opnd_off(r, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
     // each pair receives at most one term per spin (a string's links have
     // distinct pairs), so the gathers store into the zeroed rows
-    if (ia < na) {
+    if (row_ok) {
       if (half == 0) {  // all operands in shared memory
         const uint16_t *lr = sm.la + ia * a.nlink_a;
         const float *zr = sm.zrow;
@@ -172,18 +183,21 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
           const uint32_t w = lr[e];
           mine[rbase + fc_qoff((int)((w >> 8) & 0x7Fu))] = fc_sign(zr[w & 0xFFu], w);
         }
-      } else {  // z rows of the column's beta links: coalesced loads, 8 in flight
-        const float *zc = zf + ia;
-        const uint32_t *lw = sm.lb;
-        const int nl = a.nlink_b;
-        for (int e = 0; e < nl; e += 8) {
+      } else {  // z rows of the column's beta links: coalesced loads
+#pragma unroll
+        for (int j = 0; j < kPre; ++j)
+          if (j < nlb) {
+            const uint32_t w = lw[j];
+            mine[rbase + (int)((w >> 16) & 0x7FFFu)] = __uint_as_float(__float_as_uint(pre[j]) ^ (w & kSignBit));
+          }
+        for (int e = kPre; e < nlb; e += 8) {
           float f[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (e + j < nl) f[j] = __ldg(zc + (lw[e + j] & 0xFFFFu));
+            if (e + j < nlb) f[j] = __ldg(zc + (lw[e + j] & 0xFFFFu));
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (e + j < nl) {
+            if (e + j < nlb) {
               const uint32_t w = lw[e + j];
               mine[rbase + (int)((w >> 16) & 0x7FFFu)] = __uint_as_float(__float_as_uint(f[j]) ^ (w & kSignBit));
             }

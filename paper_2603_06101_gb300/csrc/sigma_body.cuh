@@ -76,7 +76,9 @@ __device__ __forceinline__ bool scatter_body(const SigmaArgs &a, int vb, int nvb
 // transpose of the alpha part A, so sigma = A + A^T.  Work unit: a pair of
 // 32 x 32 tiles (ti, tj), ti >= tj, of A, both read coalesced into shared
 // memory; it writes the two sigma tiles (one on the diagonal), takes the dots
-// of sigma against x, y and z, and the last block runs the subspace solve.
+// of sigma against x, y and z over tile (ti, tj) (weight 2 off the diagonal:
+// all four are symmetric matrices), and the last block runs the subspace
+// solve.
 constexpr int kSfT = 32;
 
 
@@ -94,6 +96,7 @@ __device__ __forceinline__ bool symfin_body(const SigmaArgs &a, int vb, int nvb)
   for (int u = vb; u < units; u += nvb) {
     int ti, tj;
     tri_unit(u, &ti, &tj);
+    double ud[3] = {0.0, 0.0, 0.0};  // this unit's dots over tile (ti, tj)
     __syncthreads();  // the previous unit's readers are done
     for (int k = tid; k < kSfT * kSfT; k += blockDim.x) {
       const int r = k / kSfT, c = k - r * kSfT;
@@ -111,18 +114,17 @@ __device__ __forceinline__ bool symfin_body(const SigmaArgs &a, int vb, int nvb)
         const double sv = (double)(tA[r][c] + tB[c][r]);
         sig[I] = sv;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) dots[j] = fma(du[j][I], sv, dots[j]);
+        for (int j = 0; j < 3; ++j) ud[j] = fma(du[j][I], sv, ud[j]);
       }
-      // tile (tj, ti), off the diagonal
+      // tile (tj, ti), off the diagonal: the transpose of tile (ti, tj), since
+      // sigma, x, y and z are symmetric matrices (the same values; the dots of
+      // the pair count tile (ti, tj) twice)
       const int i2 = tj * kSfT + r, j2 = ti * kSfT + c;
-      if (ti != tj && i2 < n && j2 < n) {
-        const size_t I = (size_t)i2 * n + j2;
-        const double sv = (double)(tB[r][c] + tA[c][r]);
-        sig[I] = sv;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dots[j] = fma(du[j][I], sv, dots[j]);
-      }
+      if (ti != tj && i2 < n && j2 < n) sig[(size_t)i2 * n + j2] = (double)(tB[r][c] + tA[c][r]);
     }
+    const double wgt = (ti != tj) ? 2.0 : 1.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dots[j] = fma(wgt, ud[j], dots[j]);
   }
   block_partials<3, kScTile>(dots, a.dot_slot, a.partials, nvb, vb);
   if (!last_block(a.counter, nvb)) return false;
