@@ -12,10 +12,12 @@ namespace sbci {
 // Block partials of NV values per thread -> partials[slot * grid + block]
 // (slots[j] < 0: value j unused).  NT = threads per block; block is the
 // (virtual) block index within its grid of size grid; buf: shared memory of
-// [NT / 32][NV][33] doubles.
+// [NT / 32][NV][33] doubles; scale (optional): a factor per value applied to
+// the block's sum.
 template <int NV, int NT>
 __device__ __forceinline__ void block_partials_in(const double (&v)[NV], const int (&slots)[NV],
-                                                  double *partials, int grid, int block, double (*buf)[NV][33]) {
+                                                  double *partials, int grid, int block, double (*buf)[NV][33],
+                                                  const double *scale = nullptr) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();  // a persistent block may come back with the buffer still in use
 #pragma unroll
@@ -31,6 +33,7 @@ __device__ __forceinline__ void block_partials_in(const double (&v)[NV], const i
     const int j = threadIdx.x;
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += buf[w][j][32];
+    if (scale) s *= scale[j];  // a block sum's weight (exact for powers of two)
     if (slots[j] >= 0) partials[(size_t)slots[j] * grid + block] = s;
   }
 }

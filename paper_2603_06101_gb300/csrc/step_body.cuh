@@ -37,6 +37,14 @@ __device__ __forceinline__ double recip(double d) {
   return r;
 }
 
+// 1/d to ~2^-46 relative (one Newton step): the preconditioner values of the
+// sector sweep, where an error of 1e-14 in a component of z moves the step's
+// coefficients far less than the FP64 rounding of the dot products does.
+__device__ __forceinline__ double recip46(double d) {
+  const double r = (double)__frcp_rn((float)d);
+  return r * fma(-d, r, 2.0);
+}
+
 // Symplectic-Euler update sweep (Eqs. 10-11, S56-S59), residual (Eq. S60) and
 // preconditioner (Eqs. 6-7); the last block runs the convergence / restart
 // test of the controller (Eq. S61, S62).
@@ -126,7 +134,8 @@ __device__ __forceinline__ bool update_body(const StepArgs &a, int vb, int nvb, 
 // tiles, (ti, tj) read coalesced and its transpose (tj, ti) written through
 // shared memory (on a diagonal tile the elements with row >= column).  Per
 // pair: the recurrences and the residual once; the preconditioner at both
-// diagonal elements D_ij and D_ji, and the symmetrised w = (w_ij + w_ji) / 2
+// diagonal elements D_ij and D_ji (reciprocals to 2^-46), and the symmetrised
+// w = (w_ij + w_ji) / 2
 // of reading R10 (formerly the projection's first step); the dot products
 // weighted by the pair's two elements.  For the ground state (no stored
 // state to project against) it writes z itself, with its FP32 copy and the
@@ -190,8 +199,8 @@ __device__ __forceinline__ bool update_body_sym(const StepArgs &a, int vb, int n
       const double X = fma(u.b, Y, unit ? a.X[I] : u.sx * a.X[I]);
       const double zp = fma(-u.E, x, X) * u.kinv;
       const double dA = a.diag[I], dB = sm.dT[c][r];
-      const double pa = pinv ? pinv[I] : recip(guarded(dA - u.Epre, guard));
-      const double pb = on_diag ? pa : (pinv ? sm.pT[c][r] : recip(guarded(dB - u.Epre, guard)));
+      const double pa = pinv ? pinv[I] : recip46(guarded(dA - u.Epre, guard));
+      const double pb = on_diag ? pa : (pinv ? sm.pT[c][r] : recip46(guarded(dB - u.Epre, guard)));
       const double w = 0.5 * (zp * pa + zp * pb);
       a.y[I] = y;
       a.Y[I] = Y;
@@ -245,8 +254,11 @@ __device__ __forceinline__ bool update_body_sym(const StepArgs &a, int vb, int n
       if (zf) zf[I2] = sm.f[r][c];
     }
   }
+  // the half-weighted sums count twice (the y^T D y sum is in full weight):
+  // doubled once per block, in the reduction's last stage
+  double wgt[NV];
 #pragma unroll
-  for (int j = 0; j < NV - 1; ++j) acc[j] = 2.0 * acc[j];  // (the y^T D y sum is in full weight)
+  for (int j = 0; j < NV; ++j) wgt[j] = (j < NV - 1) ? 2.0 : 1.0;
   __syncthreads();  // the tile buffers become the reduction's
   int slots[NV];
 #pragma unroll
@@ -257,7 +269,7 @@ __device__ __forceinline__ bool update_body_sym(const StepArgs &a, int vb, int n
   for (int j = 0; j < kMaxStates; ++j) slots[10 + j] = (j < nxc) ? S_XCW0 + j : -1;
   slots[NV - 1] = S_YDY;
   block_partials_in<NV, kStepThreads>(acc, slots, a.partials, nvb, vb,
-                                      reinterpret_cast<double (*)[NV][33]>(smem));
+                                      reinterpret_cast<double (*)[NV][33]>(smem), wgt);
   if (!last_block(a.counter + 0, nvb)) return false;
   int act[NV];
   int na = 0;

@@ -90,3 +90,22 @@ def test_sigma_bf16x3_n16_sampled_rows(ctx16):
     assert np.abs(got - ref).max() < 2e-4 * scale
     del c, s
     torch.cuda.empty_cache()
+
+
+def test_sigma_fp64_n16_sampled_rows(ctx16):
+    """The FP64 sigma of the largest space (its [npair][Ndet] FP64 scratch is
+    180 GB, resident in HBM; the contraction in the density-fitted form of
+    reading L1): sampled rows against the oracle's Slater-Condon rows to
+    1e-12 of max|sigma|, the FP64 target of the sigma tests."""
+    import torch
+
+    sbci, I, ctx = ctx16
+    c = torch.from_numpy(inputs.random_vector(12870, 12870, 163)).cuda()
+    s = ctx.sigma(c, prec=sbci.SBCI_FP64)
+    rows = np.random.default_rng(19).choice(ctx.ndet, 8, replace=False)
+    ref = sc.sampled_sigma_rows(I.h1, I.eri, 8, 8, c.cpu().numpy(), rows)
+    got = s.reshape(-1)[torch.from_numpy(rows).cuda()].cpu().numpy()
+    scale = float(s.abs().max())
+    assert np.abs(got - ref).max() < 1e-12 * scale
+    del c, s
+    torch.cuda.empty_cache()
