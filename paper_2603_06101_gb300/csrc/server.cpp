@@ -28,7 +28,6 @@
 #include <map>
 #include <mutex>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/sbci.h"
@@ -38,12 +37,6 @@
 using namespace sbci;
 
 namespace {
-
-// SBCI_HOST_THREADS=0 keeps the halted solves' host work on the calling thread.
-bool host_threads() {
-  const char *e = std::getenv("SBCI_HOST_THREADS");
-  return !(e && e[0] == '0');
-}
 
 double now_s() {
   using namespace std::chrono;
@@ -596,46 +589,18 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       set_error("sbci_solve_batch: batch round failed");
       return SBCI_ERR_CUDA;
     }
-    // the halted solves' host work (FP64 re-syncs, verification, next state):
-    // each solve on its own stream from its own host thread, so that their
-    // synchronisations and kernels overlap (every context owns its stream and
-    // buffers; the engine's state is not touched)
     sbci_status host_st = SBCI_OK;
-    {
-      const size_t np = pending.size();
-      std::vector<sbci_status> st_run(np, SBCI_OK), st_fin(np, SBCI_OK);
-      std::vector<std::string> msg(np);
-      auto work = [&](size_t q) {
-        const int i = pending[q];
-        cudaSetDevice(dev);
-        st_run[q] = solve_round_finish(ctx[i], &done[i], false);
-        if (st_run[q] != SBCI_OK && st_run[q] != SBCI_ERR_NOT_CONVERGED) {
-          msg[q] = sbci_last_error();
-          return;
-        }
-        if (done[i]) {
-          st_fin[q] = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
-          if (st_fin[q] != SBCI_OK) msg[q] = sbci_last_error();
-        }
-      };
-      if (np >= 2 && host_threads()) {
-        std::vector<std::thread> th;
-        th.reserve(np);
-        for (size_t q = 0; q < np; ++q) th.emplace_back(work, q);
-        for (auto &t : th) t.join();
-      } else {
-        for (size_t q = 0; q < np; ++q) work(q);
+    for (int i : pending) {
+      is_pending[i] = 0;
+      if (host_st != SBCI_OK) continue;
+      const sbci_status st = solve_round_finish(ctx[i], &done[i], false);
+      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
+        host_st = st;
+        continue;
       }
-      for (size_t q = 0; q < np; ++q) {
-        is_pending[pending[q]] = 0;
-        if (host_st == SBCI_OK && st_run[q] != SBCI_OK && st_run[q] != SBCI_ERR_NOT_CONVERGED) {
-          host_st = st_run[q];
-          set_error(msg[q]);
-        }
-        if (st_fin[q] != SBCI_OK) {
-          worst = st_fin[q];
-          set_error(msg[q]);
-        }
+      if (done[i]) {
+        const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
+        if (fs != SBCI_OK) worst = fs;
       }
     }
     pending.clear();
