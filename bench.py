@@ -1,16 +1,24 @@
-"""Benchmark of the GB300 SBCI library on the H10 singlet workload.
+"""Benchmark of the GB300 SBCI library.
 
-Workload: linear H10 chain, STO-3G, Loewdin basis, 1.2 A spacing, 10 orbitals,
-5 alpha / 5 beta electrons, 252 x 252 = 63,504 determinants; the ground state
-and 3 excited states in the c = c^T (singlet) sector; SBCI1 with the paper's
-thresholds.  One step = one complete solve of the 4 states.
+Headline workload: linear H10 chain, STO-3G, Loewdin basis, 1.2 A spacing, 10
+orbitals, 5 alpha / 5 beta electrons, 252 x 252 = 63,504 determinants; the
+ground state and 3 excited states in the c = c^T (singlet) sector; SBCI1 with
+the paper's thresholds, TF32x3 sigma with FP64 refinement.  One step = 16
+such solves through the batched engine (CUDA-event timing on the library
+stream, L2 flushed between steps).
 
-Default arm: the CUDA library (device-resident integrals, CUDA-event timing on
-the library stream, L2 flushed between steps), plus an end-to-end number
-through the C ABI with host buffers, a roofline entry for the dominant kernel
-and the CPU oracle timed on the host cores.  ``--impl reference`` times the
-oracle alone (bounded samples).  Under torchrun every rank runs independent
-solves (replicas); rank 0 prints one JSON line.
+Legs of the default line (rank 0, one GPU): an end-to-end number through the
+C ABI with host buffers; per-step latency percentiles; the same workload one
+solve per launch, mixed and plain FP64; the roofline of the dominant kernel
+(16 B per determinant per sigma, 2 npair^2 flops) and of every step kernel;
+the per-state energy error against the oracle's exact sector energies
+(tests/golden); a short serving stream (H6-H12, batched mixed precision
+against FP64 one solve per launch, p50/p99); random density-fitted n = 14
+(TF32x3, BF16x3 and FP64 sigma with rooflines, a 2-state mixed solve) and
+n = 16 (BF16x3 sigma); the CPU oracle timed on the host cores.
+``--impl reference`` times the oracle alone (bounded samples).  Under
+torchrun every rank runs independent solves (replicas); rank 0 prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -41,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu", action="store_true",
@@ -56,6 +64,7 @@ def parse():
                     help="requests of the short serving stream in the default bench line")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-n14", action="store_true")
+    ap.add_argument("--no-n16", action="store_true")
     ap.add_argument("--batch", type=int, default=16,
                     help="H10 solves per step, solved together by the batched persistent kernels "
                          "(1: one solve per step through its own graph loop)")
@@ -265,7 +274,7 @@ def run_reference(args, rank, world):
 
 TF32_OF_BF16 = 0.5  # nominal dense TF32 / BF16 tensor rate (1.1 vs 2.25 PFLOP/s)
 SIGMA_FAMILIES = ("gather_contract_tc", "gather_contract_os", "gather_contract", "gather_contract_lr",
-                  "scatter", "symfinish", "fused_column")
+                  "gather_contract_bf16", "scatter", "symfinish", "fused_column")
 
 
 def family_of(name: str) -> str:
@@ -294,10 +303,11 @@ def roofline(name, launches, ms, dets_per_launch, npair, prec, pk, pk_kind, sm_m
                                    f"{dets_per_launch} determinants"}
         hbm["frac"] = hbm["achieved"] / hbm_peak
         other = None
-        if fam in ("gather_contract_tc", "fused_column", "gather_contract_os"):
-            tpeak = pk.get("bf16_tflops", 1900.0) * (TF32_OF_BF16 if prec != "fp64" else 1.0)
-            note = ("TF32: measured bf16 x nominal TF32/BF16 ratio 0.5" if prec != "fp64"
-                    else "BF16 slices of the exact FP64 contraction: measured bf16")
+        if fam in ("gather_contract_tc", "fused_column", "gather_contract_os", "gather_contract_bf16"):
+            tf32 = fam in ("gather_contract_tc", "fused_column")
+            tpeak = pk.get("bf16_tflops", 1900.0) * (TF32_OF_BF16 if tf32 else 1.0)
+            note = ("TF32: measured bf16 x nominal TF32/BF16 ratio 0.5" if tf32
+                    else "BF16 operands (BF16x3 split, or the exact slices of the FP64 contraction): measured bf16")
             other = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                      "peak_kind": f"{pk_kind} {note}", "algorithmic_per_launch": flops,
                      "algorithmic_note": "2 npair^2 flops per determinant (the split precisions execute more)"}
@@ -439,7 +449,8 @@ def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
     out = torch.empty_like(c)
     res = {"workload": "random density-fitted integrals n=14, 7a/7b, seed 14", "ndet": ctx.ndet,
            "npair": ctx.npair}
-    for tag, prec, pname in (("tf32x3", sbci.SBCI_TF32X3, "tf32x3"), ("fp64", sbci.SBCI_FP64, "fp64")):
+    for tag, prec, pname in (("tf32x3", sbci.SBCI_TF32X3, "tf32x3"), ("bf16x3", sbci.SBCI_BF16X3, "bf16x3"),
+                             ("fp64", sbci.SBCI_FP64, "fp64")):
         ctx.sigma(c, out, prec=prec)  # warm-up (scratch allocation)
         torch.cuda.synchronize()
         ctx.profile(True)
@@ -471,6 +482,42 @@ def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
     return res
 
 
+def random_df_n16_leg(pk, pk_kind, sm_mhz, reps=2):
+    """The largest space: random density-fitted integrals, n = 16, 8 alpha / 8
+    beta (seed 16; 165,636,900 determinants, 1.3 GB per FP64 vector): the
+    BF16x3 sigma on the tensor cores, timed per kernel with CUDA events on the
+    library stream, with its roofline (the TF32 operands do not fit shared
+    memory at this size)."""
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    I = inputs.random_df(16, 16)
+    ctx = sbci.Context.from_integrals(I)
+    c = torch.from_numpy(inputs.random_vector(ctx.na, ctx.nb, 1)).cuda()
+    out = torch.empty_like(c)
+    ctx.sigma(c, out, prec=sbci.SBCI_BF16X3)  # warm-up (scratch allocation)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.sigma(c, out, prec=sbci.SBCI_BF16X3)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = {k: v for k, v in ctx.profile_read().items() if v[0] and k.startswith("sigma_")}
+    ctx.profile(False)
+    dom = max(st.items(), key=lambda kv: kv[1][1])
+    res = {"workload": "random density-fitted integrals n=16, 8a/8b, seed 16", "ndet": ctx.ndet, "npair": ctx.npair,
+           "sigma_bf16x3": {"ms_per_sigma": sum(v[1] for v in st.values()) / reps, "wall_ms_per_sigma": 1e3 * wall / reps,
+                            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in st.items()},
+                            "roofline": roofline(dom[0], dom[1][0], dom[1][1], ctx.ndet, ctx.npair, "bf16x3", pk,
+                                                 pk_kind, sm_mhz)}}
+    del c, out
+    ctx.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
 
@@ -482,12 +529,13 @@ def run_gb300(args, rank, world, local_rank):
         import torch.distributed as dist
 
     I = workload()
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3,
+            "bf16x3": sbci.SBCI_BF16X3}[args.prec]
     stream = torch.cuda.Stream()
     ctx = sbci.Context.from_integrals(I, stream=stream.cuda_stream)
     p = sbci.params(sector=1, prec=prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    B = max(1, args.batch) if args.prec == "tf32x3" else 1
+    B = max(1, args.batch) if args.prec == "tf32x3" else 1  # (the batch engine takes TF32x3 solves)
     batch_ctx = [ctx] + [sbci.Context.from_integrals(I, stream=stream.cuda_stream) for _ in range(B - 1)]
     ref_E = golden_energies()
 
@@ -628,11 +676,14 @@ def run_gb300(args, rank, world, local_rank):
     # ---------------- further workloads of the measurement plan (rank 0, N = 1)
     serving = None
     n14 = None
+    n16 = None
     if rank == 0 and world == 1:
         if not args.no_serving:
             serving = serving_leg(args.serving_requests, args.slots)
         if not args.no_n14:
             n14 = random_df_leg(pk, pk_kind, sm_mhz)
+        if not args.no_n16:
+            n16 = random_df_n16_leg(pk, pk_kind, sm_mhz)
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
     oracle_same_run = None
@@ -646,7 +697,7 @@ def run_gb300(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64"}[args.prec],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "norb": 10, "ndet": ndet, "states": NSTATES,
                        "solves_per_step": B, "engine": "batched persistent kernels, one graph loop" if B > 1
@@ -664,7 +715,7 @@ def run_gb300(args, rank, world, local_rank):
             "energy_err_vs_oracle_sbci1_same_run": oracle_same_run,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "single_solve": single, "fp64_one_solve_per_launch": fp64_arm,
-            "serving": serving, "random_df_n14": n14,
+            "serving": serving, "random_df_n14": n14, "random_df_n16": n16,
             "kernel_rooflines": kernel_rooflines,
             "autotuner": sbci.batch_classes() if B > 1 else None,
             "launches_timed": {k: v[0] for k, v in stats.items() if v[0]},
@@ -683,7 +734,8 @@ def sigma_only(args):
     I = {"h10": lambda: inputs.h_chain(10, 1.2), "h12": lambda: inputs.h_chain(12, 1.2),
          "n14": lambda: inputs.random_df(14, 14), "n16": lambda: inputs.random_df(16, 16)}[args.sigma_only]()
     ctx = sbci.Context.from_integrals(I)
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3,
+            "bf16x3": sbci.SBCI_BF16X3}[args.prec]
     c = torch.from_numpy(inputs.random_vector(ctx.na, ctx.nb, 1)).cuda()
     out = torch.empty_like(c)
     for _ in range(args.reps):
@@ -701,7 +753,8 @@ def run_ncu_solve(args):
 
     I = workload()
     ctx = sbci.Context.from_integrals(I)
-    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3}[args.prec]
+    prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3,
+            "bf16x3": sbci.SBCI_BF16X3}[args.prec]
     p = sbci.params(sector=1, prec=prec)
     B = max(1, args.batch) if args.prec == "tf32x3" else 1
     if B == 1:
