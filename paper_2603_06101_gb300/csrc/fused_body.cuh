@@ -33,7 +33,7 @@
 
 namespace sbci {
 
-constexpr int kFcThreads = 256;  // two threads per string of a 128-string tile
+constexpr int kFcThreads = 512;  // four threads per string of a 128-string tile
 constexpr int kFcMaxStr = 256;   // strings per spin (two tiles of the MMA's M = 128)
 constexpr int kFcMaxLink = 64;   // link words of string b staged in shared memory
 constexpr int kFcLinkMax = 8192; // 16-bit alpha link words of a space held in shared memory (na * nlink_a)
@@ -126,11 +126,13 @@ __device__ __forceinline__ bool fc_wait(const FcSmem &sm, uint32_t &phase) {
   return ok;
 }
 
-// One column b of A (written as row b of A^T into a.symA).  256 threads;
-// TMEM holds two accumulators of Np columns, at tmem and tmem +
-// fc_acc_stride(Np).  Returns false
-// (block-uniformly) if an MMA-completion wait ran out; *pending is then 1 when
-// a commit is still outstanding.
+// One column b of A (written as row b of A^T into a.symA).  kFcThreads =
+// 512 threads, four per string of a 128-string tile: two take halves of its
+// alpha links, two halves of the column's beta links (a string's links have
+// distinct pairs, so the four write disjoint slots).  TMEM holds two
+// accumulators of Np columns, at tmem and tmem + fc_acc_stride(Np).  Returns
+// false (block-uniformly) if an MMA-completion wait ran out; *pending is then
+// 1 when a commit is still outstanding.
 __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, int b, int Kp, int Np,
                                           const FcSmem &sm, uint32_t tmem, uint32_t &phase, int *pending) {
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -138,7 +140,7 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   const int ntile = (na + kTcM - 1) / kTcM;
   const uint32_t idesc = idesc_tf32(kTcM, Np);
   const uint32_t LBO = 128, SBO = (uint32_t)Kp * 32;
-  // 0. row b of z (z[b][j] = z[j][b]) and the link words of b; the previous
+  // 0. row b of z (z[b][j] = z[j][b]) and the decoded links of b; the previous
   //    column's readers of these buffers finished at its last barrier
   for (int j = tid; j < na; j += blockDim.x) sm.zrow[j] = __ldg(zf + (size_t)b * nb + j);
   for (int e = tid; e < a.nlink_b; e += blockDim.x) {  // J * nb < 2^16 for nb <= 256
@@ -147,57 +149,65 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   }
   __syncthreads();
   const int r = tid & (kTcM - 1);
-  const int half = tid >> 7;  // 0: alpha links of row r, 1: beta links of b at column r
-  const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
+  const int part = tid >> 7;      // 0, 1: alpha link halves; 2, 3: beta link halves
+  const bool beta = part >= 2;
+  const int sub = part & 1;
   const int rbase = (r >> 3) * (Kp * 8) + (r & 7) * 4;  // row r's part of an operand offset
-  constexpr int kPre = 16;  // beta-link values loaded before the previous tile's MMAs are waited for
+  const int nla = a.nlink_a, nlb = a.nlink_b;
+  const int nl = beta ? nlb : nla, hl = (nl + 1) / 2;
+  const int e0 = sub ? hl : 0, e1 = sub ? nl : hl;        // this thread's links
+  const int nch = Kp / 4, cq = (nch + 3) / 4;            // float4 chunks of a row, per part
+  const int c0 = part * cq, c1 = min(nch, c0 + cq);       // this thread's chunks of the split
+  constexpr int kPre = 8;  // beta-link values loaded before the previous tile's MMAs are waited for
   for (int t = 0; t < ntile; ++t) {
     const int ia = t * kTcM + r;
     const bool row_ok = ia < na;
     const float *zc = zf + ia;
     const uint32_t *lw = sm.lb;
-    const int nlb = a.nlink_b;
     float pre[kPre];
-    if (half == 1 && row_ok) {  // their z loads overlap the wait below
+    if (beta && row_ok) {  // their z loads overlap the wait below
 #pragma unroll
       for (int j = 0; j < kPre; ++j)
-        if (j < nlb) pre[j] = __ldg(zc + (lw[j] & 0xFFFFu));
+        if (e0 + j < e1) pre[j] = __ldg(zc + (lw[e0 + j] & 0xFFFFu));
     }
     if (t > 0) {  // the previous tile's MMAs read A / Alo: wait before overwriting them
       *pending = 1;
       if (!fc_wait(sm, phase)) return false;
       *pending = 0;
     }
-    float *mine = half ? sm.Alo : sm.A;
-    for (int q = 0; q < Kp; q += 4)
-      *reinterpret_cast<float4 *>(mine + opnd_off(r, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    float *mine = beta ? sm.Alo : sm.A;
+    {  // zero this thread's half of its row of its buffer
+      const int qh = (Kp / 8) * 4;
+      for (int q = sub ? qh : 0; q < (sub ? Kp : qh); q += 4)
+        *reinterpret_cast<float4 *>(mine + opnd_off(r, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();  // both halves of a row are zero before either writes its terms
     // each pair receives at most one term per spin (a string's links have
     // distinct pairs), so the gathers store into the zeroed rows
     if (row_ok) {
-      if (half == 0) {  // all operands in shared memory
-        const uint16_t *lr = sm.la + ia * a.nlink_a;
+      if (!beta) {  // all operands in shared memory
+        const uint16_t *lr = sm.la + ia * nla;
         const float *zr = sm.zrow;
-        const int nl = a.nlink_a;
 #pragma unroll 4
-        for (int e = 0; e < nl; ++e) {
+        for (int e = e0; e < e1; ++e) {
           const uint32_t w = lr[e];
           mine[rbase + fc_qoff((int)((w >> 8) & 0x7Fu))] = fc_sign(zr[w & 0xFFu], w);
         }
       } else {  // z rows of the column's beta links: coalesced loads
 #pragma unroll
         for (int j = 0; j < kPre; ++j)
-          if (j < nlb) {
-            const uint32_t w = lw[j];
+          if (e0 + j < e1) {
+            const uint32_t w = lw[e0 + j];
             mine[rbase + (int)((w >> 16) & 0x7FFFu)] = __uint_as_float(__float_as_uint(pre[j]) ^ (w & kSignBit));
           }
-        for (int e = kPre; e < nlb; e += 8) {
+        for (int e = e0 + kPre; e < e1; e += 8) {
           float f[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (e + j < nlb) f[j] = __ldg(zc + (lw[e + j] & 0xFFFFu));
+            if (e + j < e1) f[j] = __ldg(zc + (lw[e + j] & 0xFFFFu));
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (e + j < nlb) {
+            if (e + j < e1) {
               const uint32_t w = lw[e + j];
               mine[rbase + (int)((w >> 16) & 0x7FFFu)] = __uint_as_float(__float_as_uint(f[j]) ^ (w & kSignBit));
             }
@@ -205,8 +215,10 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
       }
     }
     __syncthreads();
-    // D = alpha + beta part, split in place into TF32 hi (A) and lo (Alo)
-    for (int q = q_lo; q < q_hi; q += 4) {
+    // D = alpha + beta part, split in place into TF32 hi (A) and lo (Alo);
+    // each thread a quarter of its row's float4 chunks
+    for (int ch = c0; ch < c1; ++ch) {
+      const int q = ch * 4;
       float4 *p = reinterpret_cast<float4 *>(sm.A + opnd_off(r, q, Kp));
       float4 *pl = reinterpret_cast<float4 *>(sm.Alo + opnd_off(r, q, Kp));
       const float4 va = *p, vb = *pl;
@@ -247,35 +259,34 @@ __device__ __forceinline__ bool fc_column(const SigmaArgs &a, const float *zf, i
   *pending = 0;
   // 3. epilogue: G[P][Ia] (this column) into shared memory over the operand
   //    buffers, [npair][kFcMaxStr]; warp w reads lane quadrant w % 4 of each
-  //    tile, half of the columns
+  //    tile and a quarter of the 16-column groups
   float *Gs = sm.A;
-  const int ncol16 = Np / 16;
-  const int c_begin = (warp >> 2) * ((ncol16 + 1) / 2) * 16;
-  const int c_end = (warp >> 2) ? Np : ((ncol16 + 1) / 2) * 16;
+  const int ng = Np / 16, gq = (ng + 3) / 4;
+  const int g0 = (warp >> 2) * gq, g1 = min(ng, g0 + gq);
   const int lane_row = (warp & 3) * 32 + (tid & 31);
   for (int t = 0; t < ntile; ++t) {
     const uint32_t lane_addr = tmem + (uint32_t)(t * fc_acc_stride(Np)) + ((uint32_t)((warp & 3) * 32) << 16);
     const int row = t * kTcM + lane_row;
-    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld16_nowait(lane_addr + (uint32_t)c0, v);
-      if (c0 + 16 < c_end) tmem_ld16_nowait(lane_addr + (uint32_t)(c0 + 16), v + 16);
+    for (int g = g0; g < g1; ++g) {
+      uint32_t v[16];
+      tmem_ld16_nowait(lane_addr + (uint32_t)(g * 16), v);
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < c_end && c0 + j < npair) Gs[(c0 + j) * kFcMaxStr + row] = __uint_as_float(v[j]);
+      for (int j = 0; j < 16; ++j)
+        if (g * 16 + j < npair) Gs[(g * 16 + j) * kFcMaxStr + row] = __uint_as_float(v[j]);
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  // 4. alpha-only scatter of the column: A[Ia, b] -> A^T[b][Ia]
+  // 4. alpha-only scatter of the column: A[Ia, b] -> A^T[b][Ia], one thread
+  //    per string, in link order (the order of the scatter kernel's sums)
   float *At = reinterpret_cast<float *>(a.symA) + (size_t)b * nb;
   for (int ia = tid; ia < na; ia += blockDim.x) {
-    const uint16_t *lr = sm.la + ia * a.nlink_a;
+    const uint16_t *lr = sm.la + ia * nla;
     float acc = 0.f;
 #pragma unroll 4
-    for (int e = 0; e < a.nlink_a; ++e) {  // in link order, as the scatter kernel sums
+    for (int e = 0; e < nla; ++e) {
       const uint32_t w = lr[e];
       acc += fc_sign(Gs[((w >> 8) & 0x7Fu) * kFcMaxStr + (w & 0xFFu)], w);
     }
