@@ -47,7 +47,7 @@ constexpr int kOsBeta = 8;
 constexpr int kOsLevels = 8;  // L = 2..9
 constexpr int kOsKp = 64, kOsNp = 64;
 constexpr int kOsMaxPair = 55;
-constexpr int kOsThreads = 256;
+constexpr int kOsThreads = 512;  // four per row of a 128-determinant tile
 
 // Instruction descriptor of kind::f16 with BF16 A and B (format 1 at bits
 // 7-9 and 10-12), F32 D (bits 4-5 = 1), both K-major, N >> 3 at bits 17-22,
@@ -158,7 +158,7 @@ struct OsSmem {
   __nv_bfloat16 *B;  // [7][Np x Kp]
   double *D;         // [128][npair]
   int *eI;           // [128] biased row exponents
-  int *eHalf;        // [2][128] exponents of the row halves
+  int *eQ;           // [4][128] exponents of the row quarters
   int *fP;           // [Np]
   uint64_t *bar;
   uint32_t *tmem_slot;
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(kOsThreads, 1)
   sm.B = sm.A + kOsSlices * kTcM * kOsKp;
   sm.D = reinterpret_cast<double *>(sm.B + kOsSlices * kOsNp * kOsKp);
   sm.eI = reinterpret_cast<int *>(sm.D + kTcM * npair);
-  sm.eHalf = sm.eI + kTcM;
-  sm.fP = sm.eHalf + 2 * kTcM;
+  sm.eQ = sm.eI + kTcM;
+  sm.fP = sm.eQ + 4 * kTcM;
   sm.bar = reinterpret_cast<uint64_t *>(sm.fP + kOsNp);
   sm.tmem_slot = reinterpret_cast<uint32_t *>(sm.bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -218,39 +218,45 @@ __global__ void __launch_bounds__(kOsThreads, 1)
   uint32_t phase = 0;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // 1. gather: thread r < 128 builds the alpha part of row r of D in FP64,
-    //    thread 128 + r the beta part in the A-slice area (free until the
-    //    slices are written; the previous tile's MMAs have completed)
+    // 1. gather: threads r and 128 + r build the alpha part of row r of D in
+    //    FP64 (halves of its alpha links), threads 256 + r and 384 + r the
+    //    beta part in the A-slice area (free until the slices are written; the
+    //    previous tile's MMAs have completed); a string's links have distinct
+    //    pairs, so the two halves write disjoint entries of the zeroed row
+    const int r = tid & (kTcM - 1), part = tid >> 7, sub = part & 1;
     {
-      const int r = tid & (kTcM - 1), h = tid >> 7;
-      double *row = h ? reinterpret_cast<double *>(sm.A) + (size_t)r * npair : sm.D + (size_t)r * npair;
-      for (int q = 0; q < npair; ++q) row[q] = 0.0;
+      const bool beta = part >= 2;
+      double *row = beta ? reinterpret_cast<double *>(sm.A) + (size_t)r * npair : sm.D + (size_t)r * npair;
+      const int hz = npair / 2;
+      for (int q = sub ? hz : 0; q < (sub ? npair : hz); ++q) row[q] = 0.0;
+      __syncthreads();
       const long long I = tile * kTcM + r;
       if (I < a.ndet) {
         int ia, ib;
         split_det(I, a.nb, ia, ib);
-        if (h == 0) {
-          const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+        const int nl = beta ? a.nlink_b : a.nlink_a, hl = (nl + 1) / 2;
+        const int e0 = sub ? hl : 0, ne = sub ? nl - hl : hl;
+        if (!beta) {
+          const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a + e0;
           const double *ccol = cin + ib;
           for_links<8, double>(
-              la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+              la, ne, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
               [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
         } else {
-          const uint32_t *lb = a.link_bT + ib;
+          const uint32_t *lb = a.link_bT + (size_t)e0 * a.nb + ib;
           const double *crow = cin + (size_t)ia * a.nb;
           for_links<8, double>(
-              lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+              lb, ne, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
               [&](uint32_t v, double cv) { row[link_pair(v)] += link_neg(v) ? -cv : cv; });
         }
       }
     }
     __syncthreads();
     // D = alpha part + beta part (alpha first, as the FP64 SIMT kernel adds
-    // them); two threads per row, each half of the columns
+    // them); four threads per row, each a quarter of the columns
+    const int quarter = ((npair + 31) / 32) * 8;  // quarters at multiples of 8 columns
     {
-      const int r = tid & (kTcM - 1), h = tid >> 7;
-      const int half = ((npair + 15) / 16) * 8;  // split at a multiple of 8 columns
-      const int q0 = h ? half : 0, q1 = h ? npair : min(half, npair);
+      const int q0 = min(part * quarter, npair), q1 = min(q0 + quarter, npair);
       double *row = sm.D + (size_t)r * npair;
       const double *rb = reinterpret_cast<const double *>(sm.A) + (size_t)r * npair;
       int emax = 0;
@@ -259,18 +265,17 @@ __global__ void __launch_bounds__(kOsThreads, 1)
         row[q] = d;
         emax = max(emax, bexp(d));
       }
-      sm.eHalf[h * kTcM + r] = emax;
+      sm.eQ[part * kTcM + r] = emax;
     }
     __syncthreads();
     // 2. the seven digit slices: each thread 8 consecutive columns of a row at
-    //    a time (one core-matrix row: a 16-byte store per slice), up to the
-    //    padded width (the beta staging overwrote the padding columns)
+    //    a time (one core-matrix row: a 16-byte store per slice), its quarter
+    //    of the padded width (the beta staging overwrote the padding columns)
     {
-      const int r = tid & (kTcM - 1), h = tid >> 7;
-      const int half = ((npair + 15) / 16) * 8;
-      const int q0 = h ? half : 0, q_end = h ? kOsKp : half, q1 = npair;
-      const int emax = max(sm.eHalf[r], sm.eHalf[kTcM + r]);
-      if (h == 0) sm.eI[r] = emax;
+      const int q0 = part * quarter, q_end = (part == 3) ? kOsKp : min((part + 1) * quarter, kOsKp);
+      const int q1 = npair;
+      const int emax = max(max(sm.eQ[r], sm.eQ[kTcM + r]), max(sm.eQ[2 * kTcM + r], sm.eQ[3 * kTcM + r]));
+      if (part == 0) sm.eI[r] = emax;
       const double *row = sm.D + (size_t)r * npair;
       for (int qc = q0; qc < q_end; qc += 8) {
         uint32_t w[kOsSlices][4];
@@ -319,27 +324,25 @@ __global__ void __launch_bounds__(kOsThreads, 1)
     if (!ok) break;
     phase ^= 1u;
     fence_after();
-    // 4. epilogue: warp w reads lane quadrant (w % 4) and column half (w / 4);
-    //    the eight levels of 8 columns at a time, added as integers
+    // 4. epilogue: warp w reads lane quadrant (w % 4) and column quarter
+    //    (w / 4); the eight levels of 4 columns at a time, added as integers
     {
-      const int r = (warp & 3) * 32 + (tid & 31);
-      const long long I = tile * kTcM + r;
-      const int eI = sm.eI[r];
+      const int rr = (warp & 3) * 32 + (tid & 31);
+      const long long I = tile * kTcM + rr;
+      const int eI = sm.eI[rr];
       const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-      const int c_begin = (warp >> 2) * (kOsNp / 2);
-      for (int c0 = c_begin; c0 < c_begin + kOsNp / 2; c0 += 8) {
-        uint32_t v[kOsLevels][8];
+      const int c_begin = (warp >> 2) * (kOsNp / 4);
+      for (int c0 = c_begin; c0 < c_begin + kOsNp / 4; c0 += 4) {
+        uint32_t v[kOsLevels][4];
 #pragma unroll
         for (int g = 0; g < kOsLevels; ++g)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-              : "=r"(v[g][0]), "=r"(v[g][1]), "=r"(v[g][2]), "=r"(v[g][3]), "=r"(v[g][4]), "=r"(v[g][5]),
-                "=r"(v[g][6]), "=r"(v[g][7])
-              : "r"(lane_addr + (uint32_t)(g * kOsNp + c0)));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                       : "=r"(v[g][0]), "=r"(v[g][1]), "=r"(v[g][2]), "=r"(v[g][3])
+                       : "r"(lane_addr + (uint32_t)(g * kOsNp + c0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         if (I < a.ndet) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < 4; ++j) {
             const int P = c0 + j;
             if (P >= npair) continue;
             // sum_L v_L 2^(56 - 8L) as a 64-bit integer (L = 2..9: shifts 40 .. -16;
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kOsThreads, 1)
 
 size_t os_smem_bytes(int npair) {
   return (size_t)kOsSlices * kTcM * kOsKp * 2 + (size_t)kOsSlices * kOsNp * kOsKp * 2 +
-         (size_t)kTcM * npair * 8 + (size_t)(3 * kTcM + kOsNp) * 4 + 16;
+         (size_t)kTcM * npair * 8 + (size_t)(5 * kTcM + kOsNp) * 4 + 16;
 }
 
 }  // namespace

@@ -31,7 +31,11 @@ def _ctx(sbci, I, fused: bool):
             os.environ["SBCI_FUSED"] = old
 
 
-@pytest.mark.parametrize("key,k", [(("chain", 10, 1.2), 4), (("chain", 6, 1.0), 3), (("chain", 8, 1.3), 3)])
+@pytest.mark.parametrize("key,k", [(("chain", 10, 1.2), 4), (("chain", 6, 1.0), 3), (("chain", 8, 1.3), 3),
+                                   # edge shapes: 6 strings per spin (one partial tile), 66 strings with
+                                   # 78 pairs (Np = 80: the second accumulator at a 128-column offset),
+                                   # 220 strings with 78 pairs (two tiles, Kp = 80)
+                                   (("chain", 4, 1.1), 2), (("rand", 12, 5, 2, 2), 2), (("rand", 12, 6, 3, 3), 2)])
 def test_fused_column_same_trajectory_as_tile_path(key, k):
     sbci = require_lib()
     I = make_integrals(key)
