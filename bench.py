@@ -640,6 +640,7 @@ def run_gb300(args, rank, world, local_rank):
     # ---------------- roofline of the dominant kernel
     pk, pk_kind = peaks()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
+    host_halted = kstats.pop("batch_host_halted", None)  # host time between rounds, not a kernel
     kst = {k: v for k, v in kstats.items() if v[0]}
     dom = max(kst.items(), key=lambda kv: kv[1][1])
     name, (nl, ms) = dom
@@ -720,6 +721,8 @@ def run_gb300(args, rank, world, local_rank):
             "autotuner": sbci.batch_classes() if B > 1 else None,
             "launches_timed": {k: v[0] for k, v in stats.items() if v[0]},
             "kernels_timing_pass": {k: {"launches": v[0], "ms": v[1]} for k, v in kstats.items() if v[0]},
+            "host_between_rounds_timing_pass": ({"halted_solves": host_halted[0], "ms": host_halted[1],
+                                                 "pass_ms": kpass_ms} if host_halted else None),
             "clocks": clocks, "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

@@ -361,8 +361,11 @@ sbci_status sbci_batch_profile(int enable);
 
 /* Waits for the recorded events and copies up to cap entries (families
  * "batch_update", "batch_project", "batch_gather_contract_tc",
- * "batch_fused_column", "batch_scatter", "batch_symfinish", "batch_end");
- * *n = 7.  A family that a class does not launch stays at zero. */
+ * "batch_fused_column", "batch_scatter", "batch_symfinish", "batch_end",
+ * then "batch_host_halted": launches = halted solves handled on the host
+ * between rounds, total_ms = the host wall time of that handling (their FP64
+ * re-syncs, verifications and state changes, with the GPU work it waits
+ * for)); *n = 8.  A family that a class does not launch stays at zero. */
 sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n);
 
 /* Launch shapes of the batch engine on the current device, one record per

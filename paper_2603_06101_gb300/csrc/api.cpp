@@ -131,6 +131,7 @@ struct sbci_ctx {
   size_t G_bytes = 0;
   double *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
   int *d_status = nullptr, *h_status = nullptr;  // device error word (bounded waits)
+  cudaEvent_t ev_fence = nullptr;  // marks the end of the host-issued work on the context stream
   int nsm = 1;
   int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
@@ -667,6 +668,59 @@ sbci_status finalize_state(sbci_ctx *c, bool converged, double E, double residua
   return start_state(c, alpha + 1, E_next);
 }
 
+// The end of the low-precision stage or of a refinement window without a
+// host round trip: the FP64 sigma X = H x, the dots x.x and x.X and the
+// restart all go onto the context stream (the host mirror takes the fields it
+// can know; the energy and scale stay on the device until the next read).
+// SBCI_ASYNC_SWITCH=0 keeps the synchronous path.
+bool async_switch() {
+  const char *e = std::getenv("SBCI_ASYNC_SWITCH");
+  return !(e && e[0] == '0');
+}
+
+sbci_status switch_async(sbci_ctx *c) {
+  Solver &s = c->s;
+  CtlState &h = *s.h_ctl;
+  RET(run_sigma(c, s.x, s.X, SBCI_FP64));
+  long long g = (c->ndet + 1023) / 1024;
+  if (g > c->grid) g = c->grid;
+  if (g < 1) g = 1;
+  const double *u[2] = {s.x, s.x}, *v[2] = {s.x, s.X};
+  RET(timed(c, K_DOTS, [&] { return launch_dots(u, v, 2, c->ndet, c->d_partials, (int)g, c->stream); }));
+  RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, (int)g, S_GEN0, S_GEN0 + 2, c->d_result, c->stream); }));
+  RestartArgs r{};
+  r.z0 = s.z[0];
+  r.Z0 = s.Z[0];
+  r.z1 = s.z[1];
+  r.Z1 = s.Z[1];
+  r.prec = s.p.prec;
+  r.zf = s.p.prec != SBCI_FP64 ? s.zf : nullptr;
+  r.iter_cap = 4 * s.p.max_sigma + 256;
+  r.ground = h.alpha == 0 ? 1 : 0;
+  r.Epre_fixed = h.alpha == 0 ? 0.0 : s.Ec[0];
+  CK(launch_restart_resync(s.d_ctl, c->d_result + S_GEN0, r, c->stream));
+  // the host mirror: everything but E, the scale and the update scalars
+  h.halt = H_RUN;
+  h.pending_check = 0;
+  h.first = 1;
+  h.sx_pending = 1.0;
+  h.t = 0;
+  h.stage = 1;
+  h.n_sync = 0;
+  h.prec = r.prec;
+  h.zf = r.zf;
+  h.iters = 0;
+  h.iter_cap = r.iter_cap;
+  h.zc = r.z0;
+  h.Zc = r.Z0;
+  h.zn = r.z1;
+  h.Zn = r.Z1;
+  h.n_sigma += 1;
+  h.n_sigma_fp64 += 1;
+  h.ntrace = 0;
+  return SBCI_OK;
+}
+
 // Acts on a halted controller.
 sbci_status handle_halt(sbci_ctx *c) {
   Solver &s = c->s;
@@ -678,6 +732,7 @@ sbci_status handle_halt(sbci_ctx *c) {
       set_error("non-finite values in the SB step");
       return SBCI_ERR_NUMERIC;
     case H_SWITCH: {  // end of the low-precision stage or of a refinement window: exact H-image, stage 1
+      if (async_switch()) return switch_async(c);
       double xx, xX, XX;
       RET(resync(c, &xx, &xX, &XX));
       return start_iteration(c, 1.0 / std::sqrt(xx), xX / xx, 1);
@@ -1934,6 +1989,12 @@ sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
 
 cudaStream_t sbci::ctx_stream(const sbci_ctx *c) { return c->stream; }
 
+cudaError_t sbci::ctx_fence(sbci_ctx *c, cudaStream_t waiter) {
+  cudaError_t e = cudaEventRecord(c->ev_fence, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, c->ev_fence, 0);
+  return e;
+}
+
 bool sbci::ctx_batch_job(sbci_ctx *c, BatchJob *j) {
   Solver &s = c->s;
   if (!s.active || s.done || s.p.prec != SBCI_TF32X3 || s.h_ctl->prec != SBCI_TF32X3 ||
@@ -2039,6 +2100,7 @@ void sbci_destroy(sbci_ctx *c) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
+  if (c->ev_fence) cudaEventDestroy(c->ev_fence);
   if (c->h_result) cudaFreeHost(c->h_result);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->d_status) cudaFree(c->d_status);
@@ -2204,6 +2266,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaMallocHost((void **)&c->h_status, sizeof(int)), "cudaMallocHost"));
   *c->h_status = 0;
   TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
+  TRY(cuda_ok(cudaEventCreateWithFlags(&c->ev_fence, cudaEventDisableTiming), "cudaEventCreate"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
   {  // SBCI_FUSED=0 keeps the tile kernel + scatter for singlet-sector TF32x3 steps

@@ -139,6 +139,47 @@ cudaError_t launch_pinv(const double *diag, double E, double guard, long long n,
   return cudaGetLastError();
 }
 
+__global__ void k_restart_resync(CtlState *ctl, const double *dots, RestartArgs r) {
+  CtlHead &h = *ctl;
+  const double xx = dots[0], xX = dots[1];
+  if (!(xx > 0.0) || !isfinite(xx) || !isfinite(xX)) {  // the host finds the failure at its next read
+    h.halt = H_NUMERIC;
+    return;
+  }
+  const double sx = 1.0 / sqrt(xx), E = xX / xx;
+  h.halt = H_RUN;
+  h.pending_check = 0;
+  h.first = 1;
+  h.sx_pending = 1.0;
+  h.t = 0;
+  h.E = E;
+  h.stage = 1;
+  h.n_sync = 0;
+  h.prec = r.prec;
+  h.zf = r.zf;
+  h.up.sx = sx;
+  h.up.sy = 0.0;
+  h.up.b = 0.0;
+  h.up.c = 0.0;
+  h.up.E = E;
+  h.up.kinv = 1.0;
+  h.up.Epre = r.ground ? E : r.Epre_fixed;
+  h.iters = 0;
+  h.iter_cap = r.iter_cap;
+  h.zc = r.z0;
+  h.Zc = r.Z0;
+  h.zn = r.z1;
+  h.Zn = r.Z1;
+  h.n_sigma += 1;  // the FP64 re-sync
+  h.n_sigma_fp64 += 1;
+  h.ntrace = 0;
+}
+
+cudaError_t launch_restart_resync(CtlState *ctl, const double *dots, const RestartArgs &r, cudaStream_t s) {
+  k_restart_resync<<<1, 1, 0, s>>>(ctl, dots, r);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_project_ctl(const StepArgs &a, int grid, cudaStream_t s) {
   k_project_ctl<<<grid, kStepThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -276,6 +276,10 @@ bool ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream);
 sbci_status solve_round_launch(sbci_ctx *c);
 sbci_status solve_round_finish(sbci_ctx *c, int *done, bool own_graph = true);
 cudaStream_t ctx_stream(const sbci_ctx *c);
+// Makes waiter wait for the work issued so far on the context's stream (the
+// host's asynchronous state changes of a halted solve, before a batch round
+// that includes it reads its vectors and controller).
+cudaError_t ctx_fence(sbci_ctx *c, cudaStream_t waiter);
 struct BatchJob;
 // Fills the batched-kernel view of an active TF32x3 solve with npair within the
 // batched kernels' limit; false if the solve cannot join a batch.

@@ -138,6 +138,8 @@ struct KernelStats {
   bool on = false;
   long long launches[BK_COUNT] = {};
   double ms[BK_COUNT] = {};
+  long long host_events = 0;  // halted solves handled between rounds
+  double host_ms = 0.0;       // host wall time of that handling
 };
 
 struct GraphCache {
@@ -381,6 +383,10 @@ sbci_status launch_batch_round(sbci_server *sv) {
       continue;
     }
     table_offsets(t, nj, sl.ctx);
+    if (ctx_fence(sl.ctx, sv->stream) != cudaSuccess) {
+      set_error("server: stream ordering failed");
+      return SBCI_ERR_CUDA;
+    }
     t.halted[nj] = 0;
     sv->batch_slots.push_back(i);
     ++nj;
@@ -565,6 +571,10 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
         continue;
       }
       table_offsets(t, nj, ctx[i]);
+      if (ctx_fence(ctx[i], eng.stream) != cudaSuccess) {
+        set_error("sbci_solve_batch: stream ordering failed");
+        return SBCI_ERR_CUDA;
+      }
       t.halted[nj] = 0;
       row.push_back(i);
       ++nj;
@@ -590,6 +600,8 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       return SBCI_ERR_CUDA;
     }
     sbci_status host_st = SBCI_OK;
+    const double th0 = now_s();
+    const long long nhalted = (long long)pending.size();
     for (int i : pending) {
       is_pending[i] = 0;
       if (host_st != SBCI_OK) continue;
@@ -604,6 +616,10 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
       }
     }
     pending.clear();
+    if (eng.prof.on && nhalted > 0) {
+      eng.prof.host_events += nhalted;
+      eng.prof.host_ms += 1e3 * (now_s() - th0);
+    }
     if (nj > 0 && cudaStreamSynchronize(eng.stream) != cudaSuccess) {
       set_error("sbci_solve_batch: batch round failed");
       return SBCI_ERR_CUDA;
@@ -640,6 +656,8 @@ sbci_status sbci_batch_profile(int enable) {
     pe->prof.launches[k] = 0;
     pe->prof.ms[k] = 0.0;
   }
+  pe->prof.host_events = 0;
+  pe->prof.host_ms = 0.0;
   pe->prof.on = enable != 0;
   return SBCI_OK;
 }
@@ -652,12 +670,19 @@ sbci_status sbci_batch_profile_read(sbci_kernel_stat *out, int cap, int *n) {
     return SBCI_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lock(pe->mu);
-  if (n) *n = BK_COUNT;
+  if (n) *n = BK_COUNT + 1;
   for (int k = 0; k < BK_COUNT && out && k < cap; ++k) {
     std::memset(out[k].name, 0, sizeof(out[k].name));
     std::strncpy(out[k].name, kBatchKernelName[k], sizeof(out[k].name) - 1);
     out[k].launches = pe->prof.launches[k];
     out[k].total_ms = pe->prof.ms[k];
+  }
+  if (out && BK_COUNT < cap) {
+    sbci_kernel_stat &h = out[BK_COUNT];
+    std::memset(h.name, 0, sizeof(h.name));
+    std::strncpy(h.name, "batch_host_halted", sizeof(h.name) - 1);
+    h.launches = pe->prof.host_events;
+    h.total_ms = pe->prof.host_ms;
   }
   return SBCI_OK;
 }

@@ -128,7 +128,8 @@ def test_batch_profile_same_result():
     sbci.batch_profile(False)
     assert np.array_equal(E1, E0)
     assert set(stats) == {"batch_update", "batch_project", "batch_gather_contract_tc", "batch_fused_column",
-                          "batch_scatter", "batch_symfinish", "batch_end"}
+                          "batch_scatter", "batch_symfinish", "batch_end", "batch_host_halted"}
+    assert stats.pop("batch_host_halted")[0] > 0  # (halted solves handled between rounds)
     bodies = stats["batch_end"][0]
     # every solve of this mix is outside the singlet sector: the tile kernel and
     # the scatter run, the column kernel and the symmetric finish do not
