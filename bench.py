@@ -274,7 +274,7 @@ def run_reference(args, rank, world):
 
 TF32_OF_BF16 = 0.5  # nominal dense TF32 / BF16 tensor rate (1.1 vs 2.25 PFLOP/s)
 SIGMA_FAMILIES = ("gather_contract_tc", "gather_contract_os", "gather_contract", "gather_contract_lr",
-                  "gather_contract_bf16", "scatter", "symfinish", "fused_column")
+                  "gather_contract_bf16", "gather_contract_tc_lr", "scatter", "symfinish", "fused_column")
 
 
 def family_of(name: str) -> str:
@@ -303,14 +303,18 @@ def roofline(name, launches, ms, dets_per_launch, npair, prec, pk, pk_kind, sm_m
                                    f"{dets_per_launch} determinants"}
         hbm["frac"] = hbm["achieved"] / hbm_peak
         other = None
-        if fam in ("gather_contract_tc", "fused_column", "gather_contract_os", "gather_contract_bf16"):
-            tf32 = fam in ("gather_contract_tc", "fused_column")
+        if fam in ("gather_contract_tc", "fused_column", "gather_contract_os", "gather_contract_bf16",
+                   "gather_contract_tc_lr"):
+            tf32 = fam in ("gather_contract_tc", "fused_column", "gather_contract_tc_lr")
             tpeak = pk.get("bf16_tflops", 1900.0) * (TF32_OF_BF16 if tf32 else 1.0)
             note = ("TF32: measured bf16 x nominal TF32/BF16 ratio 0.5" if tf32
                     else "BF16 operands (BF16x3 split, or the exact slices of the FP64 contraction): measured bf16")
+            anote = "2 npair^2 flops per determinant (the split precisions execute more)"
+            if fam == "gather_contract_tc_lr":
+                anote += "; the factored form executes 4 npair (r + 2) products' worth, r + 2 the factor's rank"
             other = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                      "peak_kind": f"{pk_kind} {note}", "algorithmic_per_launch": flops,
-                     "algorithmic_note": "2 npair^2 flops per determinant (the split precisions execute more)"}
+                     "algorithmic_note": anote}
         elif fam in ("gather_contract", "gather_contract_lr"):
             lanes = 2.0 if prec == "fp64" else 128.0
             peak = 2.0 * lanes * 152 * sm_mhz * 1e6 / 1e12
@@ -433,10 +437,34 @@ def serving_leg(n, slots, quiet=True):
     return out
 
 
+def _time_sigma(ctx, c, out, prec, pname, reps, pk, pk_kind, sm_mhz):
+    """One warm-up and reps sigma calls, per-kernel CUDA-event times on the
+    library stream; the roofline of the dominant kernel."""
+    import torch
+
+    ctx.sigma(c, out, prec=prec)  # warm-up (scratch allocation)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.sigma(c, out, prec=prec)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = ctx.profile_read()
+    ctx.profile(False)
+    st = {k: v for k, v in st.items() if v[0] and k.startswith("sigma_")}
+    dom = max(st.items(), key=lambda kv: kv[1][1])
+    return {"ms_per_sigma": sum(v[1] for v in st.values()) / reps, "wall_ms_per_sigma": 1e3 * wall / reps,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in st.items()},
+            "roofline": roofline(dom[0], dom[1][0], dom[1][1], ctx.ndet, ctx.npair, pname, pk, pk_kind, sm_mhz)}
+
+
 def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
     """Random density-fitted integrals, n = 14, 7 alpha / 7 beta (seed 14;
-    11,778,624 determinants): one TF32x3 sigma and one FP64 sigma timed per
-    kernel with CUDA events on the library stream (roofline of each), then the
+    11,778,624 determinants): one TF32x3 sigma (the full form, and the
+    factored tensor-core contraction on a second context with
+    SBCI_TC_LOWRANK=1), one BF16x3 and one FP64 sigma, timed per kernel
+    with CUDA events on the library stream (roofline of each), then the
     2-state solve in mixed precision with FP64 refinement (solve time, FP64
     residual per state)."""
     import torch
@@ -451,23 +479,8 @@ def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
            "npair": ctx.npair}
     for tag, prec, pname in (("tf32x3", sbci.SBCI_TF32X3, "tf32x3"), ("bf16x3", sbci.SBCI_BF16X3, "bf16x3"),
                              ("fp64", sbci.SBCI_FP64, "fp64")):
-        ctx.sigma(c, out, prec=prec)  # warm-up (scratch allocation)
-        torch.cuda.synchronize()
-        ctx.profile(True)
-        t0 = time.perf_counter()
-        for _ in range(reps if prec != sbci.SBCI_FP64 else 1):
-            ctx.sigma(c, out, prec=prec)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        st = ctx.profile_read()
-        ctx.profile(False)
-        st = {k: v for k, v in st.items() if v[0] and k.startswith("sigma_")}
-        nsig = reps if prec != sbci.SBCI_FP64 else 1
-        dom = max(st.items(), key=lambda kv: kv[1][1])
-        res[f"sigma_{tag}"] = {
-            "ms_per_sigma": sum(v[1] for v in st.values()) / nsig, "wall_ms_per_sigma": 1e3 * wall / nsig,
-            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in st.items()},
-            "roofline": roofline(dom[0], dom[1][0], dom[1][1], ctx.ndet, ctx.npair, pname, pk, pk_kind, sm_mhz)}
+        res[f"sigma_{tag}"] = _time_sigma(ctx, c, out, prec, pname, reps if prec != sbci.SBCI_FP64 else 1,
+                                          pk, pk_kind, sm_mhz)
     p = sbci.params(prec=sbci.SBCI_TF32X3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -479,6 +492,18 @@ def random_df_leg(pk, pk_kind, sm_mhz, reps=3):
         "converged": [int(r.converged) for r in R], "sigma_per_state": [int(r.n_sigma) for r in R],
         "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R]}
     ctx.close()
+    # the factored TF32x3 contraction on the same space, for comparison
+    old = os.environ.get("SBCI_TC_LOWRANK")
+    os.environ["SBCI_TC_LOWRANK"] = "1"
+    try:
+        fac = sbci.Context.from_integrals(I)
+    finally:
+        if old is None:
+            del os.environ["SBCI_TC_LOWRANK"]
+        else:
+            os.environ["SBCI_TC_LOWRANK"] = old
+    res["sigma_tf32x3_factored"] = _time_sigma(fac, c, out, sbci.SBCI_TF32X3, "tf32x3", reps, pk, pk_kind, sm_mhz)
+    fac.close()
     return res
 
 

@@ -64,7 +64,13 @@ typedef enum {
                       instead of npair^2 multiply-adds; SBCI_LOWRANK=0, read
                       when a context is created, turns it off. */
   SBCI_TF32X3 = 1, /* 3-term TF32 split on the tensor cores, FP32 accumulation
-                      (about 2^-21 relative per product), n <= 14; singlet-sector
+                      (about 2^-21 relative per product), n <= 14, and n = 15
+                      with density-fitted integrals: there the full form's
+                      operands exceed shared memory and the factored form
+                      G = (D F)(F M)^T runs as two chained tensor-core products
+                      per tile (SBCI_TC_LOWRANK=1, read when a context is
+                      created, takes that form wherever it fits, 0 never);
+                      singlet-sector
                       steps of spaces with at most 256 strings per spin run the
                       column-fused kernel (gather, contraction and scatter of one
                       column of the alpha part per CTA, no scratch in global

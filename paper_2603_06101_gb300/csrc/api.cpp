@@ -60,13 +60,14 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_GCBF, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_GCBF, K_GCTCLR, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
                                        "davidson_dots", "davidson_combine", "davidson_precond",
                                        "sigma_gather_contract_os", "sigma_gather_contract_lr",
-                                       "sigma_fused_column", "sigma_gather_contract_bf16"};
+                                       "sigma_fused_column", "sigma_gather_contract_bf16",
+                                       "sigma_gather_contract_tc_lr"};
 
 struct Prof {
   bool on = false;
@@ -125,6 +126,11 @@ struct sbci_ctx {
   // factored form W = F M F^T of the FP64 SIMT contraction (lowrank.h, df_factor): its rank, 0: off
   int lr_rank = 0;
   void *d_lrUt64 = nullptr, *d_lrUL64 = nullptr;
+  // the same factor as pre-split TF32 operands of the factored tensor-core
+  // contraction (kernels_tclr.cu), and that kernel's CTAs (0: full form)
+  uint32_t *d_Wtclr = nullptr;
+  int tclr_grid = 0;
+  bool tclr_first = false;  // SBCI_TC_LOWRANK=1: the factored form also where the full one fits
   double *d_diag = nullptr;
   double *d_ea = nullptr, *d_eb = nullptr, *d_ja = nullptr;
   void *d_G = nullptr;
@@ -218,8 +224,9 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
     int Kp, Np;
     uint32_t cols;
     size_t smem;
-    if (tc_dims(c->npair, &Kp, &Np, &cols, &smem) && c->tc_grid > 0) return SBCI_OK;
-    set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14); use SBCI_BF16X3 or SBCI_FP32");
+    if ((tc_dims(c->npair, &Kp, &Np, &cols, &smem) && c->tc_grid > 0) || c->tclr_grid > 0) return SBCI_OK;
+    set_error("SBCI_TF32X3: operands of this orbital count exceed shared memory (n <= 14, n = 15 with "
+              "density-fitted integrals); use SBCI_BF16X3 or SBCI_FP32");
     return SBCI_ERR_INVALID;
   }
   if (prec == SBCI_BF16X3) {
@@ -233,7 +240,7 @@ sbci_status check_prec(const sbci_ctx *c, int prec) {
 
 // The gather + contract kernel family of a sigma precision, and its launch.
 int gc_kid(const sbci_ctx *c, int prec) {
-  if (prec == SBCI_TF32X3) return K_GCTC;
+  if (prec == SBCI_TF32X3) return c->tclr_grid > 0 && (c->tc_grid <= 0 || c->tclr_first) ? K_GCTCLR : K_GCTC;
   if (prec == SBCI_BF16X3) return K_GCBF;
   if (prec == SBCI_FP64 && c->d_Wos) return K_GCOS;
   if (prec == SBCI_FP64 && c->lr_rank > 0) return K_GCLR;
@@ -244,6 +251,8 @@ cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
   switch (gc_kid(c, prec)) {
     case K_GCTC:
       return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream);
+    case K_GCTCLR:
+      return launch_gather_contract_tclr(a, c->d_Wtclr, c->lr_rank, c->d_status, c->tclr_grid, c->stream);
     case K_GCBF:
       return launch_gather_contract_bf(a, c->d_Wbf, c->d_status, c->bf_grid, c->stream);
     case K_GCOS:
@@ -2096,7 +2105,7 @@ void sbci_destroy(sbci_ctx *c) {
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wbf, c->d_fc_link_a, c->d_Wos, c->d_fexp, c->d_cf,
                   c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
-                  c->d_tmp_out, c->d_lrUt64, c->d_lrUL64};
+                  c->d_tmp_out, c->d_lrUt64, c->d_lrUL64, c->d_Wtclr};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
@@ -2314,6 +2323,24 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       TRY(up(&c->d_lrUt64, Ut.data(), Ut.size() * 8));
       TRY(up(&c->d_lrUL64, UL.data(), UL.size() * 8));
       c->lr_rank = rr;
+      // the factored TF32x3 contraction on the tensor cores where the full
+      // form's operands do not fit shared memory (n = 15) and its own do; at
+      // n = 14 the full form is faster (the factor saves 14 % of the tensor
+      // work of a gather-bound kernel and adds a TMEM round trip).
+      // SBCI_TC_LOWRANK=1 takes the factored form wherever it fits, 0 never.
+      const char *tlr = std::getenv("SBCI_TC_LOWRANK");
+      c->tclr_first = tlr && std::strcmp(tlr, "1") == 0;
+      const size_t words = tclr_W_words(np, rr);
+      if (!(tlr && std::strcmp(tlr, "0") == 0) && words > 0) {
+        const int g = tclr_grid(np, rr, c->ndet, c->nsm);
+        if (g > 0) {
+          TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtclr, sizeof(uint32_t) * words), "cudaMalloc"));
+          TRY(cuda_ok(launch_split_lr_tc(static_cast<const double *>(c->d_lrUt64),
+                                         static_cast<const double *>(c->d_lrUL64), rr, np, c->d_Wtclr, c->stream),
+                      "split kernel"));
+          c->tclr_grid = g;
+        }
+      }
     }
   }
   {

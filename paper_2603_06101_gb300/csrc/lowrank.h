@@ -10,9 +10,11 @@
 // exact-slice kernel) forms G = (F M) (F^T D): 2 (r + 2) npair multiply-adds
 // per determinant instead of npair^2 (the density-fitted contraction, T = B D
 // then G = B^T T, with the Cholesky vectors in place of B).  That contraction
-// is bound by GB300's FP64 pipe, so the flops count; the FP32 one is bound by
-// its gathers and keeps the full form (the two-pass form measured 2.4x slower
-// there).
+// is bound by GB300's FP64 pipe, so the flops count; the FP32 SIMT one is
+// bound by its gathers and keeps the full form (the two-pass form measured
+// 2.4x slower there).  The TF32x3 tensor-core contraction has a factored
+// kernel of its own (kernels_tclr.cu), two chained products per tile on the
+// pre-split factor.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -205,6 +205,18 @@ size_t bf_W_elems(int npair);
 cudaError_t launch_split_W_bf(const double *W, int npair, uint16_t *out, cudaStream_t s);
 cudaError_t launch_gather_contract_bf(const SigmaArgs &a, const uint16_t *Wbf, int *status, int grid,
                                       cudaStream_t s);
+// Factored (density-fitted) TF32x3 gather + contract (kernels_tclr.cu):
+// W = F M F^T of rank rr (lowrank.h), G = (D F)(F M)^T as two chained tcgen05
+// products per tile; writes FP32 G like prec 1.  The factor as pre-split
+// operands, tclr_W_words(npair, rr) words from launch_split_lr_tc (Ut = F^T
+// [rr][npair], UL = F M [npair][rr], FP64).
+bool tclr_dims(int npair, int rr, int *Kp, int *Np, int *Rp, uint32_t *cols, size_t *smem);
+size_t tclr_W_words(int npair, int rr);  // 0: unsupported shape
+cudaError_t launch_split_lr_tc(const double *Ut, const double *UL, int rr, int npair, uint32_t *out,
+                               cudaStream_t s);
+int tclr_grid(int npair, int rr, long long ndet, int num_sms);  // 0: unsupported shape
+cudaError_t launch_gather_contract_tclr(const SigmaArgs &a, const uint32_t *Wlr, int rr, int *status, int grid,
+                                        cudaStream_t s);
 size_t sigma_scratch_bytes(int npair, long long ndet, int prec);
 
 // Helper kernels (kernels_vec.cu)

@@ -152,6 +152,91 @@ __device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, co
   fence_after();
 }
 
+// Steps 1 and 2 of a tile, row (threadIdx.x % 128) of D for determinant I
+// (a zero row when !valid): the gather in FP32, the alpha part into A and the
+// beta part into Alo (free until the split), each row owned by one thread;
+// then D = alpha part + beta part split in place, A <- tf32(D) and
+// Alo <- tf32(D - tf32(D)), each thread half a row.  256 threads.  Ends with
+// the fences and the barrier that hand the operand to the tensor core.
+__device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float *cin, long long I, bool valid,
+                                                int Kp, const TcSmem &sm) {
+  const int tid = threadIdx.x;
+  float *A = sm.A, *Alo = sm.Alo;
+  const int row = tid & (kTcM - 1);  // determinant row of this thread
+  const int half = tid >> 7;         // 0: alpha links / first half, 1: beta links / second half
+  const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
+  float *mine = half ? Alo : A;
+  for (int q = 0; q < Kp; q += 4)
+    *reinterpret_cast<float4 *>(mine + opnd_off(row, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    int ia, ib;
+    split_det(I, a.nb, ia, ib);
+    if (half == 0) {
+      const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+      const float *ccol = cin + ib;
+      for_links_pipelined<8, float>(
+          la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+          [&](uint32_t v, float f) {
+            mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
+    } else {
+      const uint32_t *lb = a.link_bT + ib;
+      const float *crow = cin + (size_t)ia * a.nb;
+      for_links_pipelined<8, float>(
+          lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+          [&](uint32_t v, float f) {
+            mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
+    }
+  }
+  __syncthreads();
+  for (int q = q_lo; q < q_hi; q += 4) {
+    float4 *p = reinterpret_cast<float4 *>(A + opnd_off(row, q, Kp));
+    float4 *pl = reinterpret_cast<float4 *>(Alo + opnd_off(row, q, Kp));
+    const float4 va = *p, vb = *pl;
+    const float4 v = make_float4(va.x + vb.x, va.y + vb.y, va.z + vb.z, va.w + vb.w);
+    float4 h, l;
+    h.x = tf32_round(v.x);
+    h.y = tf32_round(v.y);
+    h.z = tf32_round(v.z);
+    h.w = tf32_round(v.w);
+    l.x = tf32_round(v.x - h.x);
+    l.y = tf32_round(v.y - h.y);
+    l.z = tf32_round(v.z - h.z);
+    l.w = tf32_round(v.w - h.w);
+    *p = h;
+    *pl = l;
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+}
+
+// Epilogue of a tile: the 128 x Np FP32 accumulator at TMEM column acc into
+// G[P][I] (P < npair, valid rows only); warp w reads lane quadrant (w % 4)
+// and column half (w / 4).  256 threads.
+__device__ __forceinline__ void tc_store_G(const SigmaArgs &a, uint32_t acc, long long I, bool valid, int Np) {
+  const int warp = threadIdx.x >> 5;
+  float *G = reinterpret_cast<float *>(a.G);
+  const uint32_t lane_addr = acc + ((uint32_t)((warp & 3) * 32) << 16);
+  const int ncol16 = Np / 16;
+  const int c_begin = (warp >> 2) * ((ncol16 + 1) / 2) * 16;
+  const int c_end = (warp >> 2) ? Np : ((ncol16 + 1) / 2) * 16;
+  for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+    // up to two 16-column loads in flight before one wait
+    uint32_t r[32];
+    tmem_ld16_nowait(lane_addr + (uint32_t)c0, r);
+    if (c0 + 16 < c_end) tmem_ld16_nowait(lane_addr + (uint32_t)(c0 + 16), r + 16);
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < c_end && c0 + j < a.npair) G[(size_t)(c0 + j) * a.ndet + I] = __uint_as_float(r[j]);
+    }
+  }
+}
+
 // One tile of 128 determinants: gather, split, three MMAs per K step, bounded
 // wait, epilogue into G.  256 threads.  Returns false (block-uniformly) if
 // the MMA-completion wait ran out.
@@ -159,111 +244,38 @@ __device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, co
 // conversion before a plain sigma call).
 __device__ __forceinline__ bool tc_tile(const SigmaArgs &a, const float *cin, long long tile, int Kp, int Np,
                                         const TcSmem &sm, uint32_t tmem, uint32_t &phase) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int npair = a.npair;
-  float *A = sm.A, *Alo = sm.Alo;
+  const int tid = threadIdx.x;
   const uint32_t sA = sm.sA, sAlo = sm.sAlo, sBhi = sm.sBhi, sBlo = sm.sBlo, sbar = sm.sbar;
   const uint32_t idesc = idesc_tf32(kTcM, Np);
   const uint32_t LBO = 128, SBO = (uint32_t)Kp * 32;
-  float *G = reinterpret_cast<float *>(a.G);
-  bool ok = true;
-  const int row = tid & (kTcM - 1);  // determinant row of this thread
-  const int half = tid >> 7;         // 0: alpha links / first half, 1: beta links / second half
-  const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
-  {
-    const long long I = tile * kTcM + row;
-    const bool valid = I < a.ndet;
-    // 1. gather this row of D (FP32): the alpha part into A, the beta part
-    //    into Alo (free until the split), each row owned by one thread
-    float *mine = half ? Alo : A;
-    for (int q = 0; q < Kp; q += 4)
-      *reinterpret_cast<float4 *>(mine + opnd_off(row, q, Kp)) = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-      int ia, ib;
-      split_det(I, a.nb, ia, ib);
-      if (half == 0) {
-        const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
-        const float *ccol = cin + ib;
-        for_links_pipelined<8, float>(
-            la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
-            [&](uint32_t v, float f) {
-              mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
-            });
-      } else {
-        const uint32_t *lb = a.link_bT + ib;
-        const float *crow = cin + (size_t)ia * a.nb;
-        for_links_pipelined<8, float>(
-            lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-            [&](uint32_t v, float f) {
-              mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
-            });
-      }
+  const long long I = tile * kTcM + (tid & (kTcM - 1));
+  const bool valid = I < a.ndet;
+  // 1-2. D gathered and split into A / Alo
+  tc_gather_split(a, cin, I, valid, Kp, sm);
+  // 3. three products per K step, one issuing thread
+  if (tid == 0) {
+    for (int kk = 0; kk < Kp / 8; ++kk) {
+      const uint32_t koff = (uint32_t)kk * 256;  // two K-adjacent core matrices
+      const uint64_t ah = smem_desc(sA + koff, LBO, SBO), al = smem_desc(sAlo + koff, LBO, SBO);
+      const uint64_t bh = smem_desc(sBhi + koff, LBO, SBO), bl = smem_desc(sBlo + koff, LBO, SBO);
+      mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
+      mma_tf32(tmem, ah, bl, idesc, 1u);
+      mma_tf32(tmem, al, bh, idesc, 1u);
     }
-    __syncthreads();
-    // 2. D = alpha part + beta part, split in place: A <- tf32(D), Alo <- tf32(D - tf32(D));
-    //    each thread half a row
-    for (int q = q_lo; q < q_hi; q += 4) {
-      float4 *p = reinterpret_cast<float4 *>(A + opnd_off(row, q, Kp));
-      float4 *pl = reinterpret_cast<float4 *>(Alo + opnd_off(row, q, Kp));
-      const float4 va = *p, vb = *pl;
-      const float4 v = make_float4(va.x + vb.x, va.y + vb.y, va.z + vb.z, va.w + vb.w);
-      float4 h, l;
-      h.x = tf32_round(v.x);
-      h.y = tf32_round(v.y);
-      h.z = tf32_round(v.z);
-      h.w = tf32_round(v.w);
-      l.x = tf32_round(v.x - h.x);
-      l.y = tf32_round(v.y - h.y);
-      l.z = tf32_round(v.z - h.z);
-      l.w = tf32_round(v.w - h.w);
-      *p = h;
-      *pl = l;
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // 3. three products per K step, one issuing thread
-    if (tid == 0) {
-      for (int kk = 0; kk < Kp / 8; ++kk) {
-        const uint32_t koff = (uint32_t)kk * 256;  // two K-adjacent core matrices
-        const uint64_t ah = smem_desc(sA + koff, LBO, SBO), al = smem_desc(sAlo + koff, LBO, SBO);
-        const uint64_t bh = smem_desc(sBhi + koff, LBO, SBO), bl = smem_desc(sBlo + koff, LBO, SBO);
-        mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
-        mma_tf32(tmem, ah, bl, idesc, 1u);
-        mma_tf32(tmem, al, bh, idesc, 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       sbar)
-                   : "memory");
-    }
-    ok = mbar_wait(sbar, phase, kWaitIters);
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) return false;
-    phase ^= 1u;
-    fence_after();
-    // 4. epilogue: warp w reads lane quadrant (w % 4), column half (w / 4)
-    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const int ncol16 = Np / 16;
-    const int c_begin = (warp >> 2) * ((ncol16 + 1) / 2) * 16;
-    const int c_end = (warp >> 2) ? Np : ((ncol16 + 1) / 2) * 16;
-    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
-      // up to two 16-column loads in flight before one wait
-      uint32_t r[32];
-      tmem_ld16_nowait(lane_addr + (uint32_t)c0, r);
-      if (c0 + 16 < c_end) tmem_ld16_nowait(lane_addr + (uint32_t)(c0 + 16), r + 16);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (valid) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < c_end && c0 + j < npair) G[(size_t)(c0 + j) * a.ndet + I] = __uint_as_float(r[j]);
-      }
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sbar)
+                 : "memory");
   }
-  return ok;
+  bool ok = mbar_wait(sbar, phase, kWaitIters);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) return false;
+  phase ^= 1u;
+  fence_after();
+  // 4. epilogue
+  tc_store_G(a, tmem, I, valid, Np);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  return true;
 }
 
 }  // namespace sbci
