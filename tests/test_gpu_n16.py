@@ -10,6 +10,8 @@ resident in HBM).
   verification to the paper's thresholds): the library's FP64 residual is
   below r0 = 1e-5, and on sampled rows the oracle's (H x)_I - E x_I is within
   that bound too (an eigenpair check independent of the library's sigma).
+* The same solve with the BF16x3 stage on the tensor cores (tcgen05
+  kind::f16), checked the same way.
 """
 import gc
 
@@ -70,6 +72,26 @@ def test_mixed_ground_state_n16(ctx16):
     hx = sc.sampled_sigma_rows(I.h1, I.eri, 8, 8, x, rows)
     e_el = E[0] - I.e_core
     assert np.abs(hx - e_el * x[rows]).max() < p.r0
+
+
+def test_mixed_bf16x3_ground_state_n16(ctx16):
+    """The ground state of the largest space with its low-precision stage on
+    the tensor cores: the BF16x3 kernel runs the stage (kernel counters),
+    FP64 re-sync and verification bring the residual below r0, and the
+    oracle's sampled Slater-Condon rows confirm the eigenpair to r0."""
+    sbci, I, ctx = ctx16
+    p = sbci.params(prec=sbci.SBCI_BF16X3)
+    ctx.profile(False)
+    E, V, R, st = ctx.solve(1, p, want_vectors=True)
+    launches = ctx.profile_read()
+    assert st == sbci.SBCI_OK and R[0].converged
+    assert R[0].residual < p.r0
+    assert launches["sigma_gather_contract_bf16"][0] > 0
+    assert R[0].n_sigma_fp64 < R[0].n_sigma
+    x = V[0] / np.linalg.norm(V[0])
+    rows = np.random.default_rng(21).choice(ctx.ndet, 8, replace=False)
+    hx = sc.sampled_sigma_rows(I.h1, I.eri, 8, 8, x, rows)
+    assert np.abs(hx - (E[0] - I.e_core) * x[rows]).max() < p.r0
 
 
 def test_sigma_bf16x3_n16_sampled_rows(ctx16):
