@@ -9,19 +9,12 @@
 // The dropped D_lo W_lo term and the BF16 rounding of the lo parts leave a
 // relative error of about 2^-17 per product (TF32x3: 2^-21).
 //
-// Per tile of 128 determinants (persistent CTAs of 256 threads, each a
-// contiguous chunk of tiles):
-//   0. stage    where shared memory holds it, row Ia of c (the beta gathers
-//               of a tile's determinants (Ia, Ib) read c[Ia, Jb]) is staged
-//               once per alpha string; a chunk meets each string for about
-//               Nb / 128 consecutive tiles.  Rows of a tile that straddles
-//               into the next string read that string's row from global;
-//   1. gather   threads r and r + 128 each add half of the alpha links and
-//               half of the beta links of row r into one FP32 row of D in
-//               shared memory (row stride Kp + 1 words).  A pair receives at
-//               most one alpha and one beta term, and one FP32 addition is
-//               commutative, so the shared-memory atomic adds give the same D
-//               in any order and any split of the links;
+// Per tile of 128 determinants (persistent CTAs of 256 threads):
+//   1. gather   thread r adds the alpha links of row r, thread r + 128 the beta
+//               links, into one FP32 row of D in shared memory (row stride
+//               Kp + 1 words).  A pair receives at most one alpha and one beta
+//               term, and one FP32 addition is commutative, so the shared-memory
+//               atomic adds give the same D in any order;
 //   2. split    each thread reads half a row into registers; after a barrier
 //               it writes the BF16 hi and lo halves of that half row over the
 //               same bytes, as the K-major no-swizzle canonical operand A;
@@ -94,8 +87,7 @@ __global__ void k_split_W_bf(const double *W, int npair, int Kp, int Np, uint16_
 constexpr int kBfHalfMax = 72;
 
 __global__ void __launch_bounds__(kBfThreads, 1)
-    k_gather_contract_bf(SigmaArgs a, const uint16_t *Wbf, int Kp, int Np, uint32_t tmem_cols, int stage_row,
-                         int *status) {
+    k_gather_contract_bf(SigmaArgs a, const uint16_t *Wbf, int Kp, int Np, uint32_t tmem_cols, int *status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = Kp + 1;                          // FP32 row stride of the gather buffer
   float *Dst = reinterpret_cast<float *>(smem);  // 128 x S FP32, then the BF16 operand A (hi, lo)
@@ -106,7 +98,6 @@ __global__ void __launch_bounds__(kBfThreads, 1)
   uint16_t *Blo = Bhi + Np * Kp;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(Blo + Np * Kp);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-  float *srow = reinterpret_cast<float *>(mbar + 2);  // row Ia of c, Nb floats (stage_row != 0)
   const uint32_t sAhi = smem_u32(Ahi), sAlo = smem_u32(Alo), sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
   const uint32_t sbar = smem_u32(mbar);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -149,30 +140,11 @@ __global__ void __launch_bounds__(kBfThreads, 1)
   const int hq = Kp / 2;  // a multiple of 8
   const int q0 = half * hq;
   const long long ntiles = (a.ndet + kTcM - 1) / kTcM;
-  const long long chunk = (ntiles + gridDim.x - 1) / gridDim.x;
-  const long long t_first = (long long)blockIdx.x * chunk;
-  const long long t_last = t_first + chunk < ntiles ? t_first + chunk : ntiles;
-  // this thread's halves of the link lists
-  const int hla = a.nlink_a / 2, hlb = a.nlink_b / 2;
-  const int ea0 = half ? hla : 0, ea1 = half ? a.nlink_a : hla;
-  const int eb0 = half ? hlb : 0, eb1 = half ? a.nlink_b : hlb;
-  int s_ia = -1;  // the alpha string whose row of c is staged (block-uniform)
   uint32_t phase = 0;
   bool ok = true;
-  for (long long tile = t_first; tile < t_last && ok; ++tile) {
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long I = tile * kTcM + r;
     const bool valid = I < a.ndet;
-    // 0. the row of the tile's first alpha string; the previous tile's
-    //    readers of srow finished at its post-gather barrier, and the barrier
-    //    below publishes the new row
-    if (stage_row) {
-      const int ia0 = (int)(tile * kTcM / a.nb);
-      if (ia0 != s_ia) {
-        const float *src = cin + (size_t)ia0 * a.nb;
-        for (int j = tid; j < a.nb; j += blockDim.x) srow[j] = __ldg(src + j);
-        s_ia = ia0;
-      }
-    }
     // 1. zero the FP32 rows (each thread half a row), then gather with atomic adds
     for (int q = q0; q < q0 + hq; ++q) Dst[r * S + q] = 0.f;
     if (half == 0 && r == 0) Dst[kTcM * S - 1] = 0.f;  // (the padding word past the last row's Kp)
@@ -181,18 +153,17 @@ __global__ void __launch_bounds__(kBfThreads, 1)
       int ia, ib;
       split_det(I, a.nb, ia, ib);
       float *row = Dst + r * S;
-      auto add = [&](uint32_t v, float f) { atomicAdd(row + link_pair(v), link_neg(v) ? -f : f); };
-      const float *ccol = cin + ib;  // alpha links: c[Ja, Ib], coalesced across the tile's rows
-      for_links_pipelined<8, float>(
-          a.link_a + (size_t)ia * a.nlink_a + ea0, ea1 - ea0, 1,
-          [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); }, add);
-      const uint32_t *lb = a.link_bT + ib + (size_t)eb0 * a.nb;  // beta links: c[Ia, Jb]
-      if (stage_row && ia == s_ia) {
-        for_links_pipelined<8, float>(lb, eb1 - eb0, a.nb, [&](uint32_t v) { return srow[link_J(v)]; }, add);
+      if (half == 0) {
+        const float *ccol = cin + ib;
+        for_links_pipelined<8, float>(
+            a.link_a + (size_t)ia * a.nlink_a, a.nlink_a, 1,
+            [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+            [&](uint32_t v, float f) { atomicAdd(row + link_pair(v), link_neg(v) ? -f : f); });
       } else {
         const float *crow = cin + (size_t)ia * a.nb;
-        for_links_pipelined<8, float>(lb, eb1 - eb0, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
-                                      add);
+        for_links_pipelined<8, float>(
+            a.link_bT + ib, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+            [&](uint32_t v, float f) { atomicAdd(row + link_pair(v), link_neg(v) ? -f : f); });
       }
     }
     __syncthreads();
@@ -337,12 +308,7 @@ cudaError_t launch_gather_contract_bf(const SigmaArgs &a, const uint16_t *Wbf, i
   uint32_t cols;
   size_t smem;
   if (!bf_dims(a.npair, &Kp, &Np, &cols, &smem) || grid < 1) return cudaErrorInvalidValue;
-  // the staged row of c where it fits beside the operands (bf_grid set the
-  // function's limit to the device's opt-in maximum, 227 KB)
-  const size_t row = ((size_t)a.nb * 4 + 15) / 16 * 16;
-  const int stage = smem + row <= (size_t)227 * 1024 ? 1 : 0;
-  if (stage) smem += row;
-  k_gather_contract_bf<<<grid, kBfThreads, smem, s>>>(a, Wbf, Kp, Np, cols, stage, status);
+  k_gather_contract_bf<<<grid, kBfThreads, smem, s>>>(a, Wbf, Kp, Np, cols, status);
   return cudaGetLastError();
 }
 

@@ -153,20 +153,17 @@ __device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, co
 }
 
 // Steps 1 and 2 of a tile, row (threadIdx.x % 128) of D for determinant I
-// (a zero row when !valid): the gather in FP32 by two threads per row, thread
-// r taking the first half of the row's alpha links and of its beta links into
-// A, thread r + 128 the second halves into Alo (free until the split); then
-// D = A + Alo split in place, A <- tf32(D) and Alo <- tf32(D - tf32(D)), each
-// thread half a row.  A pair receives at most one alpha and one beta term, so
-// D[pair] is the one FP32 sum of those two terms whichever buffers they went
-// to.  256 threads.  Ends with the fences and the barrier that hand the
-// operand to the tensor core.
+// (a zero row when !valid): the gather in FP32, the alpha part into A and the
+// beta part into Alo (free until the split), each row owned by one thread;
+// then D = alpha part + beta part split in place, A <- tf32(D) and
+// Alo <- tf32(D - tf32(D)), each thread half a row.  256 threads.  Ends with
+// the fences and the barrier that hand the operand to the tensor core.
 __device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float *cin, long long I, bool valid,
                                                 int Kp, const TcSmem &sm) {
   const int tid = threadIdx.x;
   float *A = sm.A, *Alo = sm.Alo;
   const int row = tid & (kTcM - 1);  // determinant row of this thread
-  const int half = tid >> 7;         // 0: first halves of the link lists and of the row, 1: second halves
+  const int half = tid >> 7;         // 0: alpha links / first half, 1: beta links / second half
   const int q_lo = half ? (Kp / 8) * 4 : 0, q_hi = half ? Kp : (Kp / 8) * 4;
   float *mine = half ? Alo : A;
   for (int q = 0; q < Kp; q += 4)
@@ -174,16 +171,23 @@ __device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float 
   if (valid) {
     int ia, ib;
     split_det(I, a.nb, ia, ib);
-    const int hla = a.nlink_a / 2, hlb = a.nlink_b / 2;
-    const int ea0 = half ? hla : 0, ea1 = half ? a.nlink_a : hla;
-    const int eb0 = half ? hlb : 0, eb1 = half ? a.nlink_b : hlb;
-    auto add = [&](uint32_t v, float f) { mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f; };
-    const float *ccol = cin + ib;  // alpha links: c[Ja, Ib], coalesced across the tile's rows
-    for_links_pipelined<8, float>(a.link_a + (size_t)ia * a.nlink_a + ea0, ea1 - ea0, 1,
-                                  [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); }, add);
-    const float *crow = cin + (size_t)ia * a.nb;  // beta links: c[Ia, Jb]
-    for_links_pipelined<8, float>(a.link_bT + ib + (size_t)eb0 * a.nb, eb1 - eb0, a.nb,
-                                  [&](uint32_t v) { return __ldg(crow + link_J(v)); }, add);
+    if (half == 0) {
+      const uint32_t *la = a.link_a + (size_t)ia * a.nlink_a;
+      const float *ccol = cin + ib;
+      for_links_pipelined<8, float>(
+          la, a.nlink_a, 1, [&](uint32_t v) { return __ldg(ccol + (size_t)link_J(v) * a.nb); },
+          [&](uint32_t v, float f) {
+            mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
+    } else {
+      const uint32_t *lb = a.link_bT + ib;
+      const float *crow = cin + (size_t)ia * a.nb;
+      for_links_pipelined<8, float>(
+          lb, a.nlink_b, a.nb, [&](uint32_t v) { return __ldg(crow + link_J(v)); },
+          [&](uint32_t v, float f) {
+            mine[opnd_off(row, link_pair(v), Kp)] += link_neg(v) ? -f : f;
+          });
+    }
   }
   __syncthreads();
   for (int q = q_lo; q < q_hi; q += 4) {
