@@ -141,6 +141,7 @@ struct sbci_ctx {
   int nsm = 1;
   int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
+  int tcp_grid = 0;  // resident CTAs of its pipelined form (0: the plain kernel)
   int fc_grid = 0;  // CTAs of the column-fused sector kernel (0: unsupported shape or turned off)
   uint16_t *d_fc_link_a = nullptr;  // its 16-bit alpha links (J | pair << 8 | sign << 15)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
@@ -250,6 +251,7 @@ int gc_kid(const sbci_ctx *c, int prec) {
 cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
   switch (gc_kid(c, prec)) {
     case K_GCTC:
+      if (c->tcp_grid > 0) return launch_gather_contract_tcp(a, c->d_status, c->tcp_grid, c->stream);
       return launch_gather_contract_tc(a, c->d_status, c->tc_grid, c->stream);
     case K_GCTCLR:
       return launch_gather_contract_tclr(a, c->d_Wtclr, c->lr_rank, c->d_status, c->tclr_grid, c->stream);
@@ -2278,6 +2280,18 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaEventCreateWithFlags(&c->ev_fence, cudaEventDisableTiming), "cudaEventCreate"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
+  {  // the pipelined form of the tensor-core kernel where the plain one runs
+     // one CTA per SM (its operands take more than half of shared memory:
+     // npair > 55); SBCI_TC_PIPE=0 keeps the plain kernel, 1 takes the
+     // pipelined one for every size
+    const char *e = std::getenv("SBCI_TC_PIPE");
+    const bool off = e && std::strcmp(e, "0") == 0, all = e && std::strcmp(e, "1") == 0;
+    int Kp, Np;
+    uint32_t cols;
+    size_t smem = 0;
+    const bool one_cta = tc_dims(c->npair, &Kp, &Np, &cols, &smem) && smem > 113 * 1024;
+    if (c->tc_grid > 0 && !off && (one_cta || all)) c->tcp_grid = tcp_grid(c->npair, c->ndet, c->nsm);
+  }
   {  // SBCI_FUSED=0 keeps the tile kernel + scatter for singlet-sector TF32x3 steps
     const char *e = std::getenv("SBCI_FUSED");
     c->fc_grid = (e && e[0] == '0') ? 0 : fc_grid(c->npair, c->Na, c->Nb, c->sb.nlink, c->nsm);

@@ -188,6 +188,11 @@ int tc_grid(int npair, long long ndet, int num_sms);
 // Writes W (FP64 [npair_pad][npair]) as TF32 hi/lo operand B, [2][Np*Kp].
 cudaError_t launch_split_W(const double *W, int npair, int Kp, int Np, uint32_t *out, cudaStream_t s);
 cudaError_t launch_gather_contract_tc(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
+// The same contraction with the epilogue of one tile overlapped with the
+// gather and MMAs of the next (kernels_tcp.cu: 8 gather warps, 4 epilogue
+// warps, two TMEM accumulators); writes the same G.
+int tcp_grid(int npair, long long ndet, int num_sms);  // 0: unsupported shape
+cudaError_t launch_gather_contract_tcp(const SigmaArgs &a, int *status, int grid, cudaStream_t s);
 // Column-fused TF32x3 sigma of the singlet sector (kernels_loop.cu,
 // fused_body.cuh): gather, contraction and alpha-only scatter of one column
 // of A per CTA step, G kept in shared memory; device-controlled mode only

@@ -152,12 +152,23 @@ __device__ __forceinline__ void tc_load_B(const SigmaArgs &a, int Kp, int Np, co
   fence_after();
 }
 
+// The barrier of the threads that gather a tile: the whole CTA, or (kAll =
+// false) the first 256 threads on named barrier 1, in a CTA whose other warps
+// have work of their own.
+template <bool kAll>
+__device__ __forceinline__ void tc_sync() {
+  if (kAll) __syncthreads();
+  else asm volatile("bar.sync 1, 256;\n" ::: "memory");
+}
+
 // Steps 1 and 2 of a tile, row (threadIdx.x % 128) of D for determinant I
 // (a zero row when !valid): the gather in FP32, the alpha part into A and the
 // beta part into Alo (free until the split), each row owned by one thread;
 // then D = alpha part + beta part split in place, A <- tf32(D) and
-// Alo <- tf32(D - tf32(D)), each thread half a row.  256 threads.  Ends with
-// the fences and the barrier that hand the operand to the tensor core.
+// Alo <- tf32(D - tf32(D)), each thread half a row.  256 threads, whose
+// barrier is tc_sync<kAll>.  Ends with the fences and the barrier that hand
+// the operand to the tensor core.
+template <bool kAll = true>
 __device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float *cin, long long I, bool valid,
                                                 int Kp, const TcSmem &sm) {
   const int tid = threadIdx.x;
@@ -189,7 +200,7 @@ __device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float 
           });
     }
   }
-  __syncthreads();
+  tc_sync<kAll>();
   for (int q = q_lo; q < q_hi; q += 4) {
     float4 *p = reinterpret_cast<float4 *>(A + opnd_off(row, q, Kp));
     float4 *pl = reinterpret_cast<float4 *>(Alo + opnd_off(row, q, Kp));
@@ -209,7 +220,7 @@ __device__ __forceinline__ void tc_gather_split(const SigmaArgs &a, const float 
   }
   fence_async_smem();
   fence_before();
-  __syncthreads();
+  tc_sync<kAll>();
   fence_after();
 }
 
