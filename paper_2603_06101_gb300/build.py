@@ -23,8 +23,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # The SB step loop is compiled without multiply-add contraction: every fused
 # multiply-add there is an explicit fma(), so the one-solve and the batched
-# kernels round identically whatever the compiler inlines or schedules.
-FILE_FLAGS = {"kernels_loop.cu": ["-fmad=false"]}
+# kernels round identically whatever the compiler inlines or schedules.  The
+# SBCI2 pair controller likewise (no contraction, as in the host pair step on
+# x86-64).
+FILE_FLAGS = {"kernels_loop.cu": ["-fmad=false"], "kernels_sbci2.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

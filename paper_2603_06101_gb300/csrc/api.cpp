@@ -29,6 +29,7 @@
 #include "ctl.h"
 #include "batch.h"
 #include "lowrank.h"
+#include "pair_ctl.h"
 #include "sbci_internal.h"
 #include "step.h"
 
@@ -60,14 +61,14 @@ namespace {
 // Per-kernel launch counts (always) and CUDA-event times on the context stream
 // (when profiling is enabled).
 enum Kid { K_GC = 0, K_SC, K_UPD, K_PROJ, K_RED, K_LIN, K_DOTS, K_DIAG, K_GCTC, K_SF,
-           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_GCBF, K_GCTCLR, K_COUNT };
+           K_DAVD, K_DAVC, K_DAVP, K_GCOS, K_GCLR, K_FC, K_GCBF, K_GCTCLR, K_PAIR, K_COUNT };
 const char *const kKidName[K_COUNT] = {"sigma_gather_contract", "sigma_scatter", "sb_update",
                                        "sb_project", "reduce", "lincomb", "dots", "diagonal",
                                        "sigma_gather_contract_tc", "sigma_symfinish",
                                        "davidson_dots", "davidson_combine", "davidson_precond",
                                        "sigma_gather_contract_os", "sigma_gather_contract_lr",
                                        "sigma_fused_column", "sigma_gather_contract_bf16",
-                                       "sigma_gather_contract_tc_lr"};
+                                       "sigma_gather_contract_tc_lr", "sbci2_pair_ctl"};
 
 struct Prof {
   bool on = false;
@@ -142,6 +143,7 @@ struct sbci_ctx {
   int device = -1;  // the CUDA device the context was created on
   int tc_grid = 0;  // resident CTAs of the tensor-core kernel (0: unsupported shape)
   int tcp_grid = 0;  // resident CTAs of its pipelined form (0: the plain kernel)
+  bool sbci2_device = false;  // SBCI_SBCI2_DEVICE=1: SBCI2 pair steps on the device controller
   int fc_grid = 0;  // CTAs of the column-fused sector kernel (0: unsupported shape or turned off)
   uint16_t *d_fc_link_a = nullptr;  // its 16-bit alpha links (J | pair << 8 | sign << 15)
   double *d_tmp_in = nullptr, *d_tmp_out = nullptr;  // staging for host sigma calls
@@ -266,10 +268,8 @@ cudaError_t launch_gc(const sbci_ctx *c, const SigmaArgs &a, int prec) {
   }
 }
 
-// sigma of one device vector in the given precision (out = H in).
-sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
-  RET(check_prec(c, prec));
-  RET(ensure_G(c, prec));
+// Arguments of a plain (not device-controlled) sigma out = H in.
+SigmaArgs plain_sigma_args(const sbci_ctx *c, const double *in, double *out) {
   SigmaArgs a{};
   a.c = in;
   a.sigma = out;
@@ -289,6 +289,14 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   a.ndet = c->ndet;
   a.partials = c->d_partials;  // (no dots: dot_u all null)
   a.grid = scatter_grid(c->ndet, c->nsm);
+  return a;
+}
+
+// sigma of one device vector in the given precision (out = H in).
+sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
+  RET(check_prec(c, prec));
+  RET(ensure_G(c, prec));
+  SigmaArgs a = plain_sigma_args(c, in, out);
   const int p32 = (prec == SBCI_FP64) ? 0 : 1;
   if (prec == SBCI_TF32X3 || prec == SBCI_BF16X3) {  // the tensor-core gathers read an FP32 copy
     if (!c->d_cf) RET(dmalloc(&c->d_cf, (size_t)c->ndet));
@@ -1613,9 +1621,11 @@ struct PairVecs {
   double *x[2], *X[2], *y[2], *Y[2], *z[2], *Z[2];  // z holds z' between steps
 };
 
-sbci_status sbci2_pair(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2], int max_cycle2) {
+// Algorithm 2 lines 1-3 for the pair (alpha, alpha + 1): the start vectors
+// projected against the stored states (Eqs. S77-S80), normalised, and the
+// residuals z'_0 = X_0 - E_0 x_0.
+sbci_status pair_start(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, const double E[2]) {
   Solver &s = c->s;
-  const sbci_params &p = s.p;
   const long long N = c->ndet;
   std::vector<double> r;
   const double *xc = s.xc;
@@ -1651,29 +1661,72 @@ sbci_status sbci2_pair(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, doub
     RET(dav_combine(vs, {P.x[0], P.x[1], P.X[0], P.X[1]}, {P.x[0], P.x[1], P.X[0], P.X[1]}, co));
   }
   // line 3: z'_0 = X_0 - E_0 x_0
-  RET(dav_combine(vs, {P.z[0], P.z[1]}, {P.x[0], P.x[1], P.X[0], P.X[1]},
-                  {-E[0], 0.0, 0.0, -E[1], 1.0, 0.0, 0.0, 1.0}));
+  return dav_combine(vs, {P.z[0], P.z[1]}, {P.x[0], P.x[1], P.X[0], P.X[1]},
+                     {-E[0], 0.0, 0.0, -E[1], 1.0, 0.0, 0.0, 1.0});
+}
+
+// The lower state of the pair used its H-product budget (Q8): stored
+// unconverged; the normalised upper vector becomes the next lower one.
+sbci_status pair_finish_cap(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2], long long sigma,
+                            int nstep, const int restarts[4]) {
+  Solver &s = c->s;
+  const long long N = c->ndet;
+  std::vector<double> r;
+  RET(dav_dots(vs, {P.x[0], P.x[1]}, {P.x[0], P.x[1]}, r));
+  const double n0 = std::sqrt(r[0]), n1 = std::sqrt(r[1]);
+  RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / n0}));
+  s.Ec.push_back(E[0]);
+  sbci_report &rep = s.rep[alpha];
+  rep = sbci_report{};
+  rep.energy = E[0] + c->e_core;
+  rep.converged = 0;
+  rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
+  rep.n_step = nstep;
+  for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
+  s.any_unconverged = 1;
+  RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / n1, 0.0, 0.0, 1.0 / n1}));
+  E[0] = E[1];
+  return SBCI_OK;
+}
+
+// The lower state converged (Eq. S127) at Ritz values w, with |z'^a| = dz
+// and |x^a|, |x^b| = nx: stored; the normalised upper vector becomes the next
+// lower one.
+sbci_status pair_finish_converged(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2],
+                                  const double w[2], double dz, const double nx[2], long long sigma, int nstep,
+                                  const int restarts[4]) {
+  Solver &s = c->s;
+  const long long N = c->ndet;
+  RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / nx[0]}));
+  s.Ec.push_back(w[0]);
+  sbci_report &rep = s.rep[alpha];
+  rep = sbci_report{};
+  rep.energy = w[0] + c->e_core;
+  rep.residual = dz;
+  rep.converged = 1;
+  rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
+  rep.n_step = nstep;
+  for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
+  RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / nx[1], 0.0, 0.0, 1.0 / nx[1]}));
+  E[0] = w[1];
+  return SBCI_OK;
+}
+
+// The pair loop driven from the host (the default): one round trip per step
+// for the dots and one for the norms, the small eigen-problems on the host.
+sbci_status sbci2_pair_host(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2], int max_cycle2) {
+  Solver &s = c->s;
+  const sbci_params &p = s.p;
+  const long long N = c->ndet;
+  std::vector<double> r;
+  const double *xc = s.xc;
+  auto xcv = [&](int j) { return xc + (size_t)j * N; };
+  RET(pair_start(c, vs, P, alpha, E));
   bool first = true;
   int t = 0, nstep = 0, restarts[4] = {0, 0, 0, 0};
   long long sigma = 0;
   for (;;) {
-    sbci_report &rep = s.rep[alpha];
-    if (sigma >= p.max_sigma) {  // Q8: the lower state ends unconverged
-      RET(dav_dots(vs, {P.x[0], P.x[1]}, {P.x[0], P.x[1]}, r));
-      const double n0 = std::sqrt(r[0]), n1 = std::sqrt(r[1]);
-      RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / n0}));
-      s.Ec.push_back(E[0]);
-      rep = sbci_report{};
-      rep.energy = E[0] + c->e_core;
-      rep.converged = 0;
-      rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
-      rep.n_step = nstep;
-      for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
-      s.any_unconverged = 1;
-      RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / n1, 0.0, 0.0, 1.0 / n1}));
-      E[0] = E[1];
-      return SBCI_OK;
-    }
+    if (sigma >= p.max_sigma) return pair_finish_cap(c, vs, P, alpha, E, sigma, nstep, restarts);  // Q8
     const double E_pre = alpha == 0 ? E[0] : s.Ec[0];  // Q3
     for (int i = 0; i < 2; ++i) {  // Eqs. S81 / S101
       RET(timed(c, K_DAVP, [&] {
@@ -1798,19 +1851,8 @@ sbci_status sbci2_pair(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, doub
     if (dE < p.eps0 && dz < p.r0) {  // Eq. S99 / S127
       rec.event = 1;
       s.trace.push_back(rec);
-      RET(dav_combine(vs, {s.xc + (size_t)alpha * N}, {P.x[0]}, {1.0 / nx0}));
-      s.Ec.push_back(pc.w[0]);
-      rep = sbci_report{};
-      rep.energy = pc.w[0] + c->e_core;
-      rep.residual = dz;
-      rep.converged = 1;
-      rep.n_sigma = rep.n_sigma_fp64 = (int)sigma;
-      rep.n_step = nstep;
-      for (int i = 0; i < 4; ++i) rep.n_restart[i] = restarts[i];
-      // the normalised upper vector starts the next pair (or the last state)
-      RET(dav_combine(vs, {P.x[0], P.X[0]}, {P.x[1], P.X[1]}, {1.0 / nx1, 0.0, 0.0, 1.0 / nx1}));
-      E[0] = pc.w[1];
-      return SBCI_OK;
+      const double nx[2] = {nx0, nx1};
+      return pair_finish_converged(c, vs, P, alpha, E, pc.w, dz, nx, sigma, nstep, restarts);
     }
     int cause = -1;  // Section S2.5
     if ((std::fabs(pc.B[0][0]) < p.b_th || std::fabs(pc.B[1][1]) < p.b_th) && dE < p.eps1) cause = 0;
@@ -1836,6 +1878,228 @@ sbci_status sbci2_pair(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, doub
     s.trace.push_back(rec);
     first = false;
     ++t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The pair loop on the device: one step = preconditioner and projection of
+// the residuals, two FP64 H-products, the dots of the step basis, the pair
+// controller (pair_ctl.h: the 6x6 canonical orthogonalisation and subspace
+// eigen-problem on one GPU thread), one combination with the coefficients it
+// wrote, the norms, the controller's decision and the rescaling of a restart.
+// The steps run as one CUDA-graph while-loop; the host acts only when the
+// lower state converged or used its budget.  Selected by SBCI_SBCI2_DEVICE=1
+// (read when a context is created).  On GB300 it is the slower loop: the two
+// FP64 6x6 Jacobi solves of a step on one GPU thread (FP64 at two lanes per
+// SM and clock) take longer than the host round trips they replace (H10:
+// 112 ms against 52 ms per 4-state solve), so the host-driven loop is the
+// default.
+
+
+// Device buffers of the pair controller: its state and its trace ring.
+struct PairDev {
+  PairCtl *d = nullptr;
+  sbci_trace_record *trace = nullptr;
+  int trace_cap = 0;
+  ~PairDev() {
+    if (d) cudaFree(d);
+    if (trace) cudaFree(trace);
+  }
+};
+
+// The kernels of one pair step (cond: the graph's loop handle, 0 outside a
+// graph; timing: count and time each launch, not in a capture).
+sbci_status pair_body(sbci_ctx *c, VecScratch &vs, PairVecs &P, PairCtl *d, int alpha, unsigned long long cond,
+                      bool timing) {
+  Solver &s = c->s;
+  const sbci_params &p = s.p;
+  const long long N = c->ndet;
+  cudaStream_t st = c->stream;
+  auto L = [&](int kid, auto &&f) -> sbci_status {
+    if (timing) return timed(c, kid, f);
+    CK(f());
+    return SBCI_OK;
+  };
+  // Eqs. S81 / S101, shift Q3
+  const double *shift = alpha == 0 ? &d->E[0] : &d->Ec0;
+  for (int i = 0; i < 2; ++i) {
+    RET(L(K_DAVP, [&] { return launch_dav_precond_dev(P.z[i], P.z[i], c->d_diag, shift, p.guard, N, c->nsm, st); }));
+    if (p.sector) RET(L(K_DAVP, [&] { return launch_symmetrize(P.z[i], c->Na, st); }));
+  }
+  if (alpha > 0) {  // against the stored states
+    std::vector<const double *> u, v, in{P.z[0], P.z[1]};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < alpha; ++j) {
+        u.push_back(s.xc + (size_t)j * N);
+        v.push_back(P.z[i]);
+      }
+    for (int j = 0; j < alpha; ++j) in.push_back(s.xc + (size_t)j * N);
+    RET(L(K_DAVD, [&] { return launch_dav_dots(u.data(), v.data(), 2 * alpha, N, vs.partials, vs.grid, st); }));
+    RET(L(K_RED, [&] { return launch_reduce(vs.partials, vs.grid, 0, 2 * alpha, vs.d_res, st); }));
+    RET(L(K_PAIR, [&] { return launch_pair_proj_coef(d, vs.d_res, st); }));
+    double *out[2] = {P.z[0], P.z[1]};
+    RET(L(K_DAVC, [&] {
+      return launch_dav_combine_dev(out, 2, in.data(), (int)in.size(), d->proj, nullptr, N, c->nsm, st);
+    }));
+  }
+  for (int i = 0; i < 2; ++i) {  // Eqs. S82 / S102
+    const SigmaArgs a = plain_sigma_args(c, P.z[i], P.Z[i]);
+    RET(L(gc_kid(c, SBCI_FP64), [&] { return launch_gc(c, a, SBCI_FP64); }));
+    RET(L(K_SC, [&] { return launch_scatter(a, 0, st); }));
+  }
+  // overlap and T of the basis (x^a, x^b, y^a, y^b, z^a, z^b)
+  const double *Bv[6] = {P.x[0], P.x[1], P.y[0], P.y[1], P.z[0], P.z[1]};
+  const double *HB[6] = {P.X[0], P.X[1], P.Y[0], P.Y[1], P.Z[0], P.Z[1]};
+  std::vector<const double *> u, v;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) {
+      u.push_back(Bv[a]);
+      v.push_back(Bv[b]);
+    }
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) {
+      u.push_back(Bv[a]);
+      v.push_back(HB[b]);
+    }
+  RET(L(K_DAVD, [&] { return launch_dav_dots(u.data(), v.data(), kPairDots, N, vs.partials, vs.grid, st); }));
+  RET(L(K_RED, [&] { return launch_reduce(vs.partials, vs.grid, 0, kPairDots, vs.d_res, st); }));
+  RET(L(K_PAIR, [&] { return launch_pair_after_dots(d, vs.d_res, st); }));
+  {  // x, X (Q9), y, Y (Eqs. S94-S95 / S122-S123), z' (Eqs. S98, S100 / S126, S128)
+    const double *in[kPairIn] = {P.x[0], P.x[1], P.y[0], P.y[1], P.z[0], P.z[1],
+                                 P.X[0], P.X[1], P.Y[0], P.Y[1], P.Z[0], P.Z[1]};
+    double *out[kPairOut] = {P.x[0], P.x[1], P.X[0], P.X[1], P.y[0], P.y[1], P.Y[0], P.Y[1], P.z[0], P.z[1]};
+    RET(L(K_DAVC, [&] {
+      return launch_dav_combine_dev(out, kPairOut, in, kPairIn, d->comb, nullptr, N, c->nsm, st);
+    }));
+  }
+  const double *nu[4] = {P.z[0], P.z[1], P.x[0], P.x[1]};
+  RET(L(K_DAVD, [&] { return launch_dav_dots(nu, nu, 4, N, vs.partials, vs.grid, st); }));
+  RET(L(K_RED, [&] { return launch_reduce(vs.partials, vs.grid, 0, 4, vs.d_res, st); }));
+  RET(L(K_PAIR, [&] { return launch_pair_decide(d, vs.d_res, cond, st); }));
+  // a restart (Q7): x, X normalised, z' scaled to k / |x|
+  double *sv[6] = {P.x[0], P.x[1], P.X[0], P.X[1], P.z[0], P.z[1]};
+  const double *si[6] = {P.x[0], P.x[1], P.X[0], P.X[1], P.z[0], P.z[1]};
+  RET(L(K_DAVC, [&] { return launch_dav_combine_dev(sv, 6, si, 6, d->scale, &d->restart, N, c->nsm, st); }));
+  return SBCI_OK;
+}
+
+// Kernels a graph-run pair step launched (the counts the timed path keeps).
+void count_pair_bodies(sbci_ctx *c, int alpha, long long steps) {
+  Prof &pf = c->prof;
+  const long long sec = c->s.p.sector ? 2 : 0;
+  pf.launches[K_DAVP] += (2 + sec) * steps;
+  pf.launches[K_DAVD] += (2 + (alpha > 0)) * steps;
+  pf.launches[K_RED] += (2 + (alpha > 0)) * steps;
+  pf.launches[K_PAIR] += (2 + (alpha > 0)) * steps;
+  pf.launches[K_DAVC] += (2 + (alpha > 0)) * steps;
+  pf.launches[gc_kid(c, SBCI_FP64)] += 2 * steps;
+  pf.launches[K_SC] += 2 * steps;
+}
+
+sbci_status sbci2_pair_dev(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, double E[2], int max_cycle2,
+                           PairDev &pd) {
+  Solver &s = c->s;
+  const sbci_params &p = s.p;
+  RET(pair_start(c, vs, P, alpha, E));
+  const int none[4] = {0, 0, 0, 0};
+  if (p.max_sigma <= 0) return pair_finish_cap(c, vs, P, alpha, E, 0, 0, none);  // Q8 before any step
+  if (!pd.d) {
+    CK(cudaMalloc((void **)&pd.d, sizeof(PairCtl)));
+    pd.trace_cap = p.max_sigma / 2 + 16;  // two H-products per step
+    CK(cudaMalloc((void **)&pd.trace, sizeof(sbci_trace_record) * pd.trace_cap));
+  }
+  PairCtl h{};
+  h.eps0 = p.eps0;
+  h.r0 = p.r0;
+  h.b_th = p.b_th;
+  h.eps1 = p.eps1;
+  h.x_th1 = p.x_th1;
+  h.x_th2 = p.x_th2;
+  h.r1 = p.r1;
+  h.Ec0 = alpha > 0 ? s.Ec[0] : 0.0;
+  h.alpha = alpha;
+  h.max_sigma = p.max_sigma;
+  h.max_cycle2 = max_cycle2;
+  h.trace_cap = pd.trace_cap;
+  h.E[0] = E[0];
+  h.E[1] = E[1];
+  h.first = 1;
+  h.trace = pd.trace;
+  CK(cudaMemcpyAsync(pd.d, &h, sizeof(PairCtl), cudaMemcpyHostToDevice, c->stream));
+  RET(ensure_G(c, SBCI_FP64));
+  if (use_graphs(c)) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hd;
+    cudaGraphExec_t ex = nullptr;
+    auto fail = [&](sbci_status stt) {
+      if (ex) cudaGraphExecDestroy(ex);
+      cudaGraphDestroy(g);
+      return stt;
+    };
+    if (cudaGraphConditionalHandleCreate(&hd, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+      return fail(SBCI_ERR_CUDA);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) return fail(SBCI_ERR_CUDA);
+    if (cudaStreamBeginCaptureToGraph(c->stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail(SBCI_ERR_CUDA);
+    const sbci_status bst = pair_body(c, vs, P, pd.d, alpha, (unsigned long long)hd, false);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->stream, &captured);
+    if (bst != SBCI_OK) return fail(bst);
+    if (ce != cudaSuccess || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess ||
+        cudaGraphLaunch(ex, c->stream) != cudaSuccess) {
+      set_error("SBCI2: the pair-step graph could not be built or launched");
+      return fail(SBCI_ERR_CUDA);
+    }
+    CK(cudaMemcpyAsync(&h, pd.d, sizeof(PairCtl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    fail(SBCI_OK);
+    count_pair_bodies(c, alpha, h.nstep);
+  } else {  // one step at a time (per-kernel timing)
+    for (;;) {
+      RET(pair_body(c, vs, P, pd.d, alpha, 0, true));
+      CK(cudaMemcpyAsync(&h, pd.d, sizeof(PairCtl), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if (h.halt != PH_RUN) break;
+    }
+  }
+  {  // a bounded MMA wait of the H-products that ran out
+    int status = 0;
+    CK(cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+      set_error("a bounded device wait ran out (tensor-core MMA completion)");
+      return SBCI_ERR_TIMEOUT;
+    }
+  }
+  if (h.ntrace > 0) {
+    const int n = std::min(h.ntrace, h.trace_cap);
+    std::vector<sbci_trace_record> tr(n);
+    CK(cudaMemcpy(tr.data(), pd.trace, sizeof(sbci_trace_record) * n, cudaMemcpyDeviceToHost));
+    s.trace.insert(s.trace.end(), tr.begin(), tr.end());
+  }
+  E[0] = h.E[0];  // the pair's energies after its last completed step
+  E[1] = h.E[1];
+  switch (h.halt) {
+    case PH_CONVERGED:
+      return pair_finish_converged(c, vs, P, alpha, E, h.w, h.dz, h.nx, h.sigma, h.nstep, h.restarts);
+    case PH_CAP:
+      return pair_finish_cap(c, vs, P, alpha, E, h.sigma, h.nstep, h.restarts);
+    case PH_UNDEF:
+      set_error("SBCI2: the pair step is undefined (subspace rank below 2)");
+      return SBCI_ERR_NUMERIC;
+    case PH_BOUND:
+      set_error("SBCI2: the pair loop ran past its step bound without reaching the H-product cap");
+      return SBCI_ERR_NUMERIC;
+    default:
+      set_error("non-finite dot product in a device reduction (SBCI2)");
+      return SBCI_ERR_NUMERIC;
   }
 }
 
@@ -1908,7 +2172,13 @@ sbci_status sbci2_run(sbci_ctx *c, int k, int max_cycle2) {
     RET(buf.get(c, &P.Y[i]));
     RET(buf.get(c, &P.z[i]));
     RET(buf.get(c, &P.Z[i]));
+    // y, Y enter the device loop's combination with zero coefficients on
+    // first-step paths: they start as zeros, not as uninitialised memory
+    CK(cudaMemsetAsync(P.y[i], 0, sizeof(double) * N, c->stream));
+    CK(cudaMemsetAsync(P.Y[i], 0, sizeof(double) * N, c->stream));
   }
+  const bool on_device = c->sbci2_device;
+  PairDev pd;
   double E[2] = {w[0], k > 1 ? w[1] : 0.0};
   RET(dav_combine(vs, {P.x[0], P.X[0]}, {xs[0], Xs[0]}, {1.0, 0.0, 0.0, 1.0}));
   for (int alpha = 0; alpha + 1 < k; ++alpha) {
@@ -1936,7 +2206,8 @@ sbci_status sbci2_run(sbci_ctx *c, int k, int max_cycle2) {
       RET(dav_dots(vs, {P.x[1]}, {P.X[1]}, r));
       E[1] = r[0];
     }
-    RET(sbci2_pair(c, vs, P, alpha, E, max_cycle2));
+    if (on_device) RET(sbci2_pair_dev(c, vs, P, alpha, E, max_cycle2, pd));
+    else RET(sbci2_pair_host(c, vs, P, alpha, E, max_cycle2));
   }
   // the highest state: SBCI1 from the last pair's normalised upper vector
   // (Fig. 1B), projected against the stored states (Eqs. S4-S7)
@@ -2280,6 +2551,10 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(cuda_ok(cudaEventCreateWithFlags(&c->ev_fence, cudaEventDisableTiming), "cudaEventCreate"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
+  {
+    const char *e = std::getenv("SBCI_SBCI2_DEVICE");
+    c->sbci2_device = e && std::strcmp(e, "1") == 0;
+  }
   {  // the pipelined form of the tensor-core kernel where the plain one runs
      // one CTA per SM (its operands take more than half of shared memory:
      // npair > 55); SBCI_TC_PIPE=0 keeps the plain kernel, 1 takes the

@@ -103,6 +103,48 @@ __global__ void k_dav_precond(double *out, const double *in, const double *diag,
   }
 }
 
+// The combination with its coefficients in device memory (coef[q * kDavMaxOut
+// + j], written by a controller kernel), skipped when *active == 0: the same
+// per-element arithmetic as k_dav_combine.
+struct DavCombDev {
+  const double *in[kDavMaxIn];
+  double *out[kDavMaxOut];
+  int nin, nout;
+};
+
+__global__ void __launch_bounds__(kDavThreads) k_dav_combine_dev(const __grid_constant__ DavCombDev C,
+                                                                 const double *coef, const int *active,
+                                                                 long long n) {
+  if (active && *active == 0) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double acc[kDavMaxOut];
+#pragma unroll
+    for (int j = 0; j < kDavMaxOut; ++j) acc[j] = 0.0;
+    for (int q = 0; q < C.nin; ++q) {
+      const double x = C.in[q][i];
+#pragma unroll
+      for (int j = 0; j < kDavMaxOut; ++j)
+        if (j < C.nout) acc[j] += coef[q * kDavMaxOut + j] * x;
+    }
+#pragma unroll
+    for (int j = 0; j < kDavMaxOut; ++j)
+      if (j < C.nout) C.out[j][i] = acc[j];
+  }
+}
+
+// k_dav_precond with the shift read from device memory.
+__global__ void k_dav_precond_dev(double *out, const double *in, const double *diag, const double *shift,
+                                  double guard, long long n) {
+  const double sh = *shift;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double d = diag[i] - sh;
+    if (fabs(d) < guard) d = d < 0.0 ? -guard : guard;
+    out[i] = in[i] / d;
+  }
+}
+
 int dav_grid(long long n, int cap) {
   long long g = (n + kDavThreads - 1) / kDavThreads;
   if (g > cap) g = cap;
@@ -151,6 +193,24 @@ cudaError_t launch_dav_combine(double *const *out, int nout, const double *const
 cudaError_t launch_dav_precond(double *out, const double *in, const double *diag, double shift, double guard,
                                long long n, int nsm, cudaStream_t s) {
   k_dav_precond<<<dav_grid(n, 8 * nsm), kDavThreads, 0, s>>>(out, in, diag, shift, guard, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dav_combine_dev(double *const *out, int nout, const double *const *in, int nin,
+                                   const double *coef, const int *active, long long n, int nsm, cudaStream_t s) {
+  if (nin < 1 || nin > kDavMaxIn || nout < 1 || nout > kDavMaxOut) return cudaErrorInvalidValue;
+  DavCombDev C{};
+  C.nin = nin;
+  C.nout = nout;
+  for (int q = 0; q < nin; ++q) C.in[q] = in[q];
+  for (int j = 0; j < nout; ++j) C.out[j] = out[j];
+  k_dav_combine_dev<<<dav_grid(n, 8 * nsm), kDavThreads, 0, s>>>(C, coef, active, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dav_precond_dev(double *out, const double *in, const double *diag, const double *shift,
+                                   double guard, long long n, int nsm, cudaStream_t s) {
+  k_dav_precond_dev<<<dav_grid(n, 8 * nsm), kDavThreads, 0, s>>>(out, in, diag, shift, guard, n);
   return cudaGetLastError();
 }
 

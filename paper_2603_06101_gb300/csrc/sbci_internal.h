@@ -274,6 +274,21 @@ cudaError_t launch_dav_combine(double *const *out, int nout, const double *const
 // out <- in / guarded(D - shift) (out may be in)
 cudaError_t launch_dav_precond(double *out, const double *in, const double *diag, double shift, double guard,
                                long long n, int nsm, cudaStream_t s);
+// The same two with device-resident coefficients / shift (written by the
+// SBCI2 pair controller): coef[q * kDavMaxOut + j]; the combination does
+// nothing while *active == 0 (active may be null).
+cudaError_t launch_dav_combine_dev(double *const *out, int nout, const double *const *in, int nin,
+                                   const double *coef, const int *active, long long n, int nsm, cudaStream_t s);
+cudaError_t launch_dav_precond_dev(double *out, const double *in, const double *diag, const double *shift,
+                                   double guard, long long n, int nsm, cudaStream_t s);
+
+// SBCI2 pair controller kernels (kernels_sbci2.cu, pair_ctl.h), one thread
+// each, on the device state of one pair: res holds the reduced dots of the
+// step (launch_reduce), cond the graph's while-loop handle (0: none).
+struct PairCtl;
+cudaError_t launch_pair_proj_coef(PairCtl *ctl, const double *res, cudaStream_t s);
+cudaError_t launch_pair_after_dots(PairCtl *ctl, const double *res, cudaStream_t s);
+cudaError_t launch_pair_decide(PairCtl *ctl, const double *res, unsigned long long cond, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small dense symmetric eigen-solver (cyclic Jacobi), ascending eigenvalues,

@@ -7,7 +7,16 @@ both runs take the same decisions (restart causes, convergence).  Where two
 Ritz values of a step coincide (a degenerate pair), the two eigen-solvers may
 return different rotations of that pair and the runs then part ways; energies
 are compared as sets.
+
+The pair steps are host-driven by default; SBCI_SBCI2_DEVICE=1 runs them on
+the device controller (a CUDA-graph loop, the 6x6 subspace problems solved on
+one GPU thread, the host pair step's arithmetic without fused multiply-adds).
+The two loops must take the same leading steps (Ritz energies within 1e-9,
+same events, as for the oracle: the host build may fuse multiply-adds where
+the device one does not) and reach the same energies (1e-8).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -132,3 +141,65 @@ def test_one_state_is_sbci1_and_bad_arguments():
         with pytest.raises(sbci.SbciError) as e:
             ctx.solve_sbci2(2, sbci.params(**kw), max_cycle2=mc)
         assert e.value.status == sbci.SBCI_ERR_INVALID
+
+
+def _ctx_env(sbci, I, name, value):
+    old = os.environ.get(name)
+    os.environ[name] = value
+    try:
+        return sbci.Context.from_integrals(I)
+    finally:
+        if old is None:
+            del os.environ[name]
+        else:
+            os.environ[name] = old
+
+
+@pytest.mark.parametrize("key,k,sector", [(("chain", 8, 1.3), 3, 1), (("chain", 6, 1.0), 4, 0)])
+def test_device_pair_loop_same_as_host_loop(key, k, sector):
+    """Device-driven and host-driven pair loops: the same leading steps
+    (state, step, event, Ritz energy within 1e-9), the same energies within
+    1e-8, the oracle's energies; the device run launched the pair controller,
+    the host run did not."""
+    sbci = require_lib()
+    I = make_integrals(key)
+    p = sbci.params(sector=sector)
+    runs = {}
+    for dev in ("1", "0"):
+        ctx = _ctx_env(sbci, I, "SBCI_SBCI2_DEVICE", dev)
+        ctx.profile(False)
+        E, _, R, st = ctx.solve_sbci2(k, p)
+        assert st == sbci.SBCI_OK and all(r.converged for r in R)
+        runs[dev] = (E, ctx.trace(), ctx.profile_read()["sbci2_pair_ctl"][0])
+        ctx.close()
+    (Ed, trd, nd), (Eh, trh, nh) = runs["1"], runs["0"]
+    assert nd > 0 and nh == 0
+    n = 0
+    for a, b in zip(trd, trh):
+        if (a.state, a.t, a.event) != (b.state, b.t, b.event) or abs(a.energy - b.energy) >= 1e-9:
+            break
+        n += 1
+    if sector == 1:  # (H6's degenerate start pair in sector 0: energies only, as for the oracle)
+        assert n >= 20
+    assert np.abs(np.sort(Ed) - np.sort(Eh)).max() < 1e-8
+    run, res = _oracle(key, k, sector=sector)
+    Eo = np.array([r.energy for r in res]) + I.e_core
+    assert np.abs(np.sort(Ed) - np.sort(Eo)).max() < 1e-8
+
+
+def test_device_pair_loop_timed_path():
+    """Under per-kernel timing the device pair loop runs one step per host
+    iteration (no graph); it reaches the graph loop's energies."""
+    sbci = require_lib()
+    key = ("chain", 6, 1.0)
+    I = make_integrals(key)
+    p = sbci.params(sector=1)
+    ctx = _ctx_env(sbci, I, "SBCI_SBCI2_DEVICE", "1")
+    E0, _, _, st0 = ctx.solve_sbci2(3, p)
+    ctx.profile(True)
+    E1, _, R, st1 = ctx.solve_sbci2(3, p)
+    stats = ctx.profile_read()
+    ctx.profile(False)
+    assert st0 == st1 == sbci.SBCI_OK
+    assert stats["sbci2_pair_ctl"][0] > 0 and stats["sbci2_pair_ctl"][1] > 0.0
+    assert np.abs(E0 - E1).max() <= 1e-12
