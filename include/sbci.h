@@ -442,8 +442,23 @@ void sbci_server_destroy(sbci_server *sv);
 /* Thread-local message of the last error in this thread ("" if none). */
 const char *sbci_last_error(void);
 
-/* Frees everything the context owns.  NULL is a no-op. */
+/* Frees everything the context owns (after waiting for its stream).  NULL
+ * is a no-op.  Device and pinned host buffers up to 256 MiB go to the
+ * library's buffer cache rather than back to CUDA (see sbci_pool_trim). */
 void sbci_destroy(sbci_ctx *ctx);
+
+/* The library's buffer cache (no counterpart in the paper: runtime support).
+ * Contexts and solves allocate their device and pinned host buffers through
+ * it; a freed buffer of at most 256 MiB is kept (up to 2 GiB cached in all,
+ * per device for device memory) and serves the next request of the same
+ * rounded size, so creating and destroying contexts in a loop does not call
+ * cudaMalloc / cudaFree (which synchronises the device) each time.
+ * sbci_pool_stats: bytes cached now and the requests served from the cache
+ * (hits) and from CUDA (misses) since the process started (each pointer may
+ * be NULL).  sbci_pool_trim: returns every cached buffer to CUDA; SBCI_ERR_CUDA
+ * if a free failed.  Thread-safe. */
+sbci_status sbci_pool_stats(size_t *cached_bytes, long long *hits, long long *misses);
+sbci_status sbci_pool_trim(void);
 
 #ifdef __cplusplus
 }

@@ -30,6 +30,7 @@
 #include "batch.h"
 #include "lowrank.h"
 #include "pair_ctl.h"
+#include "pool.h"
 #include "sbci_internal.h"
 #include "step.h"
 
@@ -168,17 +169,20 @@ template <typename T>
 sbci_status dmalloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  CK(cudaMalloc((void **)p, count * sizeof(T)));
+  CK(pool_malloc((void **)p, count * sizeof(T)));
   return SBCI_OK;
 }
 
 sbci_status ensure_G(sbci_ctx *c, int prec) {
   const size_t need = sigma_scratch_bytes(c->npair, c->ndet, prec == SBCI_FP64 ? 0 : 1);
   if (c->G_bytes >= need) return SBCI_OK;
-  if (c->d_G) CK(cudaFree(c->d_G));
+  if (c->d_G) {
+    CK(cudaStreamSynchronize(c->stream));  // queued kernels may still read the old scratch
+    CK(pool_free(c->d_G));
+  }
   c->d_G = nullptr;
   c->G_bytes = 0;
-  CK(cudaMalloc(&c->d_G, need));
+  CK(pool_malloc(&c->d_G, need));
   c->G_bytes = need;
   return SBCI_OK;
 }
@@ -798,18 +802,19 @@ void free_solver(sbci_ctx *c) {
     s.gexec[i] = nullptr;
     s.graph[i] = nullptr;
   }
+  if (s.x && c->stream) cudaStreamSynchronize(c->stream);  // its buffers go back to the pool
   double **ptrs[] = {&s.x, &s.X, &s.y, &s.Y, &s.w, &s.z[0], &s.z[1], &s.Z[0], &s.Z[1], &s.xc};
   for (double **p : ptrs) {
-    if (*p) cudaFree(*p);
+    if (*p) pool_free(*p);
     *p = nullptr;
   }
-  if (s.zf) cudaFree(s.zf);
+  if (s.zf) pool_free(s.zf);
   s.zf = nullptr;
-  if (s.pinv) cudaFree(s.pinv);
+  if (s.pinv) pool_free(s.pinv);
   s.pinv = nullptr;
-  if (s.d_ctl) cudaFree(s.d_ctl);
-  if (s.h_ctl) cudaFreeHost(s.h_ctl);
-  if (s.d_counters) cudaFree(s.d_counters);
+  if (s.d_ctl) pool_free(s.d_ctl);
+  if (s.h_ctl) pool_free_host(s.h_ctl);
+  if (s.d_counters) pool_free(s.d_counters);
   s.d_ctl = nullptr;
   s.h_ctl = nullptr;
   s.d_counters = nullptr;
@@ -828,12 +833,12 @@ sbci_status alloc_solver(sbci_ctx *c, int k) {
   if (s.p.prec != SBCI_FP64) RET(dmalloc(&s.zf, (size_t)c->ndet));
   if (k > 1) RET(dmalloc(&s.pinv, (size_t)c->ndet));
   CK(cudaMemsetAsync(s.xc, 0, sizeof(double) * (size_t)k * c->ndet, c->stream));
-  CK(cudaMalloc((void **)&s.d_ctl, sizeof(CtlState)));
+  CK(pool_malloc((void **)&s.d_ctl, sizeof(CtlState)));
   CK(cudaMemsetAsync(s.d_ctl, 0, sizeof(CtlState), c->stream));
-  CK(cudaMallocHost((void **)&s.h_ctl, sizeof(CtlState)));
+  CK(pool_malloc_host((void **)&s.h_ctl, sizeof(CtlState)));
   std::memset(s.h_ctl, 0, sizeof(CtlState));
   s.h_ctl->trace_ptr = s.d_ctl->trace;  // device address of the ring (no dereference)
-  CK(cudaMalloc((void **)&s.d_counters, 4 * sizeof(unsigned int)));
+  CK(pool_malloc((void **)&s.d_counters, 4 * sizeof(unsigned int)));
   CK(cudaMemsetAsync(s.d_counters, 0, 4 * sizeof(unsigned int), c->stream));
   return SBCI_OK;
 }
@@ -935,7 +940,7 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   }
   RET(lincomb(c, s.X, in, co));
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaFree(tmp));
+  CK(pool_free(tmp));
   *E0 = w[0];
   return SBCI_OK;
 }
@@ -996,9 +1001,10 @@ struct VecScratch {
   double *partials = nullptr, *d_res = nullptr, *h_res = nullptr;
   int grid = 1;
   ~VecScratch() {
-    if (partials) cudaFree(partials);
-    if (d_res) cudaFree(d_res);
-    if (h_res) cudaFreeHost(h_res);
+    if (c && c->stream) cudaStreamSynchronize(c->stream);  // the buffers go back to the pool
+    if (partials) pool_free(partials);
+    if (d_res) pool_free(d_res);
+    if (h_res) pool_free_host(h_res);
   }
 };
 
@@ -1007,7 +1013,7 @@ sbci_status scratch_init(VecScratch &d, sbci_ctx *c) {
   d.grid = dav_dots_grid(c->ndet, c->nsm);
   RET(dmalloc(&d.partials, (size_t)kDavMaxPairs * d.grid));
   RET(dmalloc(&d.d_res, (size_t)kDavMaxPairs));
-  CK(cudaMallocHost((void **)&d.h_res, sizeof(double) * kDavMaxPairs));
+  CK(pool_malloc_host((void **)&d.h_res, sizeof(double) * kDavMaxPairs));
   return SBCI_OK;
 }
 
@@ -1016,10 +1022,11 @@ struct DavSolve : VecScratch {
   std::vector<int> V;            // the subspace, as slots in order
   std::vector<int> free_slots;
   ~DavSolve() {
+    if (c && c->stream) cudaStreamSynchronize(c->stream);  // the buffers go back to the pool
     for (double *p : vb)
-      if (p) cudaFree(p);
+      if (p) pool_free(p);
     for (double *p : ab)
-      if (p) cudaFree(p);
+      if (p) pool_free(p);
   }
   int take() {
     const int sl = free_slots.back();
@@ -1507,11 +1514,14 @@ sbci_status begin_common(sbci_ctx *c, int k, const sbci_params *params, const ch
 
 struct DevBuffers {
   std::vector<double *> v;
+  cudaStream_t stream = nullptr;
   ~DevBuffers() {
+    if (stream) cudaStreamSynchronize(stream);  // the buffers go back to the pool
     for (double *p : v)
-      if (p) cudaFree(p);
+      if (p) pool_free(p);
   }
   sbci_status get(sbci_ctx *c, double **out) {
+    stream = c->stream;
     double *p = nullptr;
     RET(dmalloc(&p, (size_t)c->ndet));
     v.push_back(p);
@@ -1901,9 +1911,11 @@ struct PairDev {
   PairCtl *d = nullptr;
   sbci_trace_record *trace = nullptr;
   int trace_cap = 0;
+  cudaStream_t stream = nullptr;
   ~PairDev() {
-    if (d) cudaFree(d);
-    if (trace) cudaFree(trace);
+    if (stream) cudaStreamSynchronize(stream);  // the buffers go back to the pool
+    if (d) pool_free(d);
+    if (trace) pool_free(trace);
   }
 };
 
@@ -2004,9 +2016,10 @@ sbci_status sbci2_pair_dev(sbci_ctx *c, VecScratch &vs, PairVecs &P, int alpha, 
   const int none[4] = {0, 0, 0, 0};
   if (p.max_sigma <= 0) return pair_finish_cap(c, vs, P, alpha, E, 0, 0, none);  // Q8 before any step
   if (!pd.d) {
-    CK(cudaMalloc((void **)&pd.d, sizeof(PairCtl)));
+    pd.stream = c->stream;
+    CK(pool_malloc((void **)&pd.d, sizeof(PairCtl)));
     pd.trace_cap = p.max_sigma / 2 + 16;  // two H-products per step
-    CK(cudaMalloc((void **)&pd.trace, sizeof(sbci_trace_record) * pd.trace_cap));
+    CK(pool_malloc((void **)&pd.trace, sizeof(sbci_trace_record) * pd.trace_cap));
   }
   PairCtl h{};
   h.eps0 = p.eps0;
@@ -2372,20 +2385,35 @@ sbci_status sbci_params_init(sbci_params *p) {
   return SBCI_OK;
 }
 
+sbci_status sbci_pool_stats(size_t *cached_bytes, long long *hits, long long *misses) {
+  pool_stats(cached_bytes, hits, misses);
+  return SBCI_OK;
+}
+
+sbci_status sbci_pool_trim(void) {
+  const cudaError_t e = pool_trim();
+  if (e != cudaSuccess) {
+    set_error(std::string("sbci_pool_trim: ") + cudaGetErrorString(e));
+    return SBCI_ERR_CUDA;
+  }
+  return SBCI_OK;
+}
+
 void sbci_destroy(sbci_ctx *c) {
   if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);  // its buffers go back to the pool
   free_solver(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   void *ptrs[] = {c->d_link_a, c->d_link_bT, c->d_mask_b, c->d_W, c->d_Wf, c->d_Wtc, c->d_Wbf, c->d_fc_link_a, c->d_Wos, c->d_fexp, c->d_cf,
                   c->d_diag, c->d_ea, c->d_eb, c->d_ja, c->d_G, c->d_partials, c->d_result, c->d_tmp_in,
                   c->d_tmp_out, c->d_lrUt64, c->d_lrUL64, c->d_Wtclr};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
-  if (c->d_link_b && c->d_link_b != c->d_link_a) cudaFree(c->d_link_b);
+    if (p) pool_free(p);
+  if (c->d_link_b && c->d_link_b != c->d_link_a) pool_free(c->d_link_b);
   if (c->ev_fence) cudaEventDestroy(c->ev_fence);
-  if (c->h_result) cudaFreeHost(c->h_result);
-  if (c->h_status) cudaFreeHost(c->h_status);
-  if (c->d_status) cudaFree(c->d_status);
+  if (c->h_result) pool_free_host(c->h_result);
+  if (c->h_status) pool_free_host(c->h_status);
+  if (c->d_status) pool_free(c->d_status);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -2521,7 +2549,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   for (int b = 0; b < c->Nb; ++b) eb[b] = string_energy(c->sb.masks[b]);
   // device uploads
   auto up = [&](void **dst, const void *src, size_t bytes) -> sbci_status {
-    sbci_status r = cuda_ok(cudaMalloc(dst, bytes ? bytes : 1), "cudaMalloc");
+    sbci_status r = cuda_ok(pool_malloc(dst, bytes ? bytes : 1), "cudaMalloc");
     if (r != SBCI_OK) return r;
     return cuda_ok(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream), "H2D");
   };
@@ -2540,14 +2568,14 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
   TRY(up((void **)&c->d_ea, ea.data(), ea.size() * 8));
   TRY(up((void **)&c->d_eb, eb.data(), eb.size() * 8));
   TRY(up((void **)&c->d_ja, ja.data(), ja.size() * 8));
-  TRY(cuda_ok(cudaMalloc((void **)&c->d_diag, sizeof(double) * c->ndet), "cudaMalloc diag"));
-  TRY(cuda_ok(cudaMalloc((void **)&c->d_partials, sizeof(double) * S_COUNT * c->grid), "cudaMalloc"));
+  TRY(cuda_ok(pool_malloc((void **)&c->d_diag, sizeof(double) * c->ndet), "cudaMalloc diag"));
+  TRY(cuda_ok(pool_malloc((void **)&c->d_partials, sizeof(double) * S_COUNT * c->grid), "cudaMalloc"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_partials, 0, sizeof(double) * S_COUNT * c->grid, c->stream), "memset"));
-  TRY(cuda_ok(cudaMalloc((void **)&c->d_result, sizeof(double) * S_COUNT), "cudaMalloc"));
-  TRY(cuda_ok(cudaMallocHost((void **)&c->h_result, sizeof(double) * S_COUNT), "cudaMallocHost"));
-  TRY(cuda_ok(cudaMallocHost((void **)&c->h_status, sizeof(int)), "cudaMallocHost"));
+  TRY(cuda_ok(pool_malloc((void **)&c->d_result, sizeof(double) * S_COUNT), "cudaMalloc"));
+  TRY(cuda_ok(pool_malloc_host((void **)&c->h_result, sizeof(double) * S_COUNT), "cudaMallocHost"));
+  TRY(cuda_ok(pool_malloc_host((void **)&c->h_status, sizeof(int)), "cudaMallocHost"));
   *c->h_status = 0;
-  TRY(cuda_ok(cudaMalloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
+  TRY(cuda_ok(pool_malloc((void **)&c->d_status, sizeof(int)), "cudaMalloc"));
   TRY(cuda_ok(cudaEventCreateWithFlags(&c->ev_fence, cudaEventDisableTiming), "cudaEventCreate"));
   TRY(cuda_ok(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "memset"));
   c->tc_grid = tc_grid(c->npair, c->ndet, c->nsm);
@@ -2584,12 +2612,12 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
     uint32_t cols;
     size_t smem;
     if (tc_dims(c->npair, &Kp, &Np, &cols, &smem)) {
-      TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
+      TRY(cuda_ok(pool_malloc((void **)&c->d_Wtc, sizeof(uint32_t) * 2 * Np * Kp), "cudaMalloc"));
       TRY(cuda_ok(launch_split_W(c->d_W, c->npair, Kp, Np, c->d_Wtc, c->stream), "split kernel"));
     }
   }
   if (bf_W_elems(c->npair) > 0) {  // BF16x3 operand B and the kernel's launch shape
-    TRY(cuda_ok(cudaMalloc((void **)&c->d_Wbf, sizeof(uint16_t) * bf_W_elems(c->npair)), "cudaMalloc"));
+    TRY(cuda_ok(pool_malloc((void **)&c->d_Wbf, sizeof(uint16_t) * bf_W_elems(c->npair)), "cudaMalloc"));
     TRY(cuda_ok(launch_split_W_bf(c->d_W, c->npair, c->d_Wbf, c->stream), "split kernel"));
     c->bf_grid = bf_grid(c->npair, c->ndet, c->nsm);
   }
@@ -2623,7 +2651,7 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
       if (!(tlr && std::strcmp(tlr, "0") == 0) && words > 0) {
         const int g = tclr_grid(np, rr, c->ndet, c->nsm);
         if (g > 0) {
-          TRY(cuda_ok(cudaMalloc((void **)&c->d_Wtclr, sizeof(uint32_t) * words), "cudaMalloc"));
+          TRY(cuda_ok(pool_malloc((void **)&c->d_Wtclr, sizeof(uint32_t) * words), "cudaMalloc"));
           TRY(cuda_ok(launch_split_lr_tc(static_cast<const double *>(c->d_lrUt64),
                                          static_cast<const double *>(c->d_lrUL64), rr, np, c->d_Wtclr, c->stream),
                       "split kernel"));
@@ -2638,8 +2666,8 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
     const char *mode = std::getenv("SBCI_FP64_CONTRACTION");
     const bool dfma = mode && std::strcmp(mode, "dfma") == 0;
     if (!dfma && os_supported(c->npair) && prepare_os_kernel(c->npair) == cudaSuccess) {
-      TRY(cuda_ok(cudaMalloc(&c->d_Wos, os_W_bytes()), "cudaMalloc"));
-      TRY(cuda_ok(cudaMalloc((void **)&c->d_fexp, sizeof(int) * 64), "cudaMalloc"));
+      TRY(cuda_ok(pool_malloc(&c->d_Wos, os_W_bytes()), "cudaMalloc"));
+      TRY(cuda_ok(pool_malloc((void **)&c->d_fexp, sizeof(int) * 64), "cudaMalloc"));
       TRY(cuda_ok(launch_split_W_os(c->d_W, c->npair, c->d_Wos, c->d_fexp, c->stream), "slice kernel"));
       c->os_grid = os_grid(c->ndet, c->nsm);
     }
@@ -2705,8 +2733,9 @@ sbci_status sbci_sigma(sbci_ctx *c, const double *in, double *out, int nvec, int
   if (!on_device) {
     RET(check_finite(in, n * nvec, "c"));
     if (c->tmp_elems < n) {
-      if (c->d_tmp_in) cudaFree(c->d_tmp_in);
-      if (c->d_tmp_out) cudaFree(c->d_tmp_out);
+      if (c->d_tmp_in) CK(cudaStreamSynchronize(c->stream));
+      if (c->d_tmp_in) pool_free(c->d_tmp_in);
+      if (c->d_tmp_out) pool_free(c->d_tmp_out);
       c->d_tmp_in = c->d_tmp_out = nullptr;
       c->tmp_elems = 0;
       RET(dmalloc(&c->d_tmp_in, n));

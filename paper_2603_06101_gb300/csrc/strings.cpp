@@ -25,12 +25,22 @@ static long long binom(int n, int k) {
   return r;
 }
 
-// Rank of a bitmask among masks of equal popcount: sum_k C(o_k, k).
+// C(p, k) for p < 32, k <= 32 (the ranks of the masks of up to 32 orbitals).
+struct BinomTable {
+  long long c[32][33];
+  BinomTable() {
+    for (int p = 0; p < 32; ++p)
+      for (int k = 0; k <= 32; ++k) c[p][k] = binom(p, k);
+  }
+};
+
+// Rank of a bitmask among masks of equal popcount: sum_k C(o_k, k) over its
+// set bits o_1 < o_2 < ...
 static int string_address(uint32_t mask) {
+  static const BinomTable T;
   long long a = 0;
   int k = 1;
-  for (int p = 0; p < 32; ++p)
-    if (mask >> p & 1u) a += binom(p, k++);
+  for (uint32_t m = mask; m; m &= m - 1u) a += T.c[__builtin_ctz(m)][k++];
   return (int)a;
 }
 

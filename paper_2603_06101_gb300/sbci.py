@@ -79,7 +79,8 @@ EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_
            "sbci_trace", "sbci_solve_sbci2", "sbci_davidson", "sbci_profile", "sbci_profile_read", "sbci_sigma_noalloc",
            "sbci_server_create", "sbci_server_submit", "sbci_server_progress", "sbci_server_poll",
            "sbci_server_set_batching", "sbci_server_destroy", "sbci_solve_batch", "sbci_batch_profile",
-           "sbci_batch_profile_read", "sbci_batch_classes", "sbci_last_error", "sbci_destroy"]
+           "sbci_batch_profile_read", "sbci_batch_classes", "sbci_last_error", "sbci_destroy",
+           "sbci_pool_stats", "sbci_pool_trim"]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -124,6 +125,8 @@ def load(path: str = LIB_PATH):
     lib.sbci_last_error.argtypes = []
     lib.sbci_destroy.argtypes = [P]
     lib.sbci_destroy.restype = None
+    lib.sbci_pool_stats.argtypes = [C.POINTER(C.c_size_t), C.POINTER(LL), C.POINTER(LL)]
+    lib.sbci_pool_trim.argtypes = []
     for name in EXPORTS:
         if name not in ("sbci_last_error", "sbci_destroy", "sbci_server_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -381,6 +384,20 @@ def batch_profile_read() -> dict:
     n = C.c_int()
     _check(load().sbci_batch_profile_read(buf, 8, C.byref(n)))
     return {b.name.decode(): (int(b.launches), float(b.total_ms)) for b in list(buf)[: n.value]}
+
+
+def pool_stats() -> dict:
+    """The library's buffer cache: bytes cached now, requests served from the
+    cache (hits) and from CUDA (misses) since the process started."""
+    lib = load()
+    cached, hits, misses = C.c_size_t(0), C.c_longlong(0), C.c_longlong(0)
+    _check(lib.sbci_pool_stats(C.byref(cached), C.byref(hits), C.byref(misses)))
+    return {"cached_bytes": cached.value, "hits": hits.value, "misses": misses.value}
+
+
+def pool_trim():
+    """Returns every cached buffer of the library to CUDA."""
+    _check(load().sbci_pool_trim())
 
 
 def batch_classes() -> list:

@@ -1,0 +1,42 @@
+"""The library's buffer cache (csrc/pool.cpp, sbci_pool_stats / sbci_pool_trim).
+
+Contexts and solves take their device and pinned host buffers from a cache of
+freed blocks; a context created on recycled buffers must compute exactly
+what one created on fresh memory computes (sigma and a batched solve of the
+bench workload, bitwise), the second round of creations must be served from
+the cache, and a trim must return the cache to CUDA.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import make_integrals, require_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_recycled_buffers_give_identical_results():
+    sbci = require_lib()
+    I = make_integrals(("chain", 10, 1.2))
+    sbci.pool_trim()
+    c = np.random.default_rng(3).standard_normal(63504)
+    p = sbci.params(sector=1, prec=sbci.SBCI_TF32X3)
+    out = []
+    for rnd in range(2):
+        before = sbci.pool_stats()
+        ctxs = [sbci.Context.from_integrals(I) for _ in range(4)]
+        s = ctxs[0].sigma(c, prec=sbci.SBCI_FP64)
+        E, _, st = sbci.solve_batch(ctxs, 2, p)
+        assert st == sbci.SBCI_OK
+        for x in ctxs:
+            x.close()
+        after = sbci.pool_stats()
+        out.append((s, E, before, after))
+    (s0, E0, b0, a0), (s1, E1, b1, a1) = out
+    assert np.array_equal(s0, s1)
+    assert np.array_equal(E0, E1)
+    # the second round took its buffers from the cache, not from CUDA
+    assert a1["hits"] - b1["hits"] > 0
+    assert a1["misses"] - b1["misses"] < a0["misses"] - b0["misses"]
+    assert a1["cached_bytes"] > 0
+    sbci.pool_trim()
+    assert sbci.pool_stats()["cached_bytes"] == 0
