@@ -561,7 +561,11 @@ def run_gb300(args, rank, world, local_rank):
     p = sbci.params(sector=1, prec=prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     B = max(1, args.batch) if args.prec == "tf32x3" else 1  # (the batch engine takes TF32x3 solves)
-    batch_ctx = [ctx] + [sbci.Context.from_integrals(I, stream=stream.cuda_stream) for _ in range(B - 1)]
+    # one CUDA stream per solve: a solve's own work between batch rounds (its
+    # initial guess, FP64 re-syncs and state transitions) then overlaps the
+    # others'; the batch engine orders itself after each solve's stream
+    streams = [stream] + [torch.cuda.Stream() for _ in range(B - 1)]
+    batch_ctx = [ctx] + [sbci.Context.from_integrals(I, stream=streams[i].cuda_stream) for i in range(1, B)]
     ref_E = golden_energies()
 
     def one_solve():
@@ -684,8 +688,8 @@ def run_gb300(args, rank, world, local_rank):
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
-            cs = [sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=stream.cuda_stream)
-                  for _ in range(B)]
+            cs = [sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=streams[i].cuda_stream)
+                  for i in range(B)]
             if B == 1:
                 E2, V2, _, _ = cs[0].solve(NSTATES, p, want_vectors=True)
                 d2h = E2.nbytes + V2.nbytes

@@ -312,11 +312,17 @@ sbci_status run_sigma(sbci_ctx *c, const double *in, double *out, int prec) {
   return SBCI_OK;
 }
 
-sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1, int grid) {
+// The reduction of slots [s0, s1) and the copies of its results and of the
+// status word to the host, queued on the context stream (fetch_complete waits).
+sbci_status reduce_issue(sbci_ctx *c, int s0, int s1, int grid) {
   RET(timed(c, K_RED, [&] { return launch_reduce(c->d_partials, grid, s0, s1, c->d_result, c->stream); }));
   CK(cudaMemcpyAsync(c->h_result + s0, c->d_result + s0, sizeof(double) * (s1 - s0),
                      cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return SBCI_OK;
+}
+
+sbci_status fetch_complete(sbci_ctx *c, int s0, int s1) {
   CK(cudaStreamSynchronize(c->stream));
   if (*c->h_status != 0) {
     set_error("a bounded device wait ran out (tensor-core MMA completion)");
@@ -330,8 +336,14 @@ sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1, int grid) {
   return SBCI_OK;
 }
 
-// dots over up to 16 pairs, results in h_result[S_GEN0 + i]
-sbci_status gen_dots(sbci_ctx *c, std::vector<const double *> u, std::vector<const double *> v) {
+sbci_status reduce_and_fetch(sbci_ctx *c, int s0, int s1, int grid) {
+  RET(reduce_issue(c, s0, s1, grid));
+  return fetch_complete(c, s0, s1);
+}
+
+// dots over up to 16 pairs, results in h_result[S_GEN0 + i] once
+// fetch_complete(c, S_GEN0, S_GEN0 + u.size()) has returned
+sbci_status gen_dots_issue(sbci_ctx *c, const std::vector<const double *> &u, const std::vector<const double *> &v) {
   // about four elements per thread, at most the partials' capacity of blocks
   long long g = (c->ndet + 1023) / 1024;
   if (g > c->grid) g = c->grid;
@@ -340,7 +352,12 @@ sbci_status gen_dots(sbci_ctx *c, std::vector<const double *> u, std::vector<con
   RET(timed(c, K_DOTS, [&] {
     return launch_dots(u.data(), v.data(), (int)u.size(), c->ndet, c->d_partials, grid, c->stream);
   }));
-  return reduce_and_fetch(c, S_GEN0, S_GEN0 + (int)u.size(), grid);
+  return reduce_issue(c, S_GEN0, S_GEN0 + (int)u.size(), grid);
+}
+
+sbci_status gen_dots(sbci_ctx *c, std::vector<const double *> u, std::vector<const double *> v) {
+  RET(gen_dots_issue(c, u, v));
+  return fetch_complete(c, S_GEN0, S_GEN0 + (int)u.size());
 }
 
 sbci_status lincomb(sbci_ctx *c, double *out, std::vector<const double *> in, std::vector<double> co) {
@@ -593,17 +610,28 @@ sbci_status start_state(sbci_ctx *c, int alpha, double E0) {
   return start_iteration(c, 1.0, E0, s.p.prec == SBCI_FP64 ? 1 : 0);
 }
 
-// X <- H x in FP64; returns x.x, x.X and X.X.
-sbci_status resync(sbci_ctx *c, double *xx, double *xX, double *XX) {
+// X <- H x in FP64; returns x.x, x.X and X.X.  resync_issue queues it on the
+// context stream, resync_complete waits for it.
+sbci_status resync_issue(sbci_ctx *c) {
   Solver &s = c->s;
   RET(run_sigma(c, s.x, s.X, SBCI_FP64));
-  RET(gen_dots(c, {s.x, s.x, s.X}, {s.x, s.X, s.X}));
+  return gen_dots_issue(c, {s.x, s.x, s.X}, {s.x, s.X, s.X});
+}
+
+sbci_status resync_complete(sbci_ctx *c, double *xx, double *xX, double *XX) {
+  Solver &s = c->s;
+  RET(fetch_complete(c, S_GEN0, S_GEN0 + 3));
   *xx = c->h_result[S_GEN0];
   *xX = c->h_result[S_GEN0 + 1];
   *XX = c->h_result[S_GEN0 + 2];
   s.h_ctl->n_sigma += 1;
   s.h_ctl->n_sigma_fp64 += 1;
   return SBCI_OK;
+}
+
+sbci_status resync(sbci_ctx *c, double *xx, double *xX, double *XX) {
+  RET(resync_issue(c));
+  return resync_complete(c, xx, xX, XX);
 }
 
 // Start of state alpha with a seeded full-symmetry component:
@@ -745,6 +773,26 @@ sbci_status switch_async(sbci_ctx *c) {
 }
 
 // Acts on a halted controller.
+// A converged low-precision state is verified in FP64: its host work starts
+// with a re-sync (exact X = H x).
+bool halt_needs_resync(const sbci_ctx *c) {
+  const Solver &s = c->s;
+  const CtlState &h = *s.h_ctl;
+  return h.halt == H_CONVERGED && !(s.p.prec == SBCI_FP64 || h.prec == SBCI_FP64);
+}
+
+// The FP64 residual check of a converged low-precision state from its
+// re-sync (x.x, x.X, X.X): Rayleigh quotient and |H x - E x| / |x|; the state
+// is stored, or continues in the FP64 stage.
+sbci_status converged_after_resync(sbci_ctx *c, double xx, double xX, double XX) {
+  Solver &s = c->s;
+  const CtlState &h = *s.h_ctl;
+  const double Erq = xX / xx;
+  const double r = std::sqrt(std::max(XX / xx - Erq * Erq, 0.0));
+  if (r < s.p.r0 && std::fabs(Erq - h.E) < s.p.eps0) return finalize_state(c, true, Erq, r);
+  return start_iteration(c, 1.0 / std::sqrt(xx), Erq, 1);
+}
+
 sbci_status handle_halt(sbci_ctx *c) {
   Solver &s = c->s;
   CtlState &h = *s.h_ctl;
@@ -781,14 +829,9 @@ sbci_status handle_halt(sbci_ctx *c) {
     case H_CONVERGED: {
       if (s.p.prec == SBCI_FP64 || h.prec == SBCI_FP64)  // FP64 sigma throughout (or after a fallback)
         return finalize_state(c, true, h.E, std::sqrt(h.dots[S_ZPZP]));
-      // FP64 residual check of the low-precision result: exact X = H x,
-      // Rayleigh quotient and |H x - E x| / |x|
       double xx, xX, XX;
       RET(resync(c, &xx, &xX, &XX));
-      const double Erq = xX / xx;
-      const double r = std::sqrt(std::max(XX / xx - Erq * Erq, 0.0));
-      if (r < s.p.r0 && std::fabs(Erq - h.E) < s.p.eps0) return finalize_state(c, true, Erq, r);
-      return start_iteration(c, 1.0 / std::sqrt(xx), Erq, 1);
+      return converged_after_resync(c, xx, xX, XX);
     }
   }
   return SBCI_OK;
@@ -2269,17 +2312,39 @@ sbci_status sbci::solve_round_launch(sbci_ctx *c) {
   return SBCI_OK;
 }
 
-sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
+sbci_status sbci::solve_round_read(sbci_ctx *c, int *done, bool own_graph, int *deferred) {
   Solver &s = c->s;
+  *deferred = 0;
   RET(ctl_read(c));
   const long long bodies = s.h_ctl->iters;
   const int prec = s.h_ctl->prec;
   if (own_graph) count_bodies(c, prec, bodies);  // the kernels the solve's own graph ran
   s.h_ctl->iters = 0;
   CK(cudaMemsetAsync(&s.d_ctl->iters, 0, sizeof(int), c->stream));
+  if (halt_needs_resync(c)) {
+    RET(resync_issue(c));
+    *deferred = 1;
+    *done = 0;
+    return SBCI_OK;
+  }
   const sbci_status st = handle_halt(c);
   *done = s.done ? 1 : 0;
   return st;
+}
+
+sbci_status sbci::solve_round_complete(sbci_ctx *c, int *done) {
+  Solver &s = c->s;
+  double xx, xX, XX;
+  RET(resync_complete(c, &xx, &xX, &XX));
+  const sbci_status st = converged_after_resync(c, xx, xX, XX);
+  *done = s.done ? 1 : 0;
+  return st;
+}
+
+sbci_status sbci::solve_round_finish(sbci_ctx *c, int *done, bool own_graph) {
+  int deferred = 0;
+  RET(solve_round_read(c, done, own_graph, &deferred));
+  return deferred ? solve_round_complete(c, done) : SBCI_OK;
 }
 
 cudaStream_t sbci::ctx_stream(const sbci_ctx *c) { return c->stream; }

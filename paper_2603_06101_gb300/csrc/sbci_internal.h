@@ -307,6 +307,13 @@ bool ctx_sigma_args(const sbci_ctx *c, SigmaArgs *a, cudaStream_t *stream);
 // Serving support (api.cpp): asynchronous rounds of an active solve.
 sbci_status solve_round_launch(sbci_ctx *c);
 sbci_status solve_round_finish(sbci_ctx *c, int *done, bool own_graph = true);
+// solve_round_finish in two halves, so that the FP64 re-syncs of several
+// halted solves (on their own streams) overlap: solve_round_read reads the
+// controller and, for a halt whose host work starts with a re-sync, queues it
+// and sets *deferred = 1; solve_round_complete then waits for it and finishes
+// the halt.  Otherwise the halt is handled at once and *deferred = 0.
+sbci_status solve_round_read(sbci_ctx *c, int *done, bool own_graph, int *deferred);
+sbci_status solve_round_complete(sbci_ctx *c, int *done);
 cudaStream_t ctx_stream(const sbci_ctx *c);
 // Makes waiter wait for the work issued so far on the context's stream (the
 // host's asynchronous state changes of a halted solve, before a batch round

@@ -602,17 +602,28 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     sbci_status host_st = SBCI_OK;
     const double th0 = now_s();
     const long long nhalted = (long long)pending.size();
-    for (int i : pending) {
-      is_pending[i] = 0;
-      if (host_st != SBCI_OK) continue;
-      const sbci_status st = solve_round_finish(ctx[i], &done[i], false);
-      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
-        host_st = st;
-        continue;
-      }
-      if (done[i]) {
-        const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
-        if (fs != SBCI_OK) worst = fs;
+    // two passes: the FP64 re-syncs of the converged states are queued first
+    // (each solve on its own stream) and completed after, so they overlap
+    std::vector<int> deferred;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i : pass == 0 ? pending : deferred) {
+        is_pending[i] = 0;
+        if (host_st != SBCI_OK) continue;
+        int def = 0;
+        const sbci_status st = pass == 0 ? solve_round_read(ctx[i], &done[i], false, &def)
+                                         : solve_round_complete(ctx[i], &done[i]);
+        if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
+          host_st = st;
+          continue;
+        }
+        if (def) {
+          deferred.push_back(i);
+          continue;
+        }
+        if (done[i]) {
+          const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
+          if (fs != SBCI_OK) worst = fs;
+        }
       }
     }
     pending.clear();
