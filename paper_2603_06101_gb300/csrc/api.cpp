@@ -946,24 +946,49 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   // otherwise a temporary allocation.
   double *tmp = nullptr;
   RET(dmalloc(&tmp, (size_t)m * c->ndet));
+  // the sparse vectors' (index, value) pairs, and the entries of the H-images
+  // that the subspace matrix needs, move in one copy each (one small device
+  // buffer: the pairs of every basis vector, then the entry offsets and values)
+  std::vector<double> pairs;
+  std::vector<size_t> pofs(m + 1, 0);
+  size_t nA = 0;
+  for (int i = 0; i < m; ++i) {
+    for (auto &kv : basis[i]) {
+      pairs.push_back((double)kv.first);
+      pairs.push_back(kv.second);
+    }
+    pofs[i + 1] = pairs.size() / 2;
+    nA += (size_t)m * basis[i].size();
+  }
+  double *d_aux = nullptr;
+  RET(dmalloc(&d_aux, pairs.size() + 2 * nA));
+  CK(cudaMemcpyAsync(d_aux, pairs.data(), sizeof(double) * pairs.size(), cudaMemcpyHostToDevice, c->stream));
   std::vector<double> A(m * m);
   for (int i = 0; i < m; ++i) {
     CK(cudaMemsetAsync(s.w, 0, sizeof(double) * c->ndet, c->stream));
-    for (auto &kv : basis[i])
-      CK(cudaMemcpyAsync(s.w + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_sparse_set(s.w, d_aux + 2 * pofs[i], (int)(pofs[i + 1] - pofs[i]), c->stream));
     RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, SBCI_FP64));
   }
-  CK(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) {
-      double a = 0.0;
-      for (auto &kv : basis[i]) {
-        double v;
-        CK(cudaMemcpy(&v, tmp + (size_t)j * c->ndet + kv.first, sizeof(double), cudaMemcpyDeviceToHost));
-        a += kv.second * v;
+  {  // A[i][j] = sum over the entries (I, v) of basis i of v (H b_j)[I], in that order
+    std::vector<double> offs;
+    offs.reserve(nA);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        for (auto &kv : basis[i]) offs.push_back((double)((size_t)j * c->ndet + (size_t)kv.first));
+    double *d_offs = d_aux + pairs.size(), *d_vals = d_offs + nA;
+    std::vector<double> vals(nA);
+    CK(cudaMemcpyAsync(d_offs, offs.data(), sizeof(double) * nA, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_gather_at(tmp, d_offs, (int)nA, d_vals, c->stream));
+    CK(cudaMemcpyAsync(vals.data(), d_vals, sizeof(double) * nA, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    size_t q = 0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        double a = 0.0;
+        for (auto &kv : basis[i]) a += kv.second * vals[q++];
+        A[i * m + j] = a;
       }
-      A[i * m + j] = a;
-    }
+  }
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < i; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);
   std::vector<double> w(m), U(m * m);
@@ -973,8 +998,16 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   for (int i = 0; i < m; ++i)
     for (auto &kv : basis[i]) x0[kv.first] += U[i * m] * kv.second;
   CK(cudaMemsetAsync(s.x, 0, sizeof(double) * c->ndet, c->stream));
-  for (auto &kv : x0)
-    CK(cudaMemcpyAsync(s.x + kv.first, &kv.second, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  {
+    std::vector<double> xp;
+    for (auto &kv : x0) {
+      xp.push_back((double)kv.first);
+      xp.push_back(kv.second);
+    }
+    // (the pairs of the basis are consumed: the stream has run past their scatters)
+    CK(cudaMemcpyAsync(d_aux, xp.data(), sizeof(double) * xp.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_sparse_set(s.x, d_aux, (int)(xp.size() / 2), c->stream));
+  }
   std::vector<const double *> in;
   std::vector<double> co;
   for (int i = 0; i < m; ++i) {
@@ -984,6 +1017,7 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   RET(lincomb(c, s.X, in, co));
   CK(cudaStreamSynchronize(c->stream));
   CK(pool_free(tmp));
+  CK(pool_free(d_aux));
   *E0 = w[0];
   return SBCI_OK;
 }

@@ -166,6 +166,28 @@ cudaError_t launch_dots(const double *const *u, const double *const *v, int npai
   return cudaGetLastError();
 }
 
+__global__ void k_sparse_set(double *dst, const double *pairs, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) dst[(long long)pairs[2 * q]] = pairs[2 * q + 1];
+}
+
+__global__ void k_gather_at(const double *src, const double *offs, int n, double *out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = src[(long long)offs[q]];
+}
+
+cudaError_t launch_sparse_set(double *dst, const double *pairs, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_sparse_set<<<(n + 255) / 256, 256, 0, s>>>(dst, pairs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_at(const double *src, const double *offs, int n, double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_at<<<(n + 255) / 256, 256, 0, s>>>(src, offs, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double *partials, int grid, int s0, int s1, double *result,
                           cudaStream_t s) {
   if (s1 <= s0) return cudaSuccess;

@@ -240,6 +240,10 @@ cudaError_t launch_reduce(const double *partials, int grid, int s0, int s1, doub
 cudaError_t launch_diagonal(double *diag, const double *ea, const double *eb, const double *ja,
                             const uint32_t *mask_b, int na, int nb, int norb, cudaStream_t s);
 cudaError_t launch_symmetrize(double *v, int n, cudaStream_t s);
+// dst[pairs[2 q]] = pairs[2 q + 1], q < n (indices stored as exact doubles).
+cudaError_t launch_sparse_set(double *dst, const double *pairs, int n, cudaStream_t s);
+// out[q] = src[offs[q]], q < n (offsets stored as exact doubles).
+cudaError_t launch_gather_at(const double *src, const double *offs, int n, double *out, cudaStream_t s);
 // r[I] = SplitMix64 vector of (seed, alpha) in [-1, 1)
 cudaError_t launch_splitmix(double *r, long long n, unsigned long long seed, int alpha, cudaStream_t s);
 
