@@ -37,6 +37,7 @@
 namespace sbci {
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
+std::string last_error() { return g_err; }
 }  // namespace sbci
 
 using namespace sbci;

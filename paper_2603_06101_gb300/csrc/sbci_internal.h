@@ -300,6 +300,7 @@ cudaError_t launch_pair_decide(PairCtl *ctl, const double *res, unsigned long lo
 void jacobi_eigh(int n, const double *A, double *w, double *V);
 
 void set_error(const std::string &msg);
+std::string last_error();  // this thread's message (to carry it to another thread)
 
 }  // namespace sbci
 

@@ -32,6 +32,7 @@
 
 #include "../../include/sbci.h"
 #include "batch.h"
+#include "host_pool.h"
 #include "sbci_internal.h"
 
 using namespace sbci;
@@ -534,9 +535,19 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
   std::vector<int> done(n, 0);
   long long host_launches0 = 0;
   for (int i = 0; i < n; ++i) host_launches0 += ctx_launch_count(ctx[i]);
-  for (int i = 0; i < n; ++i) {
-    const sbci_status st = sbci_begin(ctx[i], k, params, nullptr);
-    if (st != SBCI_OK) return st;
+  {  // the solves' initial guesses in parallel (each on its own stream)
+    std::vector<sbci_status> bs(n, SBCI_OK);
+    std::vector<std::string> bm(n);
+    host_parallel_for(n, [&](int i) {
+      cudaSetDevice(ctx_device(ctx[i]));
+      bs[i] = sbci_begin(ctx[i], k, params, nullptr);
+      if (bs[i] != SBCI_OK) bm[i] = last_error();
+    });
+    for (int i = 0; i < n; ++i)
+      if (bs[i] != SBCI_OK) {
+        set_error(bm[i]);
+        return bs[i];
+      }
   }
   std::memset(eng.h_table, 0, sizeof(BatchTable));
   if (cudaMemsetAsync(eng.d_status, 0, sizeof(int), eng.stream) != cudaSuccess) {
@@ -602,27 +613,38 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     sbci_status host_st = SBCI_OK;
     const double th0 = now_s();
     const long long nhalted = (long long)pending.size();
-    // two passes: the FP64 re-syncs of the converged states are queued first
-    // (each solve on its own stream) and completed after, so they overlap
-    std::vector<int> deferred;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i : pass == 0 ? pending : deferred) {
-        is_pending[i] = 0;
-        if (host_st != SBCI_OK) continue;
-        int def = 0;
-        const sbci_status st = pass == 0 ? solve_round_read(ctx[i], &done[i], false, &def)
-                                         : solve_round_complete(ctx[i], &done[i]);
-        if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
-          host_st = st;
-          continue;
-        }
-        if (def) {
-          deferred.push_back(i);
-          continue;
+    // the halted solves' host work (FP64 re-syncs, verification, next state)
+    // in parallel: each solve on its own stream, so their launches and waits
+    // overlap; statuses and messages are collected in solve order
+    {
+      const int np = (int)pending.size();
+      std::vector<sbci_status> rs(np, SBCI_OK), fs(np, SBCI_OK);
+      std::vector<std::string> rm(np), fm(np);
+      host_parallel_for(np, [&](int q) {
+        const int i = pending[q];
+        cudaSetDevice(ctx_device(ctx[i]));
+        rs[q] = solve_round_finish(ctx[i], &done[i], false);
+        if (rs[q] != SBCI_OK && rs[q] != SBCI_ERR_NOT_CONVERGED) {
+          rm[q] = last_error();
+          return;
         }
         if (done[i]) {
-          const sbci_status fs = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
-          if (fs != SBCI_OK) worst = fs;
+          fs[q] = sbci_finish(ctx[i], energies + (size_t)i * k, nullptr, rep ? rep + (size_t)i * k : nullptr);
+          if (fs[q] != SBCI_OK) fm[q] = last_error();
+        }
+      });
+      for (int q = 0; q < np; ++q) {
+        is_pending[pending[q]] = 0;
+        if (rs[q] != SBCI_OK && rs[q] != SBCI_ERR_NOT_CONVERGED) {
+          if (host_st == SBCI_OK) {
+            host_st = rs[q];
+            set_error(rm[q]);
+          }
+          continue;
+        }
+        if (fs[q] != SBCI_OK) {
+          worst = fs[q];
+          if (host_st == SBCI_OK) set_error(fm[q]);
         }
       }
     }
