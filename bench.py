@@ -688,8 +688,8 @@ def run_gb300(args, rank, world, local_rank):
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
-            cs = [sbci.Context(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core, stream=streams[i].cuda_stream)
-                  for i in range(B)]
+            cs = sbci.Context.many(I.norb, I.nalpha, I.nbeta, h1, eri, I.e_core,
+                                   streams=[streams[i].cuda_stream for i in range(B)])
             if B == 1:
                 E2, V2, _, _ = cs[0].solve(NSTATES, p, want_vectors=True)
                 d2h = E2.nbytes + V2.nbytes

@@ -187,6 +187,18 @@ sbci_status sbci_init_integrals(sbci_ctx **out, int norb, int nalpha, int nbeta,
                                 const double *h1, const double *eri, double e_core,
                                 void *cuda_stream);
 
+/* n contexts of the same integrals, each as sbci_init_integrals would make it,
+ * created in parallel on the library's host worker threads (no counterpart in
+ * the paper: runtime support for batched and served solves, which make many
+ * contexts at once).  out[n] receives them; cuda_streams: n streams (an entry
+ * may be NULL: that context makes its own), or NULL for all.  The contexts
+ * live on the calling thread's current device.  On an error none is left:
+ * the ones made are destroyed, out[] is NULL and the first failing context's
+ * status and message are returned. */
+sbci_status sbci_init_integrals_many(sbci_ctx **out, int n, int norb, int nalpha, int nbeta,
+                                     const double *h1, const double *eri, double e_core,
+                                     void *const *cuda_streams);
+
 /* Sizes of the determinant space: Ndet = Na*Nb; nlink = m(n-m+1) per string;
  * npair = n(n+1)/2.  Any output pointer may be NULL. */
 sbci_status sbci_dims(const sbci_ctx *ctx, long long *ndet, int *na, int *nb,

@@ -443,16 +443,27 @@ sbci_status progress_batch(sbci_server *sv) {
         sv->slots[sv->batch_slots[j]].host_pending = true;
       }
     sbci_status lst = launch_batch_round(sv);
-    for (int i : halted) {
-      SolveSlot &sl = sv->slots[i];
+    // their host work in parallel (each solve on its own stream), then the
+    // retirements in slot order on this thread
+    const int nh = (int)halted.size();
+    std::vector<sbci_status> hs(nh, SBCI_OK);
+    std::vector<int> hd(nh, 0);
+    std::vector<std::string> hm(nh);
+    host_parallel_for(nh, [&](int q) {
+      SolveSlot &sl = sv->slots[halted[q]];
+      cudaSetDevice(ctx_device(sl.ctx));
+      hs[q] = solve_round_finish(sl.ctx, &hd[q], false);
+      if (hs[q] != SBCI_OK && hs[q] != SBCI_ERR_NOT_CONVERGED) hm[q] = last_error();
+    });
+    for (int q = 0; q < nh; ++q) {
+      SolveSlot &sl = sv->slots[halted[q]];
       sl.host_pending = false;
-      int done = 0;
-      const sbci_status st = solve_round_finish(sl.ctx, &done, false);
-      if (st != SBCI_OK && st != SBCI_ERR_NOT_CONVERGED) {
-        retire(sv, sl, st);
+      if (hs[q] != SBCI_OK && hs[q] != SBCI_ERR_NOT_CONVERGED) {
+        set_error(hm[q]);
+        retire(sv, sl, hs[q]);
         continue;
       }
-      if (done) retire(sv, sl, SBCI_OK);
+      if (hd[q]) retire(sv, sl, SBCI_OK);
     }
     if (lst != SBCI_OK) return lst;
     if (!sv->batch_in_flight) return launch_batch_round(sv);  // every solve had halted
@@ -675,6 +686,38 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
     *launches = (long long)bodies + (host_launches1 - host_launches0);
   }
   return worst;
+}
+
+sbci_status sbci_init_integrals_many(sbci_ctx **out, int n, int norb, int nalpha, int nbeta, const double *h1,
+                                     const double *eri, double e_core, void *const *cuda_streams) {
+  if (!out || n < 0) {
+    set_error("sbci_init_integrals_many: NULL output or n < 0");
+    return SBCI_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("sbci_init_integrals_many: cudaGetDevice failed");
+    return SBCI_ERR_CUDA;
+  }
+  std::vector<sbci_status> st(n, SBCI_OK);
+  std::vector<std::string> msg(n);
+  host_parallel_for(n, [&](int i) {
+    cudaSetDevice(dev);
+    st[i] = sbci_init_integrals(&out[i], norb, nalpha, nbeta, h1, eri, e_core,
+                                cuda_streams ? cuda_streams[i] : nullptr);
+    if (st[i] != SBCI_OK) msg[i] = last_error();
+  });
+  for (int i = 0; i < n; ++i)
+    if (st[i] != SBCI_OK) {
+      for (int j = 0; j < n; ++j) {
+        sbci_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      set_error(msg[i]);
+      return st[i];
+    }
+  return SBCI_OK;
 }
 
 sbci_status sbci_batch_profile(int enable) {

@@ -80,7 +80,7 @@ EXPORTS = ["sbci_params_init", "sbci_init_integrals", "sbci_dims", "sbci_string_
            "sbci_server_create", "sbci_server_submit", "sbci_server_progress", "sbci_server_poll",
            "sbci_server_set_batching", "sbci_server_destroy", "sbci_solve_batch", "sbci_batch_profile",
            "sbci_batch_profile_read", "sbci_batch_classes", "sbci_last_error", "sbci_destroy",
-           "sbci_pool_stats", "sbci_pool_trim"]
+           "sbci_pool_stats", "sbci_pool_trim", "sbci_init_integrals_many"]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
     lib.sbci_params_init.argtypes = [C.POINTER(sbci_params)]
     lib.sbci_init_integrals.argtypes = [C.POINTER(P), I, I, I, P, P, D, P]
+    lib.sbci_init_integrals_many.argtypes = [C.POINTER(P), I, I, I, I, P, P, D, C.POINTER(P)]
     lib.sbci_dims.argtypes = [P, C.POINTER(LL), C.POINTER(I), C.POINTER(I), C.POINTER(I),
                               C.POINTER(I), C.POINTER(I)]
     lib.sbci_string_table.argtypes = [P, I, P]
@@ -176,16 +177,19 @@ def params(**kw) -> sbci_params:
 class Context:
     """One active space on the current CUDA device (owns the device memory)."""
 
-    def __init__(self, norb, nalpha, nbeta, h1, eri, e_core=0.0, stream=None):
+    def __init__(self, norb, nalpha, nbeta, h1, eri, e_core=0.0, stream=None, _handle=None):
         lib = load()
         self._lib = lib
-        h1 = np.ascontiguousarray(h1, dtype=np.float64)
-        eri = np.ascontiguousarray(eri, dtype=np.float64)
-        self._h = C.c_void_p()
-        st = lib.sbci_init_integrals(C.byref(self._h), int(norb), int(nalpha), int(nbeta),
-                                     h1.ctypes.data_as(C.c_void_p), eri.ctypes.data_as(C.c_void_p),
-                                     float(e_core), C.c_void_p(stream) if stream else None)
-        _check(st)
+        if _handle is not None:  # made by Context.many
+            self._h = _handle
+        else:
+            h1 = np.ascontiguousarray(h1, dtype=np.float64)
+            eri = np.ascontiguousarray(eri, dtype=np.float64)
+            self._h = C.c_void_p()
+            st = lib.sbci_init_integrals(C.byref(self._h), int(norb), int(nalpha), int(nbeta),
+                                         h1.ctypes.data_as(C.c_void_p), eri.ctypes.data_as(C.c_void_p),
+                                         float(e_core), C.c_void_p(stream) if stream else None)
+            _check(st)
         nd, na, nb, la, lb, npair = C.c_longlong(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(lib.sbci_dims(self._h, C.byref(nd), C.byref(na), C.byref(nb), C.byref(la),
                              C.byref(lb), C.byref(npair)))
@@ -196,6 +200,24 @@ class Context:
     @classmethod
     def from_integrals(cls, I, stream=None):
         return cls(I.norb, I.nalpha, I.nbeta, I.h1, I.eri, I.e_core, stream)
+
+    @classmethod
+    def many(cls, norb, nalpha, nbeta, h1, eri, e_core=0.0, streams=None, n=None):
+        """len(streams) (or n) contexts of the same integrals, created in
+        parallel by sbci_init_integrals_many; streams: CUDA stream handles,
+        one per context (None: each context makes its own)."""
+        lib = load()
+        if streams is None:
+            streams = [None] * int(n)
+        n = len(streams)
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        hs = (C.c_void_p * n)()
+        ss = (C.c_void_p * n)(*[C.c_void_p(x) if x else None for x in streams])
+        _check(lib.sbci_init_integrals_many(hs, n, int(norb), int(nalpha), int(nbeta),
+                                            h1.ctypes.data_as(C.c_void_p), eri.ctypes.data_as(C.c_void_p),
+                                            float(e_core), ss))
+        return [cls(norb, nalpha, nbeta, None, None, e_core, _handle=C.c_void_p(hs[i])) for i in range(n)]
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

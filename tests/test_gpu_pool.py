@@ -40,3 +40,25 @@ def test_recycled_buffers_give_identical_results():
     assert a1["cached_bytes"] > 0
     sbci.pool_trim()
     assert sbci.pool_stats()["cached_bytes"] == 0
+
+
+def test_contexts_made_in_parallel():
+    """sbci_init_integrals_many: contexts made on the host worker threads give
+    the sigma and the batched energies of contexts made one at a time
+    (bitwise); an invalid request leaves no context."""
+    sbci = require_lib()
+    I = make_integrals(("chain", 10, 1.2))
+    c = np.random.default_rng(9).standard_normal(63504)
+    p = sbci.params(sector=1, prec=sbci.SBCI_TF32X3)
+    many = sbci.Context.many(I.norb, I.nalpha, I.nbeta, I.h1, I.eri, I.e_core, n=4)
+    one = [sbci.Context.from_integrals(I) for _ in range(4)]
+    assert all(np.array_equal(a.sigma(c, prec=sbci.SBCI_FP64), b.sigma(c, prec=sbci.SBCI_FP64))
+               for a, b in zip(many, one))
+    Em, _, st1 = sbci.solve_batch(many, 2, p)
+    Eo, _, st2 = sbci.solve_batch(one, 2, p)
+    assert st1 == st2 == sbci.SBCI_OK and np.array_equal(Em, Eo)
+    for x in many + one:
+        x.close()
+    with pytest.raises(sbci.SbciError) as e:
+        sbci.Context.many(17, 1, 1, np.zeros((17, 17)), np.zeros((17,) * 4), 0.0, n=3)
+    assert e.value.status == sbci.SBCI_ERR_INVALID
