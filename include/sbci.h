@@ -75,7 +75,12 @@ typedef enum {
                       column-fused kernel (gather, contraction and scatter of one
                       column of the alpha part per CTA, no scratch in global
                       memory; SBCI_FUSED=0, read when a context is created,
-                      keeps the tile kernel and scatter) */
+                      keeps the tile kernel and scatter).  Where the tile
+                      kernel's operands take more than half of shared memory
+                      (npair > 55) it runs pipelined: epilogue warps drain one
+                      TMEM accumulator while the next tile is contracted
+                      (SBCI_TC_PIPE=0, read when a context is created, keeps
+                      the plain kernel; the same results) */
   SBCI_BF16X3 = 2, /* 3-term BF16 split on the tensor cores (D_hi W_hi + D_hi W_lo +
                       D_lo W_hi, FP32 accumulation; about 2^-17 relative per
                       product), every orbital count up to 16: the tensor-core
@@ -289,7 +294,11 @@ sbci_status sbci_solve(sbci_ctx *ctx, int k, const sbci_params *params, const do
  * scatter, or the column-fused kernel of singlet-sector solves with at most
  * 256 strings per spin -- the symmetric finish of sector solves, and the end
  * kernel; plus the host-driven ones).  Each context afterwards holds its
- * finished solve (sbci_finish, sbci_trace). */
+ * finished solve (sbci_finish, sbci_trace).  The per-solve host work between
+ * batch rounds (initial guesses, FP64 re-syncs and verifications, the next
+ * state's start) runs in parallel on the library's host worker threads, so
+ * contexts with their own CUDA streams overlap it; SBCI_HOST_THREADS=0 (read
+ * on first use) keeps it on the calling thread.  Results do not depend on it. */
 sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *params, double *energies,
                              sbci_report *rep, long long *launches);
 
@@ -312,7 +321,11 @@ sbci_status sbci_solve_batch(sbci_ctx **ctx, int n, int k, const sbci_params *pa
  * in the order the states were found (the pair's lower state first); rep as
  * sbci_solve (per state: H-products and steps while it was the lower state);
  * sbci_trace gives the step records of the pairs (b, c, k: b^{aa}, c^{aa},
- * k_0) followed by the last state's. */
+ * k_0) followed by the last state's.  The pair steps are driven from the
+ * host (the small eigen-problems on the host); SBCI_SBCI2_DEVICE=1, read when
+ * a context is created, runs them on a device controller as a CUDA-graph
+ * loop instead (the same steps; slower on GB300, whose FP64 rate makes the
+ * one-thread 6x6 eigen-solves dearer than the host round trips). */
 sbci_status sbci_solve_sbci2(sbci_ctx *ctx, int k, const sbci_params *params, int max_cycle2,
                              double *energies, double *vecs, sbci_report *rep);
 
