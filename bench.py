@@ -4,11 +4,12 @@ Headline workload: linear H10 chain, STO-3G, Loewdin basis, 1.2 A spacing, 10
 orbitals, 5 alpha / 5 beta electrons, 252 x 252 = 63,504 determinants; the
 ground state and 3 excited states in the c = c^T (singlet) sector; SBCI1 with
 the paper's thresholds, TF32x3 sigma with FP64 refinement.  One step = 16
-such solves through the batched engine (CUDA-event timing on the library
-stream, L2 flushed between steps).
+such solves through the batched engine, each solve's context on its own CUDA
+stream (CUDA-event timing around the call, L2 flushed between steps).
 
 Legs of the default line (rank 0, one GPU): an end-to-end number through the
-C ABI with host buffers; per-step latency percentiles; the same workload one
+C ABI with host buffers (each step creates its 16 contexts from the host
+integrals with sbci_init_integrals_many, solves them and destroys them); per-step latency percentiles; the same workload one
 solve per launch, mixed and plain FP64; the roofline of the dominant kernel
 (16 B per determinant per sigma, 2 npair^2 flops) and of every step kernel;
 the per-state energy error against the oracle's exact sector energies
