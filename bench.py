@@ -66,6 +66,12 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-n14", action="store_true")
     ap.add_argument("--no-n16", action="store_true")
+    ap.add_argument("--init-stage", type=int, default=0, choices=[0, 1],
+                    help="sbci_params.init_stage of the mixed-precision solves: the initial guess's "
+                         "H-products in the stage precision instead of FP64")
+    ap.add_argument("--large-solve", action="store_true",
+                    help="only the n = 16 random density-fitted space: one ground-state solve, BF16x3 stage "
+                         "on the tensor cores with FP64 refinement")
     ap.add_argument("--batch", type=int, default=16,
                     help="H10 solves per step, solved together by the batched persistent kernels "
                          "(1: one solve per step through its own graph loop)")
@@ -544,6 +550,40 @@ def random_df_n16_leg(pk, pk_kind, sm_mhz, reps=2):
     return res
 
 
+def large_solve_leg(init_stage=0):
+    """The single large solve of the n = 16 space (165,636,900 determinants):
+    the ground state with the BF16x3 stage on the tensor cores, FP64 re-syncs
+    and the FP64 verification to the paper's thresholds; wall time of the
+    solve (context creation excluded), H-products by precision, the FP64
+    residual and the GPU time per kernel family."""
+    import torch
+
+    from paper_2603_06101_gb300 import inputs, sbci
+
+    I = inputs.random_df(16, 16)
+    t0 = time.perf_counter()
+    ctx = sbci.Context.from_integrals(I)
+    t_ctx = time.perf_counter() - t0
+    p = sbci.params(prec=sbci.SBCI_BF16X3, init_stage=init_stage)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    t0 = time.perf_counter()
+    E, _, R, st = ctx.solve(1, p)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = {k: {"launches": v[0], "ms": v[1]} for k, v in ctx.profile_read().items() if v[0]}
+    ctx.profile(False)
+    res = {"workload": "random density-fitted integrals n=16, 8a/8b, seed 16", "ndet": ctx.ndet,
+           "npair": ctx.npair, "context_seconds": t_ctx, "init_stage": init_stage,
+           "solve_bf16x3_ground_state": {
+               "seconds": wall, "status": int(st), "energy": float(E[0]), "converged": int(R[0].converged),
+               "fp64_residual": float(R[0].residual), "r0": float(p.r0), "sigma": int(R[0].n_sigma),
+               "fp64_sigma": int(R[0].n_sigma_fp64), "kernels": prof}}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
 
@@ -559,7 +599,7 @@ def run_gb300(args, rank, world, local_rank):
             "bf16x3": sbci.SBCI_BF16X3}[args.prec]
     stream = torch.cuda.Stream()
     ctx = sbci.Context.from_integrals(I, stream=stream.cuda_stream)
-    p = sbci.params(sector=1, prec=prec)
+    p = sbci.params(sector=1, prec=prec, init_stage=args.init_stage)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     B = max(1, args.batch) if args.prec == "tf32x3" else 1  # (the batch engine takes TF32x3 solves)
     # one CUDA stream per solve: a solve's own work between batch rounds (its
@@ -733,7 +773,8 @@ def run_gb300(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "norb": 10, "ndet": ndet, "states": NSTATES,
                        "solves_per_step": B, "engine": "batched persistent kernels, one graph loop" if B > 1
                        else "one graph loop per solve",
-                       "sector": "c=c^T", "sigma_precision": args.prec, "l2": "flushed (256 MB write) between steps",
+                       "sector": "c=c^T", "sigma_precision": args.prec, "init_stage": args.init_stage,
+                       "l2": "flushed (256 MB write) between steps",
                        "parallelism": f"replicas x{world}", "sigma_per_solve": nsig,
                        "sigma_per_state": [int(r.n_sigma) for r in R],
                        "fp64_sigma_per_state": [int(r.n_sigma_fp64) for r in R],
@@ -788,7 +829,7 @@ def run_ncu_solve(args):
     ctx = sbci.Context.from_integrals(I)
     prec = {"fp64": sbci.SBCI_FP64, "fp32": sbci.SBCI_FP32, "tf32x3": sbci.SBCI_TF32X3,
             "bf16x3": sbci.SBCI_BF16X3}[args.prec]
-    p = sbci.params(sector=1, prec=prec)
+    p = sbci.params(sector=1, prec=prec, init_stage=args.init_stage)
     B = max(1, args.batch) if args.prec == "tf32x3" else 1
     if B == 1:
         E, _, R, st = ctx.solve(NSTATES, p)
@@ -891,6 +932,9 @@ def main():
         return
     if args.ncu:
         run_ncu_solve(args)
+        return
+    if args.large_solve:
+        print(json.dumps({"random_df_n16": large_solve_leg(args.init_stage)}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -127,6 +127,12 @@ typedef struct {
   long long noise_seed; /* seed of r: element I of state alpha's vector is the SplitMix64
                            output of seed + 0x9E3779B97F4A7C15*(alpha*2^40 + I + 1),
                            top 53 bits mapped to [-1, 1).  0 */
+  int init_stage;   /* 1: the H-products of the lowest-diagonal start (S1.1: H of each
+                       start vector, giving the subspace matrix, E_0 and X_0) in the
+                       stage precision prec instead of FP64, so that a mixed solve's
+                       first FP64 H-product is its first re-sync (which replaces X by
+                       an FP64 H x); no effect with prec = SBCI_FP64 or init = 1.
+                       0 or 1, else SBCI_ERR_INVALID.  0 */
 } sbci_params;
 
 typedef struct {

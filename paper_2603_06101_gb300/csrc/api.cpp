@@ -965,10 +965,13 @@ sbci_status initial_guess(sbci_ctx *c, int k, double *E0) {
   RET(dmalloc(&d_aux, pairs.size() + 2 * nA));
   CK(cudaMemcpyAsync(d_aux, pairs.data(), sizeof(double) * pairs.size(), cudaMemcpyHostToDevice, c->stream));
   std::vector<double> A(m * m);
+  // FP64, or the stage precision with init_stage (the start is then as exact
+  // as the stage's own steps; the first re-sync makes X an FP64 H x)
+  const int ip = s.p.init_stage ? s.p.prec : SBCI_FP64;
   for (int i = 0; i < m; ++i) {
     CK(cudaMemsetAsync(s.w, 0, sizeof(double) * c->ndet, c->stream));
     CK(launch_sparse_set(s.w, d_aux + 2 * pofs[i], (int)(pofs[i + 1] - pofs[i]), c->stream));
-    RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, SBCI_FP64));
+    RET(run_sigma(c, s.w, tmp + (size_t)i * c->ndet, ip));
   }
   {  // A[i][j] = sum over the entries (I, v) of basis i of v (H b_j)[I], in that order
     std::vector<double> offs;
@@ -1535,6 +1538,10 @@ sbci_status begin_common(sbci_ctx *c, int k, const sbci_params *params, const ch
   else sbci_params_init(&s.p);
   if (s.p.sector && c->ne_a != c->ne_b) {
     set_error("sector = 1 needs nalpha == nbeta");
+    return SBCI_ERR_INVALID;
+  }
+  if (s.p.init_stage != 0 && s.p.init_stage != 1) {
+    set_error("init_stage must be 0 or 1");
     return SBCI_ERR_INVALID;
   }
   RET(check_prec(c, s.p.prec));
@@ -2482,6 +2489,7 @@ sbci_status sbci_params_init(sbci_params *p) {
   p->refine_max_sigma = 300;
   p->start_noise = 0.0;
   p->noise_seed = 0;
+  p->init_stage = 0;
   return SBCI_OK;
 }
 

@@ -46,7 +46,7 @@ class sbci_params(C.Structure):
                 ("gs_tol", C.c_double), ("sector", C.c_int), ("n_init", C.c_int), ("init", C.c_int),
                 ("prec", C.c_int), ("mixed_eps", C.c_double), ("mixed_r", C.c_double),
                 ("refine_max_sigma", C.c_int), ("start_noise", C.c_double),
-                ("noise_seed", C.c_longlong)]
+                ("noise_seed", C.c_longlong), ("init_stage", C.c_int)]
 
 
 class sbci_report(C.Structure):

@@ -50,6 +50,45 @@ def test_bench_config_h10_sector_batch16():
         c.close()
 
 
+def test_init_stage_h10_sector_batch():
+    """init_stage = 1 (the start's H-products in TF32x3): 8 batched H10
+    solves equal the solve run alone bit for bit and meet the oracle's exact
+    sector energies to the FP64 target after refinement; the start itself
+    (sbci_begin) runs its H-products (one per start vector: two here, the
+    four lowest determinants being two transposed pairs) on the tensor-core
+    kernel instead of the FP64 one."""
+    sbci = require_lib()
+    key = ("chain", 10, 1.2)
+    I = make_integrals(key)
+    p = sbci.params(sector=1, prec=sbci.SBCI_TF32X3, init_stage=1)
+    ctxs = [sbci.Context.from_integrals(I) for _ in range(8)]
+    E, R, st = sbci.solve_batch(ctxs, 4, p)
+    assert st == sbci.SBCI_OK
+    assert all(r.converged for r in R)
+    Ea = _alone(sbci, I, 4, p)
+    ref = oracle_sector_energies(key, 4) + I.e_core
+    for i in range(8):
+        assert np.array_equal(E[i], Ea), np.abs(E[i] - Ea).max()
+        err = np.abs(np.sort(E[i]) - ref)
+        assert err.max() < E_TOL, err
+    for c in ctxs:
+        c.close()
+    ctx = sbci.Context.from_integrals(I)
+    counts = {}
+    for stage in (0, 1):
+        ctx.profile(False)  # resets the launch counts
+        ctx.begin(4, sbci.params(sector=1, prec=sbci.SBCI_TF32X3, init_stage=stage))
+        st = ctx.profile_read()
+        counts[stage] = (st.get("sigma_gather_contract_os", (0, 0.0))[0],
+                         st.get("sigma_gather_contract_tc", (0, 0.0))[0])
+    _, _, R1, st1 = ctx.solve(4, p)
+    ctx.close()
+    m = counts[0][0]
+    assert m >= 1 and counts[0][1] == 0 and counts[1] == (0, m), counts
+    assert st1 == sbci.SBCI_OK and all(r.converged for r in R1)
+    assert all(r.n_sigma_fp64 >= 1 for r in R1)  # every state ends on FP64 H-products
+
+
 def test_sector_batch_uneven_sizes():
     """H6 / H8 / H10 / H12 in the sector, one batch: each equals its solve run
     alone bit for bit; H6-H10 meet the oracle's exact sector energies and H12
